@@ -1,0 +1,159 @@
+"""MPDATA oracle -- test infrastructure only.
+
+A plain FP64 CPU implementation of one MPDATA time step (libmpdata++ 0.1 paper,
+Sect. 3.1 and 4.1), with its tangent-linear and adjoint, written in C++
+(``mpdata_oracle.cpp``) and loaded through ctypes.  Only the tests, the
+package smoke check and the benchmark's CPU-baseline leg use this module; the
+CUDA library never imports, links or calls it.
+
+Parity status per function (details in the header of ``mpdata_oracle.cpp``):
+every sub-step is pinned by the tests in ``tests/test_oracle_pins.py``, except
+the multi-dimensional cross terms of the third-order option, which are pinned
+only by the convergence order on a diagonal flow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "mpdata_oracle.cpp")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD_DIR, "libmpdata_oracle.so")
+
+# option bits, same values as the library interface (the oracle defines its own)
+FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B = 1, 2, 4, 8, 16, 32, 64
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (host C++ only, no CUDA)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-shared", "-fPIC", SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint
+            dbl = ctypes.c_double
+            lib.mpo_step_ex.argtypes = [i32, d, d, d, d, d, d, d, dbl, i32, u32, i64, d, d]
+            lib.mpo_step_ex.restype = i32
+            lib.mpo_tl_step.argtypes = [i32, d, d, d, d, d, d, d, dbl, i32, u32, d, d, d, d, d]
+            lib.mpo_tl_step.restype = i32
+            lib.mpo_adj_step.argtypes = [i32, d, d, d, d, d, d, d, dbl, i32, u32, d, d, d, d]
+            lib.mpo_adj_step.restype = i32
+            lib.mpo_mass.argtypes = [i32, d, d, d]
+            lib.mpo_mass.restype = dbl
+            lib.mpo_set_threads.argtypes = [i32]
+            lib.mpo_set_threads.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(psi, gc, g, r):
+    psi = _f64(psi)
+    nd = psi.ndim
+    if len(gc) != nd:
+        raise ValueError("need one advector component per dimension")
+    gc = [_f64(v) for v in gc]
+    for v in gc:
+        if v.shape != psi.shape:
+            raise ValueError("advector components must have the field's shape")
+    g, r = _f64(g), _f64(r)
+    shape = np.array(psi.shape, dtype=np.int64)
+    gcp = [_ptr(v) for v in gc] + [None] * (3 - nd)
+    return psi, nd, shape, gc, gcp, g, r
+
+
+def _opts(opts, g, r, rhs):
+    o = int(opts)
+    if g is not None:
+        o |= NUG
+    if r is not None:
+        o |= RHS_EULER_B if rhs == "euler_b" else RHS_EULER_A
+    return o
+
+
+def step(psi, gc, g=None, r=None, dt=0.0, n_iters=2, opts=0, n_steps=1,
+         rhs="euler_a", return_bounds=False):
+    """Advance psi by n_steps MPDATA steps; returns the new field (a copy).
+
+    gc: sequence of advector components (G times Courant number), one per
+    dimension, each with psi's shape; component d at index i sits on the face
+    between cell i and cell i + e_d (periodic).  g: G field or None (G = 1).
+    r: source term or None; rhs selects 'euler_a' or 'euler_b' (Sect. 4.1).
+    """
+    psi, nd, shape, gc, gcp, g, r = _prep(psi, gc, g, r)
+    out = psi.copy()
+    mx = np.zeros_like(out) if return_bounds else None
+    mn = np.zeros_like(out) if return_bounds else None
+    rc = _load().mpo_step_ex(nd, _ptr(shape), _ptr(out), *gcp, _ptr(g), _ptr(r), float(dt),
+                             int(n_iters), _opts(opts, g, r, rhs), int(n_steps), _ptr(mx), _ptr(mn))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return (out, mx, mn) if return_bounds else out
+
+
+def tl_step(psi, gc, dpsi, dgc, g=None, r=None, dt=0.0, n_iters=2, opts=0, rhs="euler_a"):
+    """Tangent-linear of one step at (psi, gc) applied to (dpsi, dgc)."""
+    psi, nd, shape, gc, gcp, g, r = _prep(psi, gc, g, r)
+    dpsi = _f64(dpsi)
+    dgc = [None if v is None else _f64(v) for v in dgc] + [None] * (3 - nd)
+    out = np.zeros_like(psi)
+    rc = _load().mpo_tl_step(nd, _ptr(shape), _ptr(psi), *gcp, _ptr(g), _ptr(r), float(dt),
+                             int(n_iters), _opts(opts, g, r, rhs), _ptr(dpsi),
+                             *[_ptr(v) for v in dgc], _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return out
+
+
+def adj_step(psi, gc, psi_bar, g=None, r=None, dt=0.0, n_iters=2, opts=0, rhs="euler_a"):
+    """Adjoint of one step at (psi, gc): returns (dL/dpsi^n, [dL/dgc_d])."""
+    psi, nd, shape, gc, gcp, g, r = _prep(psi, gc, g, r)
+    pb = _f64(psi_bar).copy()
+    gcb = [np.zeros_like(psi) for _ in range(nd)]
+    ptrs = [_ptr(v) for v in gcb] + [None] * (3 - nd)
+    rc = _load().mpo_adj_step(nd, _ptr(shape), _ptr(psi), *gcp, _ptr(g), _ptr(r), float(dt),
+                              int(n_iters), _opts(opts, g, r, rhs), _ptr(pb), *ptrs)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return pb, gcb
+
+
+def mass(psi, g=None):
+    """Sum of G * psi in FP64 (G = 1 when g is None)."""
+    psi = _f64(psi)
+    g = _f64(g)
+    shape = np.array(psi.shape, dtype=np.int64)
+    return float(_load().mpo_mass(psi.ndim, _ptr(shape), _ptr(psi), _ptr(g)))
+
+
+def set_threads(n: int) -> int:
+    """Set the OpenMP thread count of the forward sweeps; returns the count in use."""
+    return int(_load().mpo_set_threads(int(n)))
