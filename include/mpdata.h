@@ -1,0 +1,166 @@
+/*
+ * mpdata.h -- C ABI of the GB300 MPDATA step library.
+ *
+ * One MPDATA time step for the generalised transport equation
+ *     d_t(G psi) + div(G u psi) = G R                         (paper Sect. 1, Eq. 1)
+ * solved in the homogeneous form d_t psi + (1/G) div(G u psi) = 0 (Sect. 3.1, Eq. 3)
+ * with the source term applied by the euler_a / euler_b schemes of Sect. 4.1, on a
+ * periodic Arakawa-C grid (Sect. 2.3): psi and G at cell centres, the advector
+ * GC = G u dt/dx (Sect. 3.1.1, text after Eq. 5) on cell faces.  A step is a
+ * donor-cell pass (Eqs. 4-5) followed by n_iters-1 corrective passes with the
+ * antidiffusive advector (Eq. 6), optionally with the third-order terms
+ * (Sect. 3.1.2), the infinite-gauge variant (Sect. 3.1.5) and the
+ * non-oscillatory (FCT) limiter (Sect. 3.1.4).  Everything runs in hand-written
+ * CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Layout (Sect. 3.2.5): row-major, last dimension fastest.  A field of shape
+ * (n_0, ..., n_{D-1}) holds N = prod n_d values.  Advector component d is a
+ * separate array of N values; its element i sits on the face between cell i and
+ * cell i + e_d, wrapping periodically (so each dimension has n_d faces, not the
+ * n_d - 1 of the paper's open boundaries).  Batched handles (n_fields > 1) hold
+ * fields of possibly different shapes; every per-field array is the
+ * concatenation of the fields in order, field f starting at the sum of the cell
+ * counts of fields 0..f-1.
+ *
+ * Ownership: every pointer argument that names a field is a DEVICE pointer
+ * (cudaMalloc'd or a tensor's storage on the handle's device), owned by the
+ * caller, never freed or retained by the library.  FP32 handles take float
+ * arrays, FP64 handles double arrays, aligned to their element size (16 bytes
+ * for the vectorised 2D path; misaligned pointers give MPDATA_EINVAL).  The
+ * handle owns only its device scratch.  Host pointers are marked "host".
+ *
+ * Errors: every call returns MPDATA_OK or an MPDATA_E* code; no call aborts the
+ * process or throws (the C analogue of the library's std::runtime_error,
+ * Sect. 2.4).  All device work is enqueued on the handle's stream and is
+ * asynchronous; a device-side failure (for example a persistent-kernel barrier
+ * that timed out) is reported by the next call on the handle that synchronises
+ * (mpdata_reduce, mpdata_sync) and then cleared.
+ */
+#ifndef MPDATA_GB300_H
+#define MPDATA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpdata_s* mpdata_t;
+
+/* element types */
+enum { MPDATA_F32 = 0, MPDATA_F64 = 1 };
+
+/* option bits (Sect. 3.1.2-3.1.5, 4.1; compile-time opts of the paper become run-time bits) */
+enum {
+  MPDATA_FCT = 1u,          /* non-oscillatory limiter (Sect. 3.1.4) */
+  MPDATA_TOT = 2u,          /* third-order terms (Sect. 3.1.2) */
+  MPDATA_IGA = 4u,          /* infinite gauge (Sect. 3.1.5); requires n_iters == 2 */
+  MPDATA_NUG = 8u,          /* non-unit G: a G field is passed to every step */
+  MPDATA_KAHAN = 16u,       /* compensated summation in the donor-cell passes (Sect. 3.1.1) */
+  MPDATA_RHS_EULER_A = 32u, /* psi^{n+1} = ADV(psi^n) + dt R (Sect. 4.1) */
+  MPDATA_RHS_EULER_B = 64u, /* psi^{n+1} = ADV(psi^n + dt R) (Sect. 4.1) */
+  MPDATA_STAGED = 128u      /* run the one-kernel-per-sub-step path even where a fused
+                               kernel covers the case (comparison and testing) */
+};
+
+/* status codes */
+enum {
+  MPDATA_OK = 0,
+  MPDATA_EINVAL = 1,       /* invalid argument */
+  MPDATA_EUNSUPPORTED = 2, /* valid but not supported by this build */
+  MPDATA_ECUDA = 3,        /* a CUDA runtime call failed */
+  MPDATA_ECOURANT = 4,     /* Courant check failed (sum of outflow advectors / G > 1) */
+  MPDATA_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  MPDATA_ESTOPPED = 6,     /* stopped after a step by mpdata_request_stop */
+  MPDATA_ENOMEM = 7        /* device or host allocation failed */
+};
+
+/*
+ * Creates a handle for n_fields independent fields of ndims dimensions.
+ * shapes (host): n_fields * ndims int64 extents, field after field.
+ * dtype: MPDATA_F32 or MPDATA_F64.  n_iters >= 1 passes per step (Sect. 3.1.1).
+ * opts: OR of MPDATA_* option bits.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream) on the current device; all work of the handle goes there.
+ * Errors: EINVAL for ndims not in 1..3, n_fields < 1, a non-positive extent,
+ * n_iters < 1, IGA with n_iters != 2, both RHS bits; ENOMEM; ECUDA.
+ */
+int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype,
+                  int n_iters, uint32_t opts, void* cuda_stream);
+
+/*
+ * Advances psi in place by n_steps >= 1 steps (the paper's advance(), Sect. 3.2.5).
+ * gc (host array of ndims device pointers): advector components, constant over
+ * the call.  g: G field (required iff MPDATA_NUG, else NULL).  r: source term R
+ * (required iff an RHS bit is set, else NULL), dt its time step.
+ * Errors: EINVAL (null or misaligned pointers, n_steps < 1), ESTOPPED when a stop
+ * was requested (the steps already enqueued complete), ECUDA.
+ */
+int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, const void* r,
+                double dt, int n_steps);
+
+/*
+ * Out-of-place variant: reads psi_in, writes psi_out (distinct buffers, or the
+ * same buffer for in-place).  gc_scale (host, nullable): n_steps factors; step s
+ * uses the advector gc * gc_scale[s] (a time-dependent flow evaluated at the
+ * half step, Sect. 3.1.1 text after Eq. 5).  Errors as mpdata_step.
+ */
+int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* const* gc,
+                   const void* g, const void* r, double dt, int n_steps, const double* gc_scale);
+
+/*
+ * Reverse of ONE step from state psi_n (no sources; R enters linearly and has no
+ * adjoint here): on entry psi_bar = dL/dpsi^{n+1}, on exit dL/dpsi^n (in place).
+ * gc_bar (host array of ndims device pointers, or NULL): dL/dgc_d is ADDED to
+ * gc_bar[d].  Branches (signs, FCT min/max) follow the forward step's choices;
+ * [x]+ and [x]- have derivative 1/2 at 0.  Errors: EINVAL, EUNSUPPORTED for
+ * batched handles, ECUDA.
+ */
+int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
+                        void* psi_bar, void* const* gc_bar);
+
+/*
+ * FP64 reductions over each field (host outputs, n_fields entries each):
+ * mass_out[f] = sum G psi (G = 1 when g is NULL).  Synchronises the stream.
+ */
+int mpdata_reduce(mpdata_t h, const void* psi, const void* g, double* mass_out);
+
+/*
+ * FP64 difference norms per field (host outputs, nullable): l2sq_out[f] =
+ * sum (a - b)^2, linf_out[f] = max |a - b|.  Synchronises the stream.
+ */
+int mpdata_diff_norms(mpdata_t h, const void* a, const void* b, double* l2sq_out, double* linf_out);
+
+/*
+ * Courant check (Sect. 3.1.1 stability of the donor-cell pass): returns
+ * MPDATA_ECOURANT if at some cell sum_d ([gc_d(i)]+ - [gc_d(i - e_d)]-) / G_i > 1,
+ * writing that maximum to *max_out (host, nullable).  Synchronises the stream.
+ */
+int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, double* max_out);
+
+/*
+ * Asks the handle to stop: later mpdata_step / mpdata_advance calls return
+ * MPDATA_ESTOPPED without enqueuing work, and a multi-step call stops after the
+ * step in progress (the paper's panic flag, Sect. 3.2.5).  Thread-safe.
+ * mpdata_clear_stop re-arms the handle.
+ */
+int mpdata_request_stop(mpdata_t h);
+int mpdata_clear_stop(mpdata_t h);
+
+/* Waits for the handle's stream and returns the first pending device error, if any. */
+int mpdata_sync(mpdata_t h);
+
+/* Destroys the handle and frees its scratch (after synchronising its stream). */
+int mpdata_destroy(mpdata_t h);
+
+/* Static description of a status code. */
+const char* mpdata_strerror(int code);
+
+/* Library version string. */
+const char* mpdata_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDATA_GB300_H */

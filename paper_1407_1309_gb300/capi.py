@@ -1,0 +1,209 @@
+"""Thin ctypes binding of the C ABI in include/mpdata.h.
+
+The functions keep the C names and only marshal arguments: tensors become
+device pointers (``data_ptr()``), sequences of advector components become
+host arrays of pointers, status codes become exceptions.  Every computation
+runs in the CUDA library; if the library cannot be built or loaded this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+# element types, option bits and status codes (include/mpdata.h)
+F32, F64 = 0, 1
+FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B, STAGED = 1, 2, 4, 8, 16, 32, 64, 128
+OK, EINVAL, EUNSUPPORTED, ECUDA, ECOURANT, ETIMEOUT, ESTOPPED, ENOMEM = range(8)
+
+EXPORTED = (
+    "mpdata_create", "mpdata_step", "mpdata_advance", "mpdata_adjoint_step", "mpdata_reduce",
+    "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
+    "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version",
+)
+
+
+class MpdataError(RuntimeError):
+    """A non-OK status code returned by the library."""
+
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {mpdata_strerror(code)} (status {code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libmpdata_gb300.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_needed and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with `python -m paper_1407_1309_gb300.build`")
+        lib = ctypes.CDLL(path)
+        P, I, U, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_double, ctypes.c_int64
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        DP = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "mpdata_create": ([ctypes.POINTER(ctypes.c_void_p), I, I, ctypes.POINTER(I64), I, I, U, P], I),
+            "mpdata_step": ([P, P, PP, P, P, D, I], I),
+            "mpdata_advance": ([P, P, P, PP, P, P, D, I, DP], I),
+            "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
+            "mpdata_reduce": ([P, P, P, DP], I),
+            "mpdata_diff_norms": ([P, P, P, DP, DP], I),
+            "mpdata_check_courant": ([P, PP, P, DP], I),
+            "mpdata_request_stop": ([P], I),
+            "mpdata_clear_stop": ([P], I),
+            "mpdata_sync": ([P], I),
+            "mpdata_destroy": ([P], I),
+            "mpdata_strerror": ([I], ctypes.c_char_p),
+            "mpdata_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Device pointer of a tensor (or an int address); None stays NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"expected a tensor or an address, got {type(x)!r}")
+
+
+def _ptr_array(xs):
+    if xs is None:
+        return None
+    arr = (ctypes.c_void_p * max(1, len(xs)))(*[_ptr(x) for x in xs])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise MpdataError(rc, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def mpdata_strerror(code: int) -> str:
+    return load().mpdata_strerror(int(code)).decode()
+
+
+def mpdata_version() -> str:
+    return load().mpdata_version().decode()
+
+
+def mpdata_create(ndims, shapes, dtype, n_iters, opts, stream=None, *, raw=False):
+    """shapes: one tuple of ndims extents per field.  Returns the handle (int)."""
+    flat = [int(s) for shp in shapes for s in shp]
+    arr = (ctypes.c_int64 * max(1, len(flat)))(*flat)
+    h = ctypes.c_void_p()
+    rc = load().mpdata_create(ctypes.byref(h), int(ndims), len(shapes), arr, int(dtype), int(n_iters),
+                              int(opts), _stream_ptr(stream))
+    if raw:
+        return rc, h.value
+    _check(rc, "mpdata_create")
+    return h.value
+
+
+def mpdata_step(h, psi, gc, g=None, r=None, dt=0.0, n_steps=1, *, raw=False):
+    gcp, _keep = _ptr_array(gc)
+    rc = load().mpdata_step(h, _ptr(psi), gcp, _ptr(g), _ptr(r), float(dt), int(n_steps))
+    if raw:
+        return rc
+    _check(rc, "mpdata_step")
+
+
+def mpdata_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1, gc_scale=None, *, raw=False):
+    gcp, _keep = _ptr_array(gc)
+    sc = None
+    if gc_scale is not None:
+        sc = (ctypes.c_double * len(gc_scale))(*[float(v) for v in gc_scale])
+        if len(gc_scale) < n_steps:
+            raise ValueError("gc_scale needs one factor per step")
+    rc = load().mpdata_advance(h, _ptr(psi_in), _ptr(psi_out), gcp, _ptr(g), _ptr(r), float(dt), int(n_steps),
+                               ctypes.cast(sc, ctypes.POINTER(ctypes.c_double)) if sc is not None else None)
+    if raw:
+        return rc
+    _check(rc, "mpdata_advance")
+
+
+def mpdata_adjoint_step(h, psi_n, gc, g, psi_bar, gc_bar=None, *, raw=False):
+    gcp, _k1 = _ptr_array(gc)
+    gbp = None
+    if gc_bar is not None:
+        gbp, _k2 = _ptr_array(gc_bar)
+    rc = load().mpdata_adjoint_step(h, _ptr(psi_n), gcp, _ptr(g), _ptr(psi_bar), gbp)
+    if raw:
+        return rc
+    _check(rc, "mpdata_adjoint_step")
+
+
+def mpdata_reduce(h, psi, g=None, n_fields=1):
+    out = (ctypes.c_double * n_fields)()
+    _check(load().mpdata_reduce(h, _ptr(psi), _ptr(g), out), "mpdata_reduce")
+    return list(out)
+
+
+def mpdata_diff_norms(h, a, b, n_fields=1):
+    l2 = (ctypes.c_double * n_fields)()
+    li = (ctypes.c_double * n_fields)()
+    _check(load().mpdata_diff_norms(h, _ptr(a), _ptr(b), l2, li), "mpdata_diff_norms")
+    return list(l2), list(li)
+
+
+def mpdata_check_courant(h, gc, g=None):
+    """Returns (status, max outflow sum); status is OK or ECOURANT."""
+    gcp, _keep = _ptr_array(gc)
+    m = ctypes.c_double(0.0)
+    rc = load().mpdata_check_courant(h, gcp, _ptr(g), ctypes.byref(m))
+    if rc not in (OK, ECOURANT):
+        _check(rc, "mpdata_check_courant")
+    return rc, m.value
+
+
+def mpdata_request_stop(h):
+    _check(load().mpdata_request_stop(h), "mpdata_request_stop")
+
+
+def mpdata_clear_stop(h):
+    _check(load().mpdata_clear_stop(h), "mpdata_clear_stop")
+
+
+def mpdata_sync(h, *, raw=False):
+    rc = load().mpdata_sync(h)
+    if raw:
+        return rc
+    _check(rc, "mpdata_sync")
+
+
+def mpdata_destroy(h):
+    _check(load().mpdata_destroy(h), "mpdata_destroy")

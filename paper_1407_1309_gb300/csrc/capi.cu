@@ -1,0 +1,341 @@
+// C ABI of the library (include/mpdata.h): handle management, argument
+// validation, dispatch to the fused / batched / staged kernels, reductions.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+struct mpdata_s {
+  int nd = 0, n_fields = 0, dtype = 0, n_iters = 0;
+  uint32_t opts = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<mpd::Grid> grids;
+  std::vector<long long> offsets;
+  long long total = 0, n_max = 0;
+  size_t esize = 4;
+  void* staged = nullptr;            // staged-path scratch
+  void* pingpong = nullptr;          // out-of-place buffer for the fused paths (total elements)
+  void* adj = nullptr;               // adjoint scratch
+  mpd::FieldSpan* d_spans = nullptr;
+  double* d_partial = nullptr;       // 2 * kRedBlocks * n_fields
+  double* d_out = nullptr;           // 2 * n_fields
+  double* h_out = nullptr;           // pinned, 2 * n_fields
+  int* d_status = nullptr;           // device-side error word (bounded waits)
+  void* batch = nullptr;             // batched-kernel tables
+  std::atomic<int> stop{0};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+template <typename T>
+int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv, const T* g, const T* r,
+                double dt, int n_steps, const double* gc_scale) {
+  const mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
+  const T* gc[3] = {static_cast<const T*>(gcv[0]), h->nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
+                    h->nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
+  const mpd::StagedScratch<T> ss = mpd::carve_staged<T>(h->staged, h->n_max);
+  for (int s = 0; s < n_steps; ++s) {
+    if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
+    const T scale = gc_scale ? static_cast<T>(gc_scale[s]) : T(1);
+    const T* src = (s == 0) ? psi_in : psi_out;
+    if (h->n_fields > 1 && !o.staged) {
+      int rc = mpd::batched_step<T>(h, src, psi_out, gc, g, r, static_cast<T>(dt), scale, o);
+      if (rc != MPDATA_EUNSUPPORTED) {
+        if (rc != MPDATA_OK) return rc;
+        continue;
+      }
+    }
+    for (int f = 0; f < h->n_fields; ++f) {
+      const long long off = h->offsets[f];
+      const mpd::Grid& gr = h->grids[f];
+      mpd::StepArgs<T> a;
+      a.psi_in = src + off;
+      a.psi_out = psi_out + off;
+      for (int d = 0; d < 3; ++d) a.gc[d] = (d < h->nd) ? gc[d] + off : nullptr;
+      a.g = g ? g + off : nullptr;
+      a.r = r ? r + off : nullptr;
+      a.dt = static_cast<T>(dt);
+      a.gc_scale = scale;
+      int rc = o.staged ? MPDATA_EUNSUPPORTED
+                        : mpd::fused_step<T>(gr, o, a, static_cast<T*>(h->pingpong) + off, h->stream);
+      if (rc == MPDATA_EUNSUPPORTED) rc = cuda_status(mpd::staged_step<T>(gr, o, a, ss, h->stream));
+      if (rc != MPDATA_OK) return rc;
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int validate_fields(mpdata_s* h, const void* psi, const void* const* gc, const void* g, const void* r) {
+  if (!psi || !gc) return MPDATA_EINVAL;
+  if (!aligned(psi, h->esize)) return MPDATA_EINVAL;
+  for (int d = 0; d < h->nd; ++d)
+    if (!gc[d] || !aligned(gc[d], h->esize)) return MPDATA_EINVAL;
+  const bool nug = h->opts & MPDATA_NUG;
+  if (nug != (g != nullptr)) return MPDATA_EINVAL;
+  if (g && !aligned(g, h->esize)) return MPDATA_EINVAL;
+  const bool rhs = h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B);
+  if (rhs != (r != nullptr)) return MPDATA_EINVAL;
+  if (r && !aligned(r, h->esize)) return MPDATA_EINVAL;
+  return MPDATA_OK;
+}
+
+int sync_status(mpdata_s* h) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  int st = 0;
+  e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  if (st != 0) {
+    cudaMemset(h->d_status, 0, sizeof(int));
+    return st;
+  }
+  return MPDATA_OK;
+}
+
+void free_all(mpdata_s* h) {
+  cudaFree(h->staged);
+  cudaFree(h->pingpong);
+  cudaFree(h->adj);
+  cudaFree(h->d_spans);
+  cudaFree(h->d_partial);
+  cudaFree(h->d_out);
+  cudaFree(h->d_status);
+  cudaFreeHost(h->h_out);
+  mpd::batched_free(h);
+}
+
+}  // namespace
+
+namespace mpd {
+int handle_nd(const mpdata_s* h) { return h->nd; }
+int handle_fields(const mpdata_s* h) { return h->n_fields; }
+const Grid* handle_grids(const mpdata_s* h) { return h->grids.data(); }
+const long long* handle_offsets(const mpdata_s* h) { return h->offsets.data(); }
+long long handle_total(const mpdata_s* h) { return h->total; }
+cudaStream_t handle_stream(const mpdata_s* h) { return h->stream; }
+int* handle_status(const mpdata_s* h) { return h->d_status; }
+void** handle_batch(mpdata_s* h) { return &h->batch; }
+void** handle_adj(mpdata_s* h) { return &h->adj; }
+int handle_n_iters(const mpdata_s* h) { return h->n_iters; }
+uint32_t handle_opts(const mpdata_s* h) { return h->opts; }
+}  // namespace mpd
+
+extern "C" {
+
+int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype, int n_iters,
+                  uint32_t opts, void* cuda_stream) {
+  if (!out || !shapes) return MPDATA_EINVAL;
+  *out = nullptr;
+  if (ndims < 1 || ndims > 3 || n_fields < 1 || n_iters < 1) return MPDATA_EINVAL;
+  if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return MPDATA_EINVAL;
+  if (opts & ~255u) return MPDATA_EINVAL;
+  if ((opts & MPDATA_IGA) && n_iters != 2) return MPDATA_EINVAL;
+  if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
+  for (long long i = 0; i < static_cast<long long>(n_fields) * ndims; ++i)
+    if (shapes[i] < 1 || shapes[i] > (int64_t(1) << 30)) return MPDATA_EINVAL;
+  mpdata_s* h = new (std::nothrow) mpdata_s;
+  if (!h) return MPDATA_ENOMEM;
+  h->nd = ndims;
+  h->n_fields = n_fields;
+  h->dtype = dtype;
+  h->n_iters = n_iters;
+  h->opts = opts;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->esize = dtype == MPDATA_F32 ? 4 : 8;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return MPDATA_ECUDA; }
+  std::vector<mpd::FieldSpan> spans(n_fields);
+  for (int f = 0; f < n_fields; ++f) {
+    mpd::Grid g = mpd::make_grid(ndims, shapes + static_cast<long long>(f) * ndims);
+    h->grids.push_back(g);
+    h->offsets.push_back(h->total);
+    spans[f] = {h->total, g.N};
+    h->total += g.N;
+    if (g.N > h->n_max) h->n_max = g.N;
+  }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chk(cudaMalloc(&h->staged, static_cast<size_t>(mpd::kStagedArrays) * h->n_max * h->esize));
+  chk(cudaMalloc(&h->pingpong, static_cast<size_t>(h->total) * h->esize));
+  chk(cudaMalloc(&h->d_spans, sizeof(mpd::FieldSpan) * n_fields));
+  chk(cudaMalloc(&h->d_partial, sizeof(double) * 2 * mpd::kRedBlocks * n_fields));
+  chk(cudaMalloc(&h->d_out, sizeof(double) * 2 * n_fields));
+  chk(cudaMalloc(&h->d_status, sizeof(int)));
+  chk(cudaMallocHost(&h->h_out, sizeof(double) * 2 * n_fields));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_spans, spans.data(), sizeof(mpd::FieldSpan) * n_fields, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? MPDATA_ENOMEM : MPDATA_ECUDA;
+  }
+  *out = h;
+  return MPDATA_OK;
+}
+
+int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* const* gc, const void* g,
+                   const void* r, double dt, int n_steps, const double* gc_scale) {
+  if (!h || n_steps < 1 || !psi_out) return MPDATA_EINVAL;
+  int rc = validate_fields(h, psi_in, gc, g, r);
+  if (rc != MPDATA_OK) return rc;
+  if (!aligned(psi_out, h->esize)) return MPDATA_EINVAL;
+  if (h->stop.load()) return MPDATA_ESTOPPED;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32)
+    return run_advance<float>(h, static_cast<const float*>(psi_in), static_cast<float*>(psi_out), gc,
+                              static_cast<const float*>(g), static_cast<const float*>(r), dt, n_steps, gc_scale);
+  return run_advance<double>(h, static_cast<const double*>(psi_in), static_cast<double*>(psi_out), gc,
+                             static_cast<const double*>(g), static_cast<const double*>(r), dt, n_steps, gc_scale);
+}
+
+int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, const void* r, double dt,
+                int n_steps) {
+  return mpdata_advance(h, psi, psi, gc, g, r, dt, n_steps, nullptr);
+}
+
+int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
+                        void* const* gc_bar) {
+  if (!h || !psi_bar) return MPDATA_EINVAL;
+  int rc = validate_fields(h, psi_n, gc, g, (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B)) ? psi_n : nullptr);
+  if (rc != MPDATA_OK) return rc;
+  if (!aligned(psi_bar, h->esize)) return MPDATA_EINVAL;
+  if (gc_bar)
+    for (int d = 0; d < h->nd; ++d)
+      if (gc_bar[d] && !aligned(gc_bar[d], h->esize)) return MPDATA_EINVAL;
+  if (h->n_fields != 1) return MPDATA_EUNSUPPORTED;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32)
+    return mpd::adjoint_step<float>(h, static_cast<const float*>(psi_n), gc, static_cast<const float*>(g),
+                                    static_cast<float*>(psi_bar), gc_bar);
+  return mpd::adjoint_step<double>(h, static_cast<const double*>(psi_n), gc, static_cast<const double*>(g),
+                                   static_cast<double*>(psi_bar), gc_bar);
+}
+
+int mpdata_reduce(mpdata_t h, const void* psi, const void* g, double* mass_out) {
+  if (!h || !psi || !mass_out) return MPDATA_EINVAL;
+  if (!aligned(psi, h->esize) || (g && !aligned(g, h->esize))) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  cudaError_t e = h->dtype == MPDATA_F32
+                      ? mpd::reduce_mass<float>(static_cast<const float*>(psi), static_cast<const float*>(g),
+                                                h->d_spans, h->n_fields, h->d_partial, h->d_out, h->stream)
+                      : mpd::reduce_mass<double>(static_cast<const double*>(psi), static_cast<const double*>(g),
+                                                 h->d_spans, h->n_fields, h->d_partial, h->d_out, h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double) * h->n_fields, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  int rc = sync_status(h);
+  std::memcpy(mass_out, h->h_out, sizeof(double) * h->n_fields);
+  return rc;
+}
+
+int mpdata_diff_norms(mpdata_t h, const void* a, const void* b, double* l2sq_out, double* linf_out) {
+  if (!h || !a || !b) return MPDATA_EINVAL;
+  if (!aligned(a, h->esize) || !aligned(b, h->esize)) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  cudaError_t e = h->dtype == MPDATA_F32
+                      ? mpd::reduce_diff<float>(static_cast<const float*>(a), static_cast<const float*>(b),
+                                                h->d_spans, h->n_fields, h->d_partial, h->d_out, h->stream)
+                      : mpd::reduce_diff<double>(static_cast<const double*>(a), static_cast<const double*>(b),
+                                                 h->d_spans, h->n_fields, h->d_partial, h->d_out, h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double) * 2 * h->n_fields, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  int rc = sync_status(h);
+  if (l2sq_out) std::memcpy(l2sq_out, h->h_out, sizeof(double) * h->n_fields);
+  if (linf_out) std::memcpy(linf_out, h->h_out + h->n_fields, sizeof(double) * h->n_fields);
+  return rc;
+}
+
+int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, double* max_out) {
+  if (!h || !gc) return MPDATA_EINVAL;
+  for (int d = 0; d < h->nd; ++d)
+    if (!gc[d] || !aligned(gc[d], h->esize)) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  cudaError_t e;
+  if (h->dtype == MPDATA_F32) {
+    const float* p[3] = {static_cast<const float*>(gc[0]), h->nd > 1 ? static_cast<const float*>(gc[1]) : nullptr,
+                         h->nd > 2 ? static_cast<const float*>(gc[2]) : nullptr};
+    e = mpd::reduce_courant<float>(h->grids.data(), h->offsets.data(), h->n_fields, p,
+                                   static_cast<const float*>(g), h->d_partial, h->d_out, h->stream);
+  } else {
+    const double* p[3] = {static_cast<const double*>(gc[0]), h->nd > 1 ? static_cast<const double*>(gc[1]) : nullptr,
+                          h->nd > 2 ? static_cast<const double*>(gc[2]) : nullptr};
+    e = mpd::reduce_courant<double>(h->grids.data(), h->offsets.data(), h->n_fields, p,
+                                    static_cast<const double*>(g), h->d_partial, h->d_out, h->stream);
+  }
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double) * h->n_fields, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return MPDATA_ECUDA;
+  int rc = sync_status(h);
+  if (rc != MPDATA_OK) return rc;
+  double m = 0.0;
+  for (int f = 0; f < h->n_fields; ++f) m = h->h_out[f] > m ? h->h_out[f] : m;
+  if (max_out) *max_out = m;
+  return m > 1.0 ? MPDATA_ECOURANT : MPDATA_OK;
+}
+
+int mpdata_request_stop(mpdata_t h) {
+  if (!h) return MPDATA_EINVAL;
+  h->stop.store(1);
+  return MPDATA_OK;
+}
+
+int mpdata_clear_stop(mpdata_t h) {
+  if (!h) return MPDATA_EINVAL;
+  h->stop.store(0);
+  return MPDATA_OK;
+}
+
+int mpdata_sync(mpdata_t h) {
+  if (!h) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  return sync_status(h);
+}
+
+int mpdata_destroy(mpdata_t h) {
+  if (!h) return MPDATA_EINVAL;
+  {
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+  }
+  delete h;
+  return MPDATA_OK;
+}
+
+const char* mpdata_strerror(int code) {
+  switch (code) {
+    case MPDATA_OK: return "ok";
+    case MPDATA_EINVAL: return "invalid argument";
+    case MPDATA_EUNSUPPORTED: return "unsupported configuration";
+    case MPDATA_ECUDA: return "CUDA runtime error";
+    case MPDATA_ECOURANT: return "Courant condition violated (sum of outflow advectors / G > 1)";
+    case MPDATA_ETIMEOUT: return "bounded device wait timed out";
+    case MPDATA_ESTOPPED: return "stopped on request";
+    case MPDATA_ENOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+const char* mpdata_version(void) { return "mpdata-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mpdata.h"
+
+namespace mpd {
+
+// Grid of one field on three internal axes: dimension d of an nd-dimensional
+// field lives on axis 3 - nd + d; unused leading axes have extent 1.
+struct Grid {
+  int nd;
+  int n[3];
+  long long N;
+};
+
+inline Grid make_grid(int nd, const int64_t* shape) {
+  Grid g;
+  g.nd = nd;
+  g.n[0] = g.n[1] = g.n[2] = 1;
+  g.N = 1;
+  for (int d = 0; d < nd; ++d) {
+    g.n[3 - nd + d] = static_cast<int>(shape[d]);
+    g.N *= shape[d];
+  }
+  return g;
+}
+
+// Run-time options of one step.
+struct Opts {
+  bool fct, tot, iga, nug, kahan, rhs_a, rhs_b, staged;
+  int n_iters;
+};
+
+inline Opts make_opts(uint32_t o, int n_iters) {
+  Opts p;
+  p.fct = o & MPDATA_FCT;
+  p.tot = o & MPDATA_TOT;
+  p.iga = o & MPDATA_IGA;
+  p.nug = o & MPDATA_NUG;
+  p.kahan = o & MPDATA_KAHAN;
+  p.rhs_a = o & MPDATA_RHS_EULER_A;
+  p.rhs_b = o & MPDATA_RHS_EULER_B;
+  p.staged = o & MPDATA_STAGED;
+  p.n_iters = n_iters;
+  return p;
+}
+
+// Pointers of one field for one step.
+template <typename T>
+struct StepArgs {
+  const T* psi_in;
+  T* psi_out;
+  const T* gc[3];
+  const T* g;    // NULL unless nug
+  const T* r;    // NULL unless an rhs bit
+  T dt;
+  T gc_scale;    // advector multiplier of this step
+};
+
+// Scratch of the staged path: 16 arrays of n_max elements.
+template <typename T>
+struct StagedScratch {
+  T* p0;          // psi^(0) when euler_b
+  T* pa;          // psi^(k) ping
+  T* pb;          // psi^(k) pong
+  T* va[3];       // advector ping
+  T* vb[3];       // advector pong
+  T* vu[3];       // unlimited antidiffusive advector (FCT)
+  T* mx;
+  T* mn;
+  T* bu;
+  T* bd;
+};
+constexpr int kStagedArrays = 16;
+
+template <typename T>
+StagedScratch<T> carve_staged(void* base, long long n_max);
+
+// One step of one field with one kernel per sub-step; returns a cudaError_t.
+template <typename T>
+cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a,
+                        const StagedScratch<T>& s, cudaStream_t st);
+
+// FP64 reductions (reduce.cu).  partial: device scratch of at least
+// kRedBlocks * n_fields doubles per output.
+constexpr int kRedBlocks = 256;
+struct FieldSpan {
+  long long offset;
+  long long n;
+};
+template <typename T>
+cudaError_t reduce_mass(const T* psi, const T* g, const FieldSpan* d_spans, int n_fields,
+                        double* d_partial, double* d_out, cudaStream_t st);
+template <typename T>
+cudaError_t reduce_diff(const T* a, const T* b, const FieldSpan* d_spans, int n_fields,
+                        double* d_partial, double* d_out, cudaStream_t st);
+template <typename T>
+cudaError_t reduce_courant(const Grid* grids, const long long* offsets, int n_fields, const T* const* gc,
+                           const T* g, double* d_partial, double* d_out, cudaStream_t st);
+
+}  // namespace mpd

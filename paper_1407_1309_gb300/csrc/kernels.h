@@ -1,0 +1,40 @@
+// Entry points of the kernel families, called by the C ABI (capi.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace mpd {
+
+// accessors of the opaque handle (capi.cu)
+int handle_nd(const mpdata_s* h);
+int handle_fields(const mpdata_s* h);
+const Grid* handle_grids(const mpdata_s* h);
+const long long* handle_offsets(const mpdata_s* h);
+long long handle_total(const mpdata_s* h);
+cudaStream_t handle_stream(const mpdata_s* h);
+int* handle_status(const mpdata_s* h);
+void** handle_batch(mpdata_s* h);
+void** handle_adj(mpdata_s* h);
+int handle_n_iters(const mpdata_s* h);
+uint32_t handle_opts(const mpdata_s* h);
+
+// Fused tile kernel for one field and one step (fused2d.cu).  Returns
+// MPDATA_EUNSUPPORTED when the field / options are not covered, so the caller
+// runs the staged path.  tmp: device buffer of the field's size, used when the
+// step is in place.
+template <typename T>
+int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
+
+// One step of all fields of a batched handle in one persistent launch
+// (batched.cu); MPDATA_EUNSUPPORTED when not covered.
+template <typename T>
+int batched_step(mpdata_s* h, const T* psi_in, T* psi_out, const T* const* gc, const T* g, const T* r, T dt,
+                 T gc_scale, const Opts& o);
+void batched_free(mpdata_s* h);
+
+// Reverse of one step of a single-field handle (adjoint.cu).
+template <typename T>
+int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* psi_bar,
+                 void* const* gc_bar);
+
+}  // namespace mpd

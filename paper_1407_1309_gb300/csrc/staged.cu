@@ -1,0 +1,342 @@
+// Staged MPDATA step: one kernel per sub-step over the whole field, with the
+// intermediates of the step in library-owned device scratch.
+//
+// This path handles every dimension (1-3) and every option combination; the
+// fused tile kernels (fused2d.cu) take over the cases they cover.  It is also
+// the forward recomputation that the adjoint kernels reverse.
+//
+// Sub-steps (paper Sect. 3.1.1, 3.1.2, 3.1.4, 3.1.5, 4.1):
+//   pre      psi0 = psi + dt R                           (euler_b)
+//   donor    psi_k = psi_{k-1} - F_{i+1/2}/G + F_{i-1/2}/G per dimension (Eqs. 4-5)
+//   bounds   FCT extrema of psi0 and psi1 over the cell and its face neighbours
+//   antidiff pseudo-advector of Eq. 6 with multi-D cross and third-order terms
+//   beta     FCT in/out flux sums and limiting factors
+//   limit    limited advector
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace mpd {
+namespace {
+
+template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+// psi-fraction with the zero-denominator guard (the ratio of Eq. 6 is 0 when its sum is 0)
+template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return d != T(0) ? n / d : T(0); }
+
+template <typename T> struct In3 { const T* p[3]; };
+template <typename T> struct Out3 { T* p[3]; };
+
+struct Coord { int c[3]; };
+
+template <int ND>
+__device__ __forceinline__ Coord coord_of(const Grid& g, long long i) {
+  Coord x;
+  x.c[2] = static_cast<int>(i % g.n[2]);
+  long long r = i / g.n[2];
+  x.c[1] = static_cast<int>(r % g.n[1]);
+  x.c[0] = static_cast<int>(r / g.n[1]);
+  return x;
+}
+__device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
+  return (static_cast<long long>(x.c[0]) * g.n[1] + x.c[1]) * g.n[2] + x.c[2];
+}
+// cell x moved by s cells along dimension d (periodic)
+template <int ND>
+__device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
+  const int a = 3 - ND + d;
+  int v = (x.c[a] + s) % g.n[a];
+  if (v < 0) v += g.n[a];
+  x.c[a] = v;
+  return x;
+}
+
+// donor-cell flux of Eq. 5 in advector units; psi -> 1 under infinite gauge
+template <typename T>
+__device__ __forceinline__ T flux(T L, T R, T V, bool unit) {
+  return unit ? V : posp(V) * L + negp(V) * R;
+}
+
+template <typename T>
+__global__ void k_pre(long long N, const T* __restrict__ psi, const T* __restrict__ r, T dt,
+                      T* __restrict__ out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i < N) out[i] = psi[i] + dt * r[i];
+}
+
+// Donor-cell pass (Eqs. 4-5): psi_i - F_{i+1/2}/G_i + F_{i-1/2}/G_i, dimension 0 first,
+// optionally with compensated (Kahan) summation; euler_a source added when post.
+template <typename T, int ND>
+__global__ void k_donor(Grid g, const T* __restrict__ psi, In3<T> V, T vscale, bool unit,
+                        const T* __restrict__ G, bool kahan, const T* __restrict__ R, T dt,
+                        bool post, T* __restrict__ out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= g.N) return;
+  const Coord x = coord_of<ND>(g, i);
+  const T p = psi[i];
+  T s = p, comp = T(0);
+  const T Gi = G ? G[i] : T(1);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const long long im = lin(g, sh<ND>(g, x, d, -1));
+    const T vp = V.p[d][i] * vscale, vm = V.p[d][im] * vscale;
+    const T Fp = flux(p, psi[ip], vp, unit);
+    const T Fm = flux(psi[im], p, vm, unit);
+    const T t0 = G ? -Fp / Gi : -Fp;
+    const T t1 = G ? Fm / Gi : Fm;
+    if (kahan) {
+      T y = t0 - comp;
+      T u = s + y;
+      comp = (u - s) - y;
+      s = u;
+      y = t1 - comp;
+      u = s + y;
+      comp = (u - s) - y;
+      s = u;
+    } else {
+      s = s + t0;
+      s = s + t1;
+    }
+  }
+  if (post) s = s + dt * R[i];
+  out[i] = s;
+}
+
+// FCT bounds (Sect. 3.1.4): extrema of psi0 and psi1 over the cell and its face neighbours.
+template <typename T, int ND>
+__global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__ p1,
+                         T* __restrict__ mx, T* __restrict__ mn) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= g.N) return;
+  const Coord x = coord_of<ND>(g, i);
+  T hi = p0[i] > p1[i] ? p0[i] : p1[i];
+  T lo = p0[i] < p1[i] ? p0[i] : p1[i];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+#pragma unroll
+    for (int s = -1; s <= 1; s += 2) {
+      const long long j = lin(g, sh<ND>(g, x, d, s));
+      const T a = p0[j], b = p1[j];
+      hi = a > hi ? a : hi;
+      hi = b > hi ? b : hi;
+      lo = a < lo ? a : lo;
+      lo = b < lo ? b : lo;
+    }
+  }
+  mx[i] = hi;
+  mn[i] = lo;
+}
+
+// Antidiffusive pseudo-advector of pass k at every face i+1/2 of cell i (Eq. 6 with the
+// multi-D cross terms, Sect. 3.1.1, and the third-order terms, Sect. 3.1.2):
+//   (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q
+//   + tot: Gb(3C|C| - 2C^3 - C)/3 D_dd + sum_q Gb|C|C_q(1 - 2|C|) D_dq - (2/3) Gb C C_q1 C_q2 D_q1q2
+// with C = V/Gb, C_q = Vq/Gb; each psi ratio is a difference over the sum of the psi
+// values it uses (over their count under infinite gauge).
+template <typename T, int ND>
+__global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vscale,
+                           const T* __restrict__ G, bool iga, bool tot, Out3<T> Vout) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= g.N) return;
+  const Coord x = coord_of<ND>(g, i);
+  const T p0 = psi[i];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const Coord xd = sh<ND>(g, x, d, +1);
+    const long long ip = lin(g, xd);
+    const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
+    const T V = Vin.p[d][i] * vscale;
+    const T p1 = psi[ip];
+    const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
+    T out = (absv(V) - V * V / Gb) * A;
+    T Vq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      if (q == d) continue;
+      const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
+      const long long iqp = lin(g, xp), idqp = lin(g, sh<ND>(g, xp, d, +1));
+      const long long iqm = lin(g, xm), idqm = lin(g, sh<ND>(g, xm, d, +1));
+      const T* Q = Vin.p[q];
+      Vq[q] = T(0.25) * ((Q[i] * vscale + Q[ip] * vscale) + (Q[iqm] * vscale + Q[idqm] * vscale));
+      const T Tp = psi[iqp] + psi[idqp];
+      const T Bt = psi[iqm] + psi[idqm];
+      const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
+      out = out - T(0.5) * V * Vq[q] / Gb * B;
+    }
+    if (tot) {
+      const T pm = psi[lin(g, sh<ND>(g, x, d, -1))];
+      const T p2 = psi[lin(g, sh<ND>(g, xd, d, +1))];
+      const T num = ((p2 - p1) - p0) + pm;
+      const T D = iga ? num * T(0.25) : fracg(num, ((p2 + p1) + p0) + pm);
+      out = out + ((T(3) * V * absv(V)) / Gb - (T(2) * V * V * V) / (Gb * Gb) - V) / T(3) * D;
+      int qs[2] = {0, 0}, nq = 0;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) {
+        if (q == d) continue;
+        qs[nq++] = q;
+        const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
+        const T a = psi[lin(g, xp)], b = psi[lin(g, sh<ND>(g, xp, d, +1))];
+        const T e = psi[lin(g, xm)], f = psi[lin(g, sh<ND>(g, xm, d, +1))];
+        const T n2 = (b - a) - (f - e);
+        const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
+        out = out + absv(V) * Vq[q] / Gb * (T(1) - T(2) * absv(V) / Gb) * D2;
+      }
+      if (ND == 3) {
+        T pr[4];
+        int m = 0;
+#pragma unroll
+        for (int s1 = 1; s1 >= -1; s1 -= 2) {
+#pragma unroll
+          for (int s2 = 1; s2 >= -1; s2 -= 2) {
+            const Coord y = sh<ND>(g, sh<ND>(g, x, qs[0], s1), qs[1], s2);
+            pr[m++] = psi[lin(g, y)] + psi[lin(g, sh<ND>(g, y, d, +1))];
+          }
+        }
+        // pr = {(+,+), (+,-), (-,+), (-,-)}
+        const T n3 = (pr[0] - pr[1]) - (pr[2] - pr[3]);
+        const T D3 = iga ? n3 * T(0.125) : fracg(n3, (pr[0] + pr[1]) + (pr[2] + pr[3]));
+        out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] / (Gb * Gb) * D3;
+      }
+    }
+    Vout.p[d][i] = out;
+  }
+}
+
+// FCT limiting factors (Sect. 3.1.4): in/out sums of the unlimited fluxes and
+// beta_up = G [psi_max - psi]+ / in, beta_dn = G [psi - psi_min]+ / out (1 when the sum is 0).
+template <typename T, int ND>
+__global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __restrict__ G, bool unit,
+                       const T* __restrict__ mx, const T* __restrict__ mn, T* __restrict__ bu,
+                       T* __restrict__ bd) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= g.N) return;
+  const Coord x = coord_of<ND>(g, i);
+  const T p = psi[i];
+  T in = T(0), out = T(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const long long im = lin(g, sh<ND>(g, x, d, -1));
+    const T Fp = flux(p, psi[ip], V.p[d][i], unit);
+    const T Fm = flux(psi[im], p, V.p[d][im], unit);
+    in = in + (posp(Fm) - negp(Fp));
+    out = out + (posp(Fp) - negp(Fm));
+  }
+  const T Gi = G ? G[i] : T(1);
+  bu[i] = in > T(0) ? Gi * posp(mx[i] - p) / in : T(1);
+  bd[i] = out > T(0) ? Gi * posp(p - mn[i]) / out : T(1);
+}
+
+// Limited advector: V min(1, beta_dn_i, beta_up_{i+e_d}) if the unlimited flux leaves
+// cell i (F > 0, or F = 0 with V > 0), else V min(1, beta_up_i, beta_dn_{i+e_d}).
+template <typename T, int ND>
+__global__ void k_limit(Grid g, const T* __restrict__ psi, In3<T> Vu, bool unit,
+                        const T* __restrict__ bu, const T* __restrict__ bd, Out3<T> Vout) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i >= g.N) return;
+  const Coord x = coord_of<ND>(g, i);
+  const T p = psi[i];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const T V = Vu.p[d][i];
+    const T F = flux(p, psi[ip], V, unit);
+    const bool right = F > T(0) || (F == T(0) && V > T(0));
+    const T a = right ? bd[i] : bu[i];
+    const T b = right ? bu[ip] : bd[ip];
+    T m = T(1);
+    if (a < m) m = a;
+    if (b < m) m = b;
+    Vout.p[d][i] = V * m;
+  }
+}
+
+template <typename T, int ND>
+cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const StagedScratch<T>& s,
+                      cudaStream_t st) {
+  const int bs = 256;
+  const unsigned nb = static_cast<unsigned>((g.N + bs - 1) / bs);
+  const int K = o.n_iters;
+  const T* G = o.nug ? a.g : nullptr;
+  const T* p0 = a.psi_in;
+  if (o.rhs_b) {
+    k_pre<T><<<nb, bs, 0, st>>>(g.N, a.psi_in, a.r, a.dt, s.p0);
+    p0 = s.p0;
+  }
+  In3<T> gc{{a.gc[0], a.gc[1], a.gc[2]}};
+  // pass 1
+  const bool inplace1 = (a.psi_out == a.psi_in) && !o.rhs_b;
+  T* dst1 = (K == 1 && !inplace1) ? a.psi_out : s.pa;
+  k_donor<T, ND><<<nb, bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
+                                    K == 1 && o.rhs_a, dst1);
+  if (K == 1) {
+    if (dst1 != a.psi_out)
+      return cudaMemcpyAsync(a.psi_out, dst1, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+  }
+  if (o.fct) k_bounds<T, ND><<<nb, bs, 0, st>>>(g, p0, s.pa, s.mx, s.mn);
+  const T* prev = s.pa;
+  In3<T> vprev = gc;
+  T vscale = a.gc_scale;
+  for (int k = 2; k <= K; ++k) {
+    T* const* lim = (k % 2 == 0) ? s.va : s.vb;
+    Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
+    k_antidiff<T, ND><<<nb, bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+    In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
+    if (o.fct) {
+      k_beta<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, G, o.iga, s.mx, s.mn, s.bu, s.bd);
+      Out3<T> vl{{lim[0], lim[1], lim[2]}};
+      k_limit<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, o.iga, s.bu, s.bd, vl);
+      vuse = In3<T>{{lim[0], lim[1], lim[2]}};
+    }
+    T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
+    k_donor<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, T(1), o.iga, G, o.kahan, a.r, a.dt,
+                                      k == K && o.rhs_a, dst);
+    prev = dst;
+    vprev = vuse;
+    vscale = T(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+StagedScratch<T> carve_staged(void* base, long long n_max) {
+  T* p = static_cast<T*>(base);
+  StagedScratch<T> s;
+  auto take = [&]() { T* q = p; p += n_max; return q; };
+  s.p0 = take();
+  s.pa = take();
+  s.pb = take();
+  for (int d = 0; d < 3; ++d) s.va[d] = take();
+  for (int d = 0; d < 3; ++d) s.vb[d] = take();
+  for (int d = 0; d < 3; ++d) s.vu[d] = take();
+  s.mx = take();
+  s.mn = take();
+  s.bu = take();
+  s.bd = take();
+  return s;
+}
+
+template <typename T>
+cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a, const StagedScratch<T>& s,
+                        cudaStream_t st) {
+  switch (g.nd) {
+    case 1: return staged_nd<T, 1>(g, o, a, s, st);
+    case 2: return staged_nd<T, 2>(g, o, a, s, st);
+    case 3: return staged_nd<T, 3>(g, o, a, s, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template StagedScratch<float> carve_staged<float>(void*, long long);
+template StagedScratch<double> carve_staged<double>(void*, long long);
+template cudaError_t staged_step<float>(const Grid&, const Opts&, const StepArgs<float>&,
+                                        const StagedScratch<float>&, cudaStream_t);
+template cudaError_t staged_step<double>(const Grid&, const Opts&, const StepArgs<double>&,
+                                         const StagedScratch<double>&, cudaStream_t);
+
+}  // namespace mpd

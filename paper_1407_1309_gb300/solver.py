@@ -1,0 +1,93 @@
+"""Handle wrapper over the C ABI for torch tensors.
+
+PyTorch provides the device memory and the stream; every step runs in the
+CUDA library through ``capi``.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import capi
+
+_DT = {torch.float32: capi.F32, torch.float64: capi.F64}
+
+
+class Mpdata:
+    """One handle of the library: n_fields fields of one dimensionality.
+
+    shapes: a shape tuple (one field) or a list of shape tuples (a batch of
+    fields held concatenated, field after field).  The handle's stream is the
+    current torch stream of `device` at construction unless one is given.
+    """
+
+    def __init__(self, shapes, dtype=torch.float32, n_iters=2, opts=0, device=None, stream=None):
+        if isinstance(shapes, (tuple, torch.Size)) and all(isinstance(s, int) for s in shapes):
+            shapes = [tuple(shapes)]
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.ndims = len(self.shapes[0])
+        if any(len(s) != self.ndims for s in self.shapes):
+            raise ValueError("all fields of a handle have the same number of dimensions")
+        if dtype not in _DT:
+            raise ValueError("dtype must be torch.float32 or torch.float64")
+        self.dtype = dtype
+        self.n_iters = int(n_iters)
+        self.opts = int(opts)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.h = capi.mpdata_create(self.ndims, self.shapes, _DT[dtype], self.n_iters, self.opts, self.stream)
+        self.sizes = [int(torch.Size(s).numel()) for s in self.shapes]
+        self.total = sum(self.sizes)
+
+    # -- stepping -----------------------------------------------------------------
+    def step(self, psi, gc, g=None, r=None, dt=0.0, n_steps=1):
+        """Advance psi in place by n_steps steps."""
+        capi.mpdata_step(self.h, psi, gc, g, r, dt, n_steps)
+        return psi
+
+    def advance(self, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1, gc_scale=None):
+        capi.mpdata_advance(self.h, psi_in, psi_out, gc, g, r, dt, n_steps, gc_scale)
+        return psi_out
+
+    def adjoint_step(self, psi_n, gc, psi_bar, g=None, gc_bar=None):
+        """psi_bar (in place): dL/dpsi^{n+1} -> dL/dpsi^n; gc_bar[d] += dL/dgc_d."""
+        capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
+        return psi_bar
+
+    # -- FP64 reductions --------------------------------------------------------------
+    def mass(self, psi, g=None):
+        m = capi.mpdata_reduce(self.h, psi, g, len(self.shapes))
+        return m if len(m) > 1 else m[0]
+
+    def diff_norms(self, a, b):
+        l2, li = capi.mpdata_diff_norms(self.h, a, b, len(self.shapes))
+        return (l2, li) if len(l2) > 1 else (l2[0], li[0])
+
+    def check_courant(self, gc, g=None):
+        return capi.mpdata_check_courant(self.h, gc, g)
+
+    def request_stop(self):
+        capi.mpdata_request_stop(self.h)
+
+    def clear_stop(self):
+        capi.mpdata_clear_stop(self.h)
+
+    def sync(self):
+        capi.mpdata_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.mpdata_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

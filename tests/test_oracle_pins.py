@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from paper_1407_1309_gb300 import workloads as wl
+from helpers import nondivergent
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -33,29 +34,6 @@ OPTION_SETS = {
     "iga_tot_fct": (2, oracle.IGA | oracle.TOT | oracle.FCT),
     "kahan_fct": (2, oracle.KAHAN | oracle.FCT),
 }
-
-
-def nondivergent(shape, rng, cmax):
-    """Random discretely nondivergent periodic advector (corner streamfunction in 2D,
-    edge vector potential in 3D, constant in 1D)."""
-    nd = len(shape)
-    if nd == 1:
-        return [np.full(shape, rng.uniform(-cmax, cmax))]
-    if nd == 2:
-        return wl.streamfunction_advector(rng.normal(size=shape), cmax)
-    # 3D: discrete curl of a random edge potential; Ax[i, b, c] is the x-edge from
-    # corner (i, b, c) to (i+1, b, c), likewise Ay[a, j, c], Az[a, b, k]
-    Ax, Ay, Az = (rng.normal(size=shape) for _ in range(3))
-    up = lambda a, d: np.roll(a, -1, axis=d)
-    fx = (up(up(Az, 0), 1) - up(Az, 0)) - (up(up(Ay, 0), 2) - up(Ay, 0))
-    fy = (up(up(Ax, 1), 2) - up(Ax, 1)) - (up(up(Az, 0), 1) - up(Az, 1))
-    fz = (up(up(Ay, 0), 2) - up(Ay, 2)) - (up(up(Ax, 1), 2) - up(Ax, 2))
-    s = cmax / max(np.abs(fx).max(), np.abs(fy).max(), np.abs(fz).max())
-    return [fx * s, fy * s, fz * s]
-
-
-def divergence(gc):
-    return sum(v - np.roll(v, 1, d) for d, v in enumerate(gc))
 
 
 SHAPES = [(37,), (12, 9), (6, 5, 7)]
