@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""MPDATA step throughput on one or more GB300s.
+
+Workload (default): 2D solid-body rotation of a cone, 1024^2 periodic cells,
+G = 1, FCT limiter, two passes, FP32 -- the rotating-cone test of the paper
+(Sect. 3.6) scaled to 1024^2, one revolution = 6434 steps.  A benchmark step
+is one MPDATA time step (all sub-steps fused in one kernel launch).  Inputs are
+resident in HBM when timing starts; the 129 MB L2 is flushed (256 MiB write)
+before every timed step because the 16 MB working set would otherwise stay in
+L2.  Each step is timed with CUDA events on the launching stream; the value is
+cells x steps / summed step time.
+
+  python bench.py [--steps K] [--warmup W] [--dtype f32|f64] [--impl ours|reference]
+  torchrun --nproc-per-node N bench.py --gpus N ...   (independent replicas, weak scaling)
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPDATA Gcell-steps/s & %HBM roofline, FP32 vs FP64 at stated err; adjoint/fwd"
+UNIT = "Gcell-steps/s"
+N_SIDE = 1024
+REV_STEPS = 6434  # steps per revolution of the 1024^2 rotation workload
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=REV_STEPS)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_SIDE, help="side length of the rotation workload")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / staged / e2e / oracle legs")
+    return ap.parse_args()
+
+
+def config(args, extra=None):
+    c = {"workload": f"2d_solid_body_rotation_{args.n}x{args.n}_fct_n_iters2", "grid": [args.n, args.n],
+         "opts": "fct", "n_iters": 2, "G": 1, "boundary": "periodic", "steps_per_revolution": REV_STEPS,
+         "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{args.gpus}"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_from_profiles(dtype):
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, "profiles", f"traffic_fused2d_rotation_{dtype}.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1407_1309_gb300 import capi, workloads
+    from paper_1407_1309_gb300.solver import Mpdata
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    esize = 4 if dtype == torch.float32 else 8
+    n = args.n
+    cells = n * n
+    psi_np, gc_np, _ = workloads.rotation_2d(n, REV_STEPS if n == N_SIDE else None)
+    psi0 = torch.tensor(psi_np, dtype=dtype, device=dev)
+    gc = [torch.tensor(v, dtype=dtype, device=dev) for v in gc_np]
+    a, b = psi0.clone(), torch.empty_like(psi0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    m = Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(K, flush_l2=True):
+        nonlocal a, b
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for e0, e1 in evs:
+            if flush_l2:
+                flush.zero_()
+            e0.record(stream)
+            m.advance(a, b, gc)
+            e1.record(stream)
+            a, b = b, a
+        torch.cuda.synchronize(dev)
+        return sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
+
+    for _ in range(args.warmup):
+        m.advance(a, b, gc)
+        a, b = b, a
+    a.copy_(psi0)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    secs = timed(args.steps)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([secs], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+        dist.barrier()
+    result_after_K = a.double().cpu().numpy()
+    value = cells * args.steps * ws / secs / 1e9
+    ms_per_step = secs / args.steps * 1e3
+
+    peaks, how = measured_peaks()
+    bytes_per_cell = 4 * esize  # read psi, gc0, gc1; write psi
+    achieved = bytes_per_cell * cells / (secs / args.steps) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic_from_profiles(args.dtype),
+                "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs, burst copy)" if how == "measured" else "fallback",
+                "algorithmic_bytes_per_cell_step": bytes_per_cell, "kernel": "k_fused2d"}
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+           "data": "synthetic (seeded rotating-cone workload, no dataset)",
+           "config": config(args, {"wall_s_timed_region_incl_flushes": round(wall, 3)}),
+           "roofline": roofline, "gpu_launches": args.steps, "clocks": clk}
+
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        # accuracy of this run's arithmetic: the same K steps in FP64 on the GPU (FP64 path matches
+        # the FP64 oracle to 1e-12), and 10 steps against the oracle itself
+        with Mpdata((n, n), dtype=torch.float64, n_iters=2, opts=capi.FCT, device=dev) as m64:
+            p64 = torch.tensor(psi_np, dtype=torch.float64, device=dev)
+            g64 = [torch.tensor(v, dtype=torch.float64, device=dev) for v in gc_np]
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            q = torch.empty_like(p64)
+            k64 = min(args.steps, 1000)
+            t0.record(stream)
+            for s in range(args.steps):
+                m64.advance(p64, q, g64)
+                p64, q = q, p64
+                if s + 1 == k64:
+                    t1.record(stream)
+            torch.cuda.synchronize(dev)
+            s64 = t0.elapsed_time(t1) / 1e3
+            ref64 = p64.cpu().numpy()
+        e = result_after_K - ref64
+        extras["err_vs_fp64_gpu_after_K_steps"] = {
+            "rel_l2": float(np.linalg.norm(e) / np.linalg.norm(ref64)),
+            "max_abs": float(np.abs(e).max()),
+            "rel_mass_drift": float(abs(result_after_K.sum() - psi_np.sum()) / abs(psi_np.sum()))}
+        extras["fp64_path"] = {"value": round(cells * k64 / s64 / 1e9, 3), "unit": UNIT, "steps": k64,
+                               "l2": "not flushed (ALU-bound: FP64 arithmetic, not HBM, limits it)",
+                               "bound": "alu_fp64"}
+        try:
+            import oracle
+            oracle.set_threads(0)
+            p32 = psi0.double().cpu().numpy()
+            g32 = [v.double().cpu().numpy() for v in gc]
+            ref = oracle.step(p32, g32, n_iters=2, opts=oracle.FCT, n_steps=10)
+            with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev) as mm:
+                x = psi0.clone()
+                y = torch.empty_like(x)
+                mm.advance(x, y, gc, n_steps=10)
+                got = y.double().cpu().numpy()
+            extras["err_vs_oracle_10_steps"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                                                "max_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
+        except Exception as ex:  # the oracle leg must not sink the bench line
+            extras["err_vs_oracle_10_steps"] = {"error": str(ex)[:200]}
+        # staged path (one kernel per sub-step) for comparison
+        with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT | capi.STAGED, device=dev) as ms:
+            x, y = psi0.clone(), torch.empty_like(psi0)
+            ks = min(args.steps, 300)
+            evs = []
+            for _ in range(ks):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ms.advance(x, y, gc)
+                e1.record(stream)
+                evs.append((e0, e1))
+                x, y = y, x
+            torch.cuda.synchronize(dev)
+            st = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
+            extras["staged_path"] = {"value": round(cells * ks / st / 1e9, 3), "unit": UNIT, "steps": ks,
+                                     "kernels_per_step": 6}
+        out["e2e"] = run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
+        out["cpu_baseline"] = cpu_baseline(psi_np, gc_np)
+        out["extras"] = extras
+    elif not args.no_extras:
+        run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
+    m.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(m, psi_np, gc_np, dtype, dev, stream, K, ws):
+    """Same metric through the public API with host buffers: every step copies its inputs
+    (psi, gc0, gc1) from pinned host memory and reads the result back."""
+    import torch
+    hp = torch.tensor(psi_np, dtype=dtype).pin_memory()
+    hg = [torch.tensor(v, dtype=dtype).pin_memory() for v in gc_np]
+    ho = torch.empty_like(hp).pin_memory()
+    dp = torch.empty(hp.shape, dtype=dtype, device=dev)
+    dq = torch.empty_like(dp)
+    dg = [torch.empty(v.shape, dtype=dtype, device=dev) for v in hg]
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        dp.copy_(hp, non_blocking=True)
+        for d, h in zip(dg, hg):
+            d.copy_(h, non_blocking=True)
+        m.advance(dp, dq, dg)
+        ho.copy_(dq, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    secs = e0.elapsed_time(e1) / 1e3
+    cells = hp.numel()
+    es = hp.element_size()
+    return {"value": round(cells * K * ws / secs / 1e9, 4), "unit": UNIT, "steps": K,
+            "h2d_bytes_per_step": 3 * cells * es, "d2h_bytes_per_step": cells * es}
+
+
+def cpu_baseline(psi_np, gc_np, budget_s=12.0):
+    """The oracle as it stands on this host's cores, on a bounded sample of the workload."""
+    import oracle
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=1)
+    one = time.perf_counter() - t0
+    k = max(1, min(40, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=k)
+    secs = time.perf_counter() - t0
+    cells = psi_np.size
+    return {"value": round(cells * k / secs / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} steps of the full {psi_np.shape[0]}x{psi_np.shape[1]} workload, FP64, OpenMP over rows"}
+
+
+# ----------------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU MPDATA) on the host cores: each timed step advances a
+    bounded sample of the workload (a 128x128 periodic sub-grid cut from the rotation
+    field) by one MPDATA step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1407_1309_gb300 import workloads
+    psi_np, gc_np, _ = workloads.rotation_2d(args.n, REV_STEPS if args.n == N_SIDE else None)
+    c = args.n // 2
+    sl = (slice(c - 64, c + 64), slice(c + args.n // 4 - 64, c + args.n // 4 + 64))
+    psi = np.ascontiguousarray(psi_np[sl])
+    gc = [np.ascontiguousarray(v[sl]) for v in gc_np]
+    cores = oracle.set_threads(0)
+    for _ in range(args.warmup):
+        psi = oracle.step(psi, gc, n_iters=2, opts=oracle.FCT)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = oracle.step(psi, gc, n_iters=2, opts=oracle.FCT)
+    secs = time.perf_counter() - t0
+    value = psi.size * args.steps / secs / 1e9
+    sample = "one MPDATA step of a 128x128 periodic sub-grid (cone region) of the rotation workload per timed step"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded rotating-cone workload, no dataset)", "config": config(args),
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 6), "unit": UNIT},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

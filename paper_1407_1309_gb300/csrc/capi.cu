@@ -54,14 +54,26 @@ int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv
   const T* gc[3] = {static_cast<const T*>(gcv[0]), h->nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
                     h->nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
   const mpd::StagedScratch<T> ss = mpd::carve_staged<T>(h->staged, h->n_max);
+  // Every step reads one buffer and writes another: the result alternates between
+  // psi_out and the handle's ping-pong buffer so that the last step lands in psi_out.
+  // In place with an odd step count, psi is first copied to the ping-pong buffer.
+  T* X = psi_out;
+  T* P = static_cast<T*>(h->pingpong);
+  const T* cur = psi_in;
+  if (psi_in == psi_out && n_steps % 2 == 1) {
+    if (cudaMemcpyAsync(P, X, sizeof(T) * h->total, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    cur = P;
+  }
   for (int s = 0; s < n_steps; ++s) {
     if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
     const T scale = gc_scale ? static_cast<T>(gc_scale[s]) : T(1);
-    const T* src = (s == 0) ? psi_in : psi_out;
+    T* dst = ((n_steps - 1 - s) % 2 == 0) ? X : P;
     if (h->n_fields > 1 && !o.staged) {
-      int rc = mpd::batched_step<T>(h, src, psi_out, gc, g, r, static_cast<T>(dt), scale, o);
+      int rc = mpd::batched_step<T>(h, cur, dst, gc, g, r, static_cast<T>(dt), scale, o);
       if (rc != MPDATA_EUNSUPPORTED) {
         if (rc != MPDATA_OK) return rc;
+        cur = dst;
         continue;
       }
     }
@@ -69,18 +81,18 @@ int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv
       const long long off = h->offsets[f];
       const mpd::Grid& gr = h->grids[f];
       mpd::StepArgs<T> a;
-      a.psi_in = src + off;
-      a.psi_out = psi_out + off;
+      a.psi_in = cur + off;
+      a.psi_out = dst + off;
       for (int d = 0; d < 3; ++d) a.gc[d] = (d < h->nd) ? gc[d] + off : nullptr;
       a.g = g ? g + off : nullptr;
       a.r = r ? r + off : nullptr;
       a.dt = static_cast<T>(dt);
       a.gc_scale = scale;
-      int rc = o.staged ? MPDATA_EUNSUPPORTED
-                        : mpd::fused_step<T>(gr, o, a, static_cast<T*>(h->pingpong) + off, h->stream);
+      int rc = o.staged ? MPDATA_EUNSUPPORTED : mpd::fused_step<T>(gr, o, a, nullptr, h->stream);
       if (rc == MPDATA_EUNSUPPORTED) rc = cuda_status(mpd::staged_step<T>(gr, o, a, ss, h->stream));
       if (rc != MPDATA_OK) return rc;
     }
+    cur = dst;
   }
   return cuda_status(cudaGetLastError());
 }
