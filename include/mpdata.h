@@ -153,6 +153,36 @@ int mpdata_sync(mpdata_t h);
 /* Destroys the handle and frees its scratch (after synchronising its stream). */
 int mpdata_destroy(mpdata_t h);
 
+/*
+ * Allocation-free step.  The paper has no counterpart: this entry point exists
+ * for callers that may not allocate device memory when they advance a field --
+ * hosts that give the library a fixed memory budget and forbid allocations after
+ * start-up (another allocator owns the device memory), or latency-critical loops
+ * that cannot afford cudaMalloc / cudaFree, which may synchronise the device.
+ * Such callers cannot create a handle, because mpdata_create allocates scratch.
+ *
+ * Advances one field (shape (host): ndims extents) by ONE step on the staged
+ * kernels, reading psi_in and writing psi_out (the same buffer is allowed),
+ * with the same option bits, pointers and alignment rules as mpdata_advance
+ * (gc: host array of ndims device pointers; g iff MPDATA_NUG; r iff an RHS bit);
+ * cuda_stream is a cudaStream_t or NULL.  It calls no allocating routine: the
+ * scratch of the sub-steps lives in one static device array of
+ * MPDATA_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
+ * holds until the process exits.  A field needs 16 arrays of its size there, so
+ * at most 262144 cells in FP32 and 131072 cells in FP64; larger fields (or any
+ * other invalid argument) return MPDATA_EINVAL without launching anything.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make that
+ * first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (nothing in it needs to start at zero); calls whose
+ * work overlaps on the GPU race on it, so serialise them.  Returns MPDATA_OK,
+ * MPDATA_EINVAL, MPDATA_EUNSUPPORTED (device index >= 64) or MPDATA_ECUDA.
+ */
+#define MPDATA_NOALLOC_SCRATCH_BYTES (16u << 20)
+int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, int n_iters, uint32_t opts,
+                        const void* psi_in, void* psi_out, const void* const* gc, const void* g,
+                        const void* r, double dt, void* cuda_stream);
+
 /* Static description of a status code. */
 const char* mpdata_strerror(int code);
 

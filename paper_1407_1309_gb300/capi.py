@@ -207,3 +207,23 @@ def mpdata_sync(h, *, raw=False):
 
 def mpdata_destroy(h):
     _check(load().mpdata_destroy(h), "mpdata_destroy")
+
+
+def mpdata_step_noalloc(ndims, shape, dtype, n_iters, opts, psi_in, psi_out, gc, g=None, r=None, dt=0.0,
+                        stream=None, *, raw=False):
+    """One step of one field without a handle and without any device allocation (the scratch is a
+    static device array inside the library); for callers that may not allocate device memory.
+    Returns the status code when raw=True, else raises on error."""
+    lib = load()
+    fn = lib.mpdata_step_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    shp = (ctypes.c_int64 * max(1, len(shape)))(*[int(v) for v in shape])
+    gcp, _keep = _ptr_array(gc)
+    rc = fn(int(ndims), shp, int(dtype), int(n_iters), int(opts), _ptr(psi_in), _ptr(psi_out), gcp, _ptr(g),
+            _ptr(r), float(dt), _stream_ptr(stream))
+    if raw:
+        return rc
+    _check(rc, "mpdata_step_noalloc")
