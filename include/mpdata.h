@@ -147,6 +147,15 @@ int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, doubl
 int mpdata_request_stop(mpdata_t h);
 int mpdata_clear_stop(mpdata_t h);
 
+/*
+ * Tuning knobs of the handle's kernels (set by the autotuner; no counterpart in
+ * the paper, whose tiling is the thread decomposition over dimension 0).
+ * MPDATA_TUNE_TILE_ROWS: rows each warp of the fused 2D kernel walks down
+ * (0 = automatic; otherwise 4..256).  Returns EINVAL for an unknown knob or value.
+ */
+enum { MPDATA_TUNE_TILE_ROWS = 1 };
+int mpdata_tune(mpdata_t h, int knob, int value);
+
 /* Waits for the handle's stream and returns the first pending device error, if any. */
 int mpdata_sync(mpdata_t h);
 

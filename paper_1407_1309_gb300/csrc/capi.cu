@@ -29,6 +29,7 @@ struct mpdata_s {
   double* h_out = nullptr;           // pinned, 2 * n_fields
   int* d_status = nullptr;           // device-side error word (bounded waits)
   void* batch = nullptr;             // batched-kernel tables
+  int tile_rows = 0;                 // MPDATA_TUNE_TILE_ROWS
   std::atomic<int> stop{0};
 };
 
@@ -50,7 +51,8 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 template <typename T>
 int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv, const T* g, const T* r,
                 double dt, int n_steps, const double* gc_scale) {
-  const mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
+  mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
+  o.tile_rows = h->tile_rows;
   const T* gc[3] = {static_cast<const T*>(gcv[0]), h->nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
                     h->nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
   const mpd::StagedScratch<T> ss = mpd::carve_staged<T>(h->staged, h->n_max);
@@ -303,6 +305,16 @@ int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, doubl
   for (int f = 0; f < h->n_fields; ++f) m = h->h_out[f] > m ? h->h_out[f] : m;
   if (max_out) *max_out = m;
   return m > 1.0 ? MPDATA_ECOURANT : MPDATA_OK;
+}
+
+int mpdata_tune(mpdata_t h, int knob, int value) {
+  if (!h) return MPDATA_EINVAL;
+  if (knob == MPDATA_TUNE_TILE_ROWS) {
+    if (value != 0 && (value < 4 || value > 256)) return MPDATA_EINVAL;
+    h->tile_rows = value;
+    return MPDATA_OK;
+  }
+  return MPDATA_EINVAL;
 }
 
 int mpdata_request_stop(mpdata_t h) {

@@ -4,34 +4,39 @@
 // intermediate written to global memory.  Covers 2D fields with n_iters = 2 and
 // every option except the third-order terms (those run on the staged path).
 //
-// Work decomposition ("warp march"): a warp owns a strip of 64 columns (two per
-// lane) and walks down TY rows.  Vertical neighbours stay in per-thread register
-// windows (one row of each quantity per iteration), horizontal neighbours are
-// exchanged with warp shuffles.  A step's stencil reaches 3 cells (two passes
-// plus the limiter), so each strip recomputes a 3-column halo on both sides and
-// stores the 56 columns in its middle; the strips' starts are 4 columns left of
-// their first output so every lane's pair of columns is 8/16-byte aligned.
-// Input rows are prefetched kPF rows ahead into a per-warp shared-memory ring
-// with cp.async (each lane copies and later reads only its own two elements).
+// Work decomposition ("warp march"): a warp owns a strip of 32*NC columns (NC
+// adjacent columns per lane) and walks down TY rows.  Vertical neighbours stay
+// in per-thread register windows (one row of each quantity per iteration),
+// horizontal neighbours inside a lane are registers and across lanes come from
+// warp shuffles.  A step's stencil reaches 3 cells (two passes plus the
+// limiter), so each strip recomputes a 3-column halo on both sides and stores
+// the 32*NC - 8 columns in its middle; strips start 4 columns left of their
+// first output, so every lane's NC columns are aligned and the copies are
+// vectorised.  Input rows are prefetched kPF rows ahead into a per-warp
+// shared-memory ring with cp.async (each lane copies and later reads only its
+// own elements, so no barrier is involved).
 //
 // Row lags at iteration t (row x = R0 - 3 + t loaded):
 //   pass 1 at row x-1; bounds, pseudo-advectors, unlimited fluxes and limiting
 //   factors at row x-2; limited fluxes and pass 2 at row x-3 (stored).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace mpd {
 namespace {
 
-constexpr int kCols = 64;    // columns computed per warp
-constexpr int kStride = 56;  // output columns per strip
 constexpr int kLead = 4;     // computed columns left of the strip's first output column
 constexpr int kPF = 4;       // rows in flight
 constexpr int kSlots = kPF + 1;
 constexpr int kArr = 5;      // psi, gc0, gc1, G, R
 constexpr int kWarps = 4;    // warps per block
 constexpr unsigned kFull = 0xffffffffu;
+
+template <int NC> constexpr int cols() { return 32 * NC; }
+template <int NC> constexpr int stride() { return 32 * NC - 2 * kLead; }
 
 template <typename T>
 struct F2Params {
@@ -43,7 +48,7 @@ struct F2Params {
   const T* R;
   int n0, n1, strips, rowtiles, ty;
   T dt, scale;
-  int iga, kahan, rhs_a, rhs_b, vec;
+  int rhs_a, rhs_b, vec;
 };
 
 __device__ __forceinline__ int wrapi(int c, int n) {
@@ -60,14 +65,13 @@ template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ?
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
 template <typename T> __device__ __forceinline__ T maxv(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T minv(T a, T b) { return a < b ? a : b; }
-// donor-cell flux (Eq. 5) in advector units
-template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return posp(V) * L + negp(V) * R; }
+// min(1, x); a NaN x gives 1 (fmin returns the non-NaN operand)
+__device__ __forceinline__ float min1(float x) { return fminf(1.0f, x); }
+__device__ __forceinline__ double min1(double x) { return fmin(1.0, x); }
+// donor-cell flux (Eq. 5) in advector units: [V]+ L + [V]- R, one term of which is zero
+template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return V * (V > T(0) ? L : R); }
 // psi-fraction of Eq. 6 with the zero-denominator guard
 template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return d != T(0) ? fdiv(n, d) : T(0); }
-
-// value of the column left of this lane's first column / right of its second
-template <typename T> __device__ __forceinline__ T from_left(const T (&a)[2]) { return __shfl_up_sync(kFull, a[1], 1); }
-template <typename T> __device__ __forceinline__ T from_right(const T (&a)[2]) { return __shfl_down_sync(kFull, a[0], 1); }
 
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
@@ -79,16 +83,6 @@ template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T>
-__device__ __forceinline__ void copy_pair(T* dst, const T* row, int c0, int c1, bool vec) {
-  if (vec) {
-    cp_async<2 * sizeof(T)>(dst, row + c0);
-  } else {
-    cp_async<sizeof(T)>(dst, row + c0);
-    cp_async<sizeof(T)>(dst + 1, row + c1);
-  }
-}
-
-template <typename T>
 __device__ __forceinline__ void kahan_add(T& s, T& comp, T t) {
   const T y = t - comp;
   const T u = s + y;
@@ -96,16 +90,19 @@ __device__ __forceinline__ void kahan_add(T& s, T& comp, T t) {
   s = u;
 }
 
-// donor-cell sum psi - Fp0/G + Fm0/G - Fp1/G + Fm1/G (dimension 0 first), rG = 1/G
-template <typename T, bool NUG>
-__device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG, bool kahan) {
-  if (NUG) {
-    Fp0 *= rG;
-    Fm0 *= rG;
-    Fp1 *= rG;
-    Fm1 *= rG;
-  }
-  if (kahan) {
+// Donor-cell update of Eq. 4 from the four face fluxes, rG = 1/G.  The flux
+// differences are added first and psi last, so only one rounding happens at the
+// scale of psi; with the Kahan option the terms psi - Fp0 + Fm0 - Fp1 + Fm1 are
+// summed in that order with compensation instead.
+template <typename T, bool NUG, bool KAHAN>
+__device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG) {
+  if (KAHAN) {
+    if (NUG) {
+      Fp0 *= rG;
+      Fm0 *= rG;
+      Fp1 *= rG;
+      Fm1 *= rG;
+    }
     T s = p, comp = T(0);
     kahan_add(s, comp, -Fp0);
     kahan_add(s, comp, Fm0);
@@ -113,266 +110,345 @@ __device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG, bool k
     kahan_add(s, comp, Fm1);
     return s;
   }
-  return (((p - Fp0) + Fm0) - Fp1) + Fm1;
+  const T div = (Fm0 - Fp0) + (Fm1 - Fp1);
+  return NUG ? p + div * rG : p + div;
 }
 
-template <typename T, bool FCT, bool NUG>
+// A row of NC columns held by one lane; the columns just outside come from the
+// neighbouring lanes.
+template <typename T, int NC> __device__ __forceinline__ T from_left(const T (&a)[NC]) {
+  return __shfl_up_sync(kFull, a[NC - 1], 1);
+}
+template <typename T, int NC> __device__ __forceinline__ T from_right(const T (&a)[NC]) {
+  return __shfl_down_sync(kFull, a[0], 1);
+}
+template <typename T, int NC> __device__ __forceinline__ T left_of(const T (&a)[NC], int c, T aL) {
+  return c == 0 ? aL : a[c > 0 ? c - 1 : 0];
+}
+template <typename T, int NC> __device__ __forceinline__ T right_of(const T (&a)[NC], int c, T aR) {
+  return c == NC - 1 ? aR : a[c < NC - 1 ? c + 1 : NC - 1];
+}
+template <typename T, int N> __device__ __forceinline__ void copy_row(T (&d)[N], const T (&s)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) d[c] = s[c];
+}
+
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
+  constexpr int kCols = cols<NC>();
+  constexpr int kStride = stride<NC>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long wid = static_cast<long long>(blockIdx.x) * kWarps + wib;
   if (wid >= static_cast<long long>(p.strips) * p.rowtiles) return;  // whole warp
   const int strip = static_cast<int>(wid % p.strips);
   const int R0 = static_cast<int>(wid / p.strips) * p.ty;
-  const int lc0 = 2 * lane;
+  const int lc0 = NC * lane;
   const int cs = strip * kStride - kLead;
-  const int c0 = wrapi(cs + lc0, p.n1), c1 = wrapi(cs + lc0 + 1, p.n1);
-  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * kCols;
+  int col[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) col[c] = wrapi(cs + lc0 + c, p.n1);
+  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * kCols + lc0;
   const int nt = p.ty + 6;
+  const T* src[kArr] = {p.psi, p.gc0, p.gc1, NUG ? p.G : nullptr, p.rhs_b ? p.R : nullptr};
+  // prefetch cursor: next row to copy, its element offset and ring slot
+  int pf_t = 0, pf_row = wrapi(R0 - 3, p.n0), pf_slot = 0;
+  long long pf_off = static_cast<long long>(pf_row) * p.n1;
 
-  auto issue = [&](int t) {
-    if (t < nt) {
-      const long long base = static_cast<long long>(wrapi(R0 - 3 + t, p.n0)) * p.n1;
-      T* slot = ring + (t % kSlots) * kArr * kCols + lc0;
-      copy_pair(slot, p.psi + base, c0, c1, p.vec);
-      copy_pair(slot + kCols, p.gc0 + base, c0, c1, p.vec);
-      copy_pair(slot + 2 * kCols, p.gc1 + base, c0, c1, p.vec);
-      if (NUG) copy_pair(slot + 3 * kCols, p.G + base, c0, c1, p.vec);
-      if (p.rhs_b) copy_pair(slot + 4 * kCols, p.R + base, c0, c1, p.vec);
+  auto issue = [&]() {
+    if (pf_t < nt) {
+      T* slot = ring + pf_slot * kArr * kCols;
+#pragma unroll
+      for (int a = 0; a < kArr; ++a) {
+        if (a == 3 && !NUG) continue;
+        if (a == 4 && !p.rhs_b) continue;
+        const T* q = src[a] + pf_off;
+        if (p.vec) {
+          constexpr int bytes = NC * static_cast<int>(sizeof(T));
+          if constexpr (bytes <= 16) {
+            cp_async<bytes>(slot + a * kCols, q + col[0]);
+          } else {
+            constexpr int per = 16 / static_cast<int>(sizeof(T));
+#pragma unroll
+            for (int h = 0; h < bytes / 16; ++h) cp_async<16>(slot + a * kCols + h * per, q + col[0] + h * per);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) cp_async<sizeof(T)>(slot + a * kCols + c, q + col[c]);
+        }
+      }
+      ++pf_t;
+      pf_slot = pf_slot + 1 == kSlots ? 0 : pf_slot + 1;
+      pf_row = pf_row + 1 == p.n0 ? 0 : pf_row + 1;
+      pf_off = static_cast<long long>(pf_row) * p.n1;
     }
     cp_commit();
   };
 #pragma unroll
-  for (int t = 0; t < kPF; ++t) issue(t);
+  for (int t = 0; t < kPF; ++t) issue();
+  int rd_slot = 0;
 
   // register windows, [row][column of the lane]; row 0 is the oldest
-  T ps[4][2], v0[3][2], v1[3][2], gg[4][2];
-  T p1[4][2], p1r[3];
-  T hi[3][2], lo[3][2];
-  T pv0[2][2], f0c[2];
-  T a0[2][2], u0[2][2], a1[2][2], u1[2][2], bu[2][2], bd[2][2], h0c[2];
+  T ps[4][NC], v0[3][NC], v1[3][NC], gg[4][NC];
+  T p1[4][NC], p1r[3];
+  T hi[3][NC], lo[3][NC];
+  T pv0[2][NC], f0c[NC];
+  T a0[2][NC], u0[2][NC], a1[2][NC], u1[2][NC], bu[2][NC], bd[2][NC], h0c[NC];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < NC; ++c) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) { ps[k][c] = T(0); gg[k][c] = T(1); p1[k][c] = T(0); }
 #pragma unroll
     for (int k = 0; k < 3; ++k) { v0[k][c] = v1[k][c] = hi[k][c] = lo[k][c] = T(0); }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) { pv0[k][c] = a0[k][c] = u0[k][c] = a1[k][c] = u1[k][c] = T(0); bu[k][c] = bd[k][c] = T(1); }
+    for (int k = 0; k < 2; ++k) {
+      pv0[k][c] = a0[k][c] = u0[k][c] = a1[k][c] = u1[k][c] = T(0);
+      bu[k][c] = bd[k][c] = T(1);
+    }
     f0c[c] = h0c[c] = T(0);
   }
   p1r[0] = p1r[1] = p1r[2] = T(0);
-  const bool iga = p.iga, kahan = p.kahan;
 
-  for (int t = 0; t < nt; ++t) {
+  // One iteration of the march: load row x = R0 - 3 + t and advance every stage by one
+  // row.  In the six ramp iterations (steady = false) a stage only runs once the rows it
+  // reads exist; afterwards every stage runs every iteration.
+  auto body = [&](const int t, auto steady) {
+    constexpr bool S = decltype(steady)::value;
     // ---- load row x = R0 - 3 + t
     cp_wait<kPF - 1>();
     {
-      const T* slot = ring + (t % kSlots) * kArr * kCols + lc0;
+      const T* slot = ring + rd_slot * kArr * kCols;
+      rd_slot = rd_slot + 1 == kSlots ? 0 : rd_slot + 1;
+      copy_row(ps[0], ps[1]); copy_row(ps[1], ps[2]); copy_row(ps[2], ps[3]);
+      copy_row(v0[0], v0[1]); copy_row(v0[1], v0[2]);
+      copy_row(v1[0], v1[1]); copy_row(v1[1], v1[2]);
+      if (NUG) { copy_row(gg[0], gg[1]); copy_row(gg[1], gg[2]); copy_row(gg[2], gg[3]); }
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        ps[0][c] = ps[1][c]; ps[1][c] = ps[2][c]; ps[2][c] = ps[3][c];
-        v0[0][c] = v0[1][c]; v0[1][c] = v0[2][c];
-        v1[0][c] = v1[1][c]; v1[1][c] = v1[2][c];
+      for (int c = 0; c < NC; ++c) {
         T x = slot[c];
         if (p.rhs_b) x = x + p.dt * slot[4 * kCols + c];
         ps[3][c] = x;
         v0[2][c] = slot[kCols + c] * p.scale;
         v1[2][c] = slot[2 * kCols + c] * p.scale;
-        if (NUG) { gg[0][c] = gg[1][c]; gg[1][c] = gg[2][c]; gg[2][c] = gg[3][c]; gg[3][c] = slot[3 * kCols + c]; }
+        if (NUG) gg[3][c] = slot[3 * kCols + c];
       }
     }
-    issue(t + kPF);
+    issue();
 
     // ---- pass 1 (Eqs. 4-5) at row r = x-1
-    T fnew[2];
+    T fnew[NC];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) fnew[c] = flux(ps[2][c], ps[3][c], v0[1][c]);  // face (x-1)+1/2
-    if (t >= 2) {
+    for (int c = 0; c < NC; ++c) fnew[c] = flux(ps[2][c], ps[3][c], v0[1][c]);  // face (x-1)+1/2
+    if (S || t >= 2) {
       const T psR = from_right(ps[2]);
-      T F1[2];
-      F1[0] = flux(ps[2][0], ps[2][1], v1[1][0]);
-      F1[1] = flux(ps[2][1], psR, v1[1][1]);
+      T F1[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) F1[c] = flux(ps[2][c], right_of(ps[2], c, psR), v1[1][c]);
       const T F1L = from_left(F1);
-      T np1[2];
+      T np1[NC];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < NC; ++c) {
         const T rG = NUG ? fdiv(T(1), gg[2][c]) : T(1);
-        np1[c] = donor<T, NUG>(ps[2][c], fnew[c], f0c[c], F1[c], c == 0 ? F1L : F1[0], rG, kahan);
+        np1[c] = donor<T, NUG, KAHAN>(ps[2][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG);
       }
+      copy_row(p1[0], p1[1]); copy_row(p1[1], p1[2]); copy_row(p1[2], p1[3]); copy_row(p1[3], np1);
+      if (FCT) {
+        copy_row(hi[0], hi[1]); copy_row(hi[1], hi[2]);
+        copy_row(lo[0], lo[1]); copy_row(lo[1], lo[2]);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        p1[0][c] = p1[1][c]; p1[1][c] = p1[2][c]; p1[2][c] = p1[3][c]; p1[3][c] = np1[c];
-        if (FCT) {
-          hi[0][c] = hi[1][c]; hi[1][c] = hi[2][c]; hi[2][c] = maxv(ps[2][c], np1[c]);
-          lo[0][c] = lo[1][c]; lo[1][c] = lo[2][c]; lo[2][c] = minv(ps[2][c], np1[c]);
-        }
+        for (int c = 0; c < NC; ++c) { hi[2][c] = maxv(ps[2][c], np1[c]); lo[2][c] = minv(ps[2][c], np1[c]); }
       }
       p1r[0] = p1r[1]; p1r[1] = p1r[2]; p1r[2] = from_right(p1[3]);
     }
-    f0c[0] = fnew[0];
-    f0c[1] = fnew[1];
+    copy_row(f0c, fnew);
 
     // ---- row r = x-2: pseudo-advectors (Eq. 6 + cross term), unlimited fluxes, FCT factors
-    if (t >= 3) {
+    if (S || t >= 3) {
       // dimension-0 faces between rows r and r+1
       const T v0R = from_right(v0[0]);
-      T S0[2], PV1[2];
+      T S0[NC], PV1[NC];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) { S0[c] = p1[2][c] + p1[3][c]; PV1[c] = v1[0][c] + v1[1][c]; }
+      for (int c = 0; c < NC; ++c) { S0[c] = p1[2][c] + p1[3][c]; PV1[c] = v1[0][c] + v1[1][c]; }
       const T S0L = from_left(S0), S0R = from_right(S0), PV1L = from_left(PV1);
-      T na0[2], nu0[2];
+      T na0[NC], nu0[NC], npv[NC];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < NC; ++c) {
         const T V = v0[0][c];
         const T Gb = NUG ? T(0.5) * (gg[1][c] + gg[2][c]) : T(1);
         const T d = p1[3][c] - p1[2][c];
-        const T A = iga ? d * T(0.5) : ratio(d, S0[c]);
-        const T Tt = c == 0 ? S0[1] : S0R, Bt = c == 0 ? S0L : S0[0];
-        const T B = iga ? (Tt - Bt) * T(0.25) : ratio(Tt - Bt, Tt + Bt);
-        const T Vq = T(0.25) * (PV1[c] + (c == 0 ? PV1L : PV1[0]));
+        const T A = IGA ? d * T(0.5) : ratio(d, S0[c]);
+        const T Tt = right_of(S0, c, S0R), Bt = left_of(S0, c, S0L);
+        const T B = IGA ? (Tt - Bt) * T(0.25) : ratio(Tt - Bt, Tt + Bt);
+        const T Vq = T(0.25) * (PV1[c] + left_of(PV1, c, PV1L));
         const T rGb = NUG ? fdiv(T(1), Gb) : T(1);
         const T out = (absv(V) - V * V * rGb) * A - T(0.5) * V * Vq * rGb * B;
         na0[c] = out;
-        nu0[c] = iga ? out : flux(p1[2][c], p1[3][c], out);
+        nu0[c] = IGA ? out : flux(p1[2][c], p1[3][c], out);
+        npv[c] = v0[0][c] + right_of(v0[0], c, v0R);
       }
-      T npv[2] = {v0[0][0] + v0[0][1], v0[0][1] + v0R};
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        pv0[0][c] = pv0[1][c]; pv0[1][c] = npv[c];
-        a0[0][c] = a0[1][c]; a0[1][c] = na0[c];
-        u0[0][c] = u0[1][c]; u0[1][c] = nu0[c];
-      }
+      copy_row(pv0[0], pv0[1]); copy_row(pv0[1], npv);
+      copy_row(a0[0], a0[1]); copy_row(a0[1], na0);
+      copy_row(u0[0], u0[1]); copy_row(u0[1], nu0);
     }
-    if (t >= 4) {
-      // dimension-1 faces (r, j+1/2)
-      T Sm[2], Sc[2], Sp[2];
-      Sm[0] = p1[1][0] + p1[1][1]; Sm[1] = p1[1][1] + p1r[0];
-      Sc[0] = p1[2][0] + p1[2][1]; Sc[1] = p1[2][1] + p1r[1];
-      Sp[0] = p1[3][0] + p1[3][1]; Sp[1] = p1[3][1] + p1r[2];
-      const T gR = NUG ? from_right(gg[1]) : T(1);
-      T na1[2], nu1[2];
+    if (S || t >= 4) {
+      // dimension-1 faces (r, j+1/2); S1 = psi1_j + psi1_{j+1} on rows r-1, r, r+1
+      T Sm[NC], Sc[NC], Sp[NC];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < NC; ++c) {
+        Sm[c] = p1[1][c] + right_of(p1[1], c, p1r[0]);
+        Sc[c] = p1[2][c] + right_of(p1[2], c, p1r[1]);
+        Sp[c] = p1[3][c] + right_of(p1[3], c, p1r[2]);
+      }
+      const T gR = NUG ? from_right(gg[1]) : T(1);
+      T na1[NC], nu1[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
         const T V = v1[0][c];
-        const T Gb = NUG ? T(0.5) * (gg[1][c] + (c == 0 ? gg[1][1] : gR)) : T(1);
-        const T q0 = p1[2][c], q1 = c == 0 ? p1[2][1] : p1r[1];
-        const T A = iga ? (q1 - q0) * T(0.5) : ratio(q1 - q0, Sc[c]);
-        const T B = iga ? (Sp[c] - Sm[c]) * T(0.25) : ratio(Sp[c] - Sm[c], Sp[c] + Sm[c]);
+        const T Gb = NUG ? T(0.5) * (gg[1][c] + right_of(gg[1], c, gR)) : T(1);
+        const T q0 = p1[2][c], q1 = right_of(p1[2], c, p1r[1]);
+        const T A = IGA ? (q1 - q0) * T(0.5) : ratio(q1 - q0, Sc[c]);
+        const T B = IGA ? (Sp[c] - Sm[c]) * T(0.25) : ratio(Sp[c] - Sm[c], Sp[c] + Sm[c]);
         const T Vq = T(0.25) * (pv0[1][c] + pv0[0][c]);
         const T rGb = NUG ? fdiv(T(1), Gb) : T(1);
         const T out = (absv(V) - V * V * rGb) * A - T(0.5) * V * Vq * rGb * B;
         na1[c] = out;
-        nu1[c] = iga ? out : flux(q0, q1, out);
+        nu1[c] = IGA ? out : flux(q0, q1, out);
       }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        a1[0][c] = a1[1][c]; a1[1][c] = na1[c];
-        u1[0][c] = u1[1][c]; u1[1][c] = nu1[c];
-      }
+      copy_row(a1[0], a1[1]); copy_row(a1[1], na1);
+      copy_row(u1[0], u1[1]); copy_row(u1[1], nu1);
       if (FCT) {
         // bounds (extrema of psi^n and psi^(1) over the cell and its face neighbours)
         const T hL = from_left(hi[1]), hR = from_right(hi[1]);
         const T lL = from_left(lo[1]), lR = from_right(lo[1]);
         const T u1L = from_left(u1[1]);
-        T nbu[2], nbd[2];
+        T nbu[NC], nbd[NC];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const T mx = maxv(maxv(maxv(hi[1][c], hi[0][c]), maxv(hi[2][c], c == 0 ? hL : hi[1][0])),
-                            c == 0 ? hi[1][1] : hR);
-          const T mn = minv(minv(minv(lo[1][c], lo[0][c]), minv(lo[2][c], c == 0 ? lL : lo[1][0])),
-                            c == 0 ? lo[1][1] : lR);
+        for (int c = 0; c < NC; ++c) {
+          const T mx = maxv(maxv(maxv(hi[1][c], hi[0][c]), maxv(hi[2][c], left_of(hi[1], c, hL))),
+                            right_of(hi[1], c, hR));
+          const T mn = minv(minv(minv(lo[1][c], lo[0][c]), minv(lo[2][c], left_of(lo[1], c, lL))),
+                            right_of(lo[1], c, lR));
           const T Fm0 = u0[0][c], Fp0 = u0[1][c];
-          const T Fp1 = u1[1][c], Fm1 = c == 0 ? u1L : u1[1][0];
+          const T Fp1 = u1[1][c], Fm1 = left_of(u1[1], c, u1L);
           const T in = (posp(Fm0) - negp(Fp0)) + (posp(Fm1) - negp(Fp1));
           const T ou = (posp(Fp0) - negp(Fm0)) + (posp(Fp1) - negp(Fm1));
           const T Gi = NUG ? gg[1][c] : T(1);
           const T q = p1[2][c];
-          nbu[c] = in > T(0) ? minv(T(1), fdiv(Gi * posp(mx - q), in)) : T(1);
-          nbd[c] = ou > T(0) ? minv(T(1), fdiv(Gi * posp(q - mn), ou)) : T(1);
+          // min(1, x / |s|) is 1 for s = 0 (x/0 is inf or NaN, and min ignores NaN)
+          nbu[c] = min1(fdiv(Gi * posp(mx - q), absv(in)));
+          nbd[c] = min1(fdiv(Gi * posp(q - mn), absv(ou)));
         }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          bu[0][c] = bu[1][c]; bu[1][c] = nbu[c];
-          bd[0][c] = bd[1][c]; bd[1][c] = nbd[c];
-        }
+        copy_row(bu[0], bu[1]); copy_row(bu[1], nbu);
+        copy_row(bd[0], bd[1]); copy_row(bd[1], nbd);
       }
     }
 
     // ---- row r = x-3: limited fluxes and pass 2
-    if (t >= 5) {
-      T h0[2], h1[2];
+    if (S || t >= 5) {
+      T h0[NC], h1[NC];
       if (FCT) {
         const T buR = from_right(bu[0]), bdR = from_right(bd[0]);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NC; ++c) {
+          // With two passes only the limited flux F*m is used, so a zero flux needs no
+          // factor: m = min(beta_dn of the upwind cell, beta_up of the downwind cell).
           {  // face (r+1/2, c) between rows r and r+1
-            const T V = a0[0][c], F = u0[0][c];
-            const bool right = F > T(0) || (F == T(0) && V > T(0));
-            const T m = minv(right ? bd[0][c] : bu[0][c], right ? bu[1][c] : bd[1][c]);
-            h0[c] = F * m;
+            const T F = u0[0][c];
+            const bool right = F > T(0);
+            h0[c] = F * minv(right ? bd[0][c] : bu[0][c], right ? bu[1][c] : bd[1][c]);
           }
           {  // face (r, c+1/2)
-            const T V = a1[0][c], F = u1[0][c];
-            const bool right = F > T(0) || (F == T(0) && V > T(0));
+            const T F = u1[0][c];
+            const bool right = F > T(0);
             const T a = right ? bd[0][c] : bu[0][c];
-            const T b = right ? (c == 0 ? bu[0][1] : buR) : (c == 0 ? bd[0][1] : bdR);
+            const T b = right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR);
             h1[c] = F * minv(a, b);
           }
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) { h0[c] = u0[0][c]; h1[c] = u1[0][c]; }
+        for (int c = 0; c < NC; ++c) { h0[c] = u0[0][c]; h1[c] = u1[0][c]; }
       }
-      if (t >= 6) {
+      if (S || t >= 6) {
         const T h1L = from_left(h1);
         const int row = R0 + t - 6;
-        T np2[2];
+        T np2[NC];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NC; ++c) {
           const T rG = NUG ? fdiv(T(1), gg[0][c]) : T(1);
-          np2[c] = donor<T, NUG>(p1[1][c], h0[c], h0c[c], h1[c], c == 0 ? h1L : h1[0], rG, kahan);
+          np2[c] = donor<T, NUG, KAHAN>(p1[1][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
         }
         if (row < p.n0) {
-          const int col = strip * kStride + lc0 - kLead;
-          const bool ok0 = lc0 >= kLead && lc0 < kLead + kStride && col < p.n1;
-          const bool ok1 = lc0 + 1 >= kLead && lc0 + 1 < kLead + kStride && col + 1 < p.n1;
-          const long long o = static_cast<long long>(row) * p.n1 + col;
-          if (p.rhs_a) {
-            if (ok0) np2[0] = np2[0] + p.dt * p.R[o];
-            if (ok1) np2[1] = np2[1] + p.dt * p.R[o + 1];
+          const int gcol = strip * kStride + lc0 - kLead;
+          const long long o = static_cast<long long>(row) * p.n1 + gcol;
+          bool ok[NC];
+          bool all = true;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            ok[c] = lc0 + c >= kLead && lc0 + c < kLead + kStride && gcol + c < p.n1;
+            all = all && ok[c];
+            if (p.rhs_a && ok[c]) np2[c] = np2[c] + p.dt * p.R[o + c];
           }
-          if (p.vec && ok0 && ok1) {
-            if constexpr (sizeof(T) == 4) {
+          if (p.vec && all) {
+            if constexpr (sizeof(T) == 4 && NC == 4) {
+              *reinterpret_cast<float4*>(p.out + o) = make_float4(np2[0], np2[1], np2[2], np2[3]);
+            } else if constexpr (sizeof(T) == 4 && NC == 2) {
               *reinterpret_cast<float2*>(p.out + o) = make_float2(np2[0], np2[1]);
-            } else {
+            } else if constexpr (sizeof(T) == 8 && NC == 2) {
               *reinterpret_cast<double2*>(p.out + o) = make_double2(np2[0], np2[1]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < NC; ++c) p.out[o + c] = np2[c];
             }
           } else {
-            if (ok0) p.out[o] = np2[0];
-            if (ok1) p.out[o + 1] = np2[1];
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              if (ok[c]) p.out[o + c] = np2[c];
           }
         }
       }
-      h0c[0] = h0[0];
-      h0c[1] = h0[1];
+      copy_row(h0c, h0);
     }
-  }
+  };
+#pragma unroll
+  for (int t = 0; t < 6; ++t) body(t, std::false_type{});
+#pragma unroll 2
+  for (int t = 6; t < nt; ++t) body(t, std::true_type{});
   cp_wait<0>();
 }
 
-template <typename T, bool FCT, bool NUG>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 void launch(const F2Params<T>& p, cudaStream_t st) {
   const long long warps = static_cast<long long>(p.strips) * p.rowtiles;
   const unsigned blocks = static_cast<unsigned>((warps + kWarps - 1) / kWarps);
-  const size_t smem = static_cast<size_t>(kWarps) * kSlots * kArr * kCols * sizeof(T);
-  static bool attr_set = false;  // FP64 rings exceed the default 48 KB of dynamic shared memory
+  const size_t smem = static_cast<size_t>(kWarps) * kSlots * kArr * cols<NC>() * sizeof(T);
+  static bool attr_set = false;  // large rings exceed the default 48 KB of dynamic shared memory
   if (!attr_set) {
-    cudaFuncSetAttribute(k_fused2d<T, FCT, NUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     attr_set = true;
   }
-  k_fused2d<T, FCT, NUG><<<blocks, kWarps * 32, smem, st>>>(p);
+  k_fused2d<T, NC, FCT, NUG, IGA, KAHAN><<<blocks, kWarps * 32, smem, st>>>(p);
+}
+
+template <typename T, int NC, bool FCT, bool NUG>
+void launch_mode(const F2Params<T>& p, bool iga, bool kahan, cudaStream_t st) {
+  if (iga) {
+    if (kahan) launch<T, NC, FCT, NUG, true, true>(p, st); else launch<T, NC, FCT, NUG, true, false>(p, st);
+  } else {
+    if (kahan) launch<T, NC, FCT, NUG, false, true>(p, st); else launch<T, NC, FCT, NUG, false, false>(p, st);
+  }
+}
+
+template <typename T, int NC>
+void launch_all(const F2Params<T>& p, const Opts& o, cudaStream_t st) {
+  if (o.fct) {
+    if (o.nug) launch_mode<T, NC, true, true>(p, o.iga, o.kahan, st);
+    else launch_mode<T, NC, true, false>(p, o.iga, o.kahan, st);
+  } else {
+    if (o.nug) launch_mode<T, NC, false, true>(p, o.iga, o.kahan, st);
+    else launch_mode<T, NC, false, false>(p, o.iga, o.kahan, st);
+  }
 }
 
 bool al(const void* q, size_t a) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) % a) == 0; }
@@ -383,6 +459,8 @@ template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStream_t st) {
   if (g.nd != 2 || o.n_iters != 2 || o.tot) return MPDATA_EUNSUPPORTED;
   if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+  // FP32 lanes own 4 columns (16-byte copies), FP64 lanes 2 (register budget)
+  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   F2Params<T> p;
   p.psi = a.psi_in;
   p.out = a.psi_out;
@@ -392,26 +470,24 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   p.R = a.r;
   p.n0 = g.n[1];
   p.n1 = g.n[2];
-  p.strips = (p.n1 + kStride - 1) / kStride;
-  p.ty = 8;
-  for (int ty : {64, 32, 16}) {
-    if (static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty) >= 152LL * 8) { p.ty = ty; break; }
+  p.strips = (p.n1 + stride<NC>() - 1) / stride<NC>();
+  if (o.tile_rows > 0) {
+    p.ty = o.tile_rows;
+  } else {  // the tallest tile that still gives 12 warps per SM (152 SMs), at least 8 rows
+    p.ty = 8;
+    for (int ty : {64, 32, 16}) {
+      if (static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty) >= 152LL * 12) { p.ty = ty; break; }
+    }
   }
   p.rowtiles = (p.n0 + p.ty - 1) / p.ty;
   p.dt = a.dt;
   p.scale = a.gc_scale;
-  p.iga = o.iga;
-  p.kahan = o.kahan;
   p.rhs_a = o.rhs_a;
   p.rhs_b = o.rhs_b;
-  const size_t va = 2 * sizeof(T);
-  p.vec = (p.n1 % 2 == 0) && al(p.psi, va) && al(p.out, va) && al(p.gc0, va) && al(p.gc1, va) &&
+  const size_t va = NC * sizeof(T) <= 16 ? NC * sizeof(T) : 16;
+  p.vec = (p.n1 % NC == 0) && al(p.psi, va) && al(p.out, va) && al(p.gc0, va) && al(p.gc1, va) &&
           al(p.G, va) && al(p.R, va);
-  if (o.fct) {
-    if (o.nug) launch<T, true, true>(p, st); else launch<T, true, false>(p, st);
-  } else {
-    if (o.nug) launch<T, false, true>(p, st); else launch<T, false, false>(p, st);
-  }
+  launch_all<T, NC>(p, o, st);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 

@@ -34,6 +34,7 @@ inline Grid make_grid(int nd, const int64_t* shape) {
 struct Opts {
   bool fct, tot, iga, nug, kahan, rhs_a, rhs_b, staged;
   int n_iters;
+  int tile_rows;  // fused 2D kernel: rows per warp tile (0 = automatic)
 };
 
 inline Opts make_opts(uint32_t o, int n_iters) {
@@ -47,6 +48,7 @@ inline Opts make_opts(uint32_t o, int n_iters) {
   p.rhs_b = o & MPDATA_RHS_EULER_B;
   p.staged = o & MPDATA_STAGED;
   p.n_iters = n_iters;
+  p.tile_rows = 0;
   return p;
 }
 

@@ -66,6 +66,9 @@ class Mpdata:
     def check_courant(self, gc, g=None):
         return capi.mpdata_check_courant(self.h, gc, g)
 
+    def tune(self, knob, value):
+        capi.mpdata_tune(self.h, knob, value)
+
     def request_stop(self):
         capi.mpdata_request_stop(self.h)
 
