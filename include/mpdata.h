@@ -109,12 +109,16 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
                    const void* g, const void* r, double dt, int n_steps, const double* gc_scale);
 
 /*
- * Reverse of ONE step from state psi_n (no sources; R enters linearly and has no
- * adjoint here): on entry psi_bar = dL/dpsi^{n+1}, on exit dL/dpsi^n (in place).
- * gc_bar (host array of ndims device pointers, or NULL): dL/dgc_d is ADDED to
- * gc_bar[d].  Branches (signs, FCT min/max) follow the forward step's choices;
- * [x]+ and [x]- have derivative 1/2 at 0.  Errors: EINVAL, EUNSUPPORTED for
- * batched handles, ECUDA.
+ * Reverse of ONE step from state psi_n (the derivative of the donor-cell passes,
+ * Eqs. 4-5, the antidiffusive advector, Eq. 6 with its multi-D cross terms, and
+ * the FCT limiter, Sect. 3.1.4): on entry psi_bar = dL/dpsi^{n+1}, on exit
+ * dL/dpsi^n (in place).  gc_bar (host array of ndims device pointers, or NULL):
+ * dL/dgc_d is ADDED to gc_bar[d].  Branches (signs, FCT min/max) follow the
+ * forward step's choices; [x]+ and [x]- have derivative 1/2 at 0; a min/max
+ * passes the derivative of its first extremal candidate.  The step is
+ * recomputed internally; the adjoint scratch is allocated on first use and kept
+ * with the handle.  Errors: EINVAL; EUNSUPPORTED for batched handles, for the
+ * third-order option, for source terms and for n_iters > 4; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
                         void* psi_bar, void* const* gc_bar);

@@ -1,7 +1,438 @@
+// Adjoint (reverse mode) of one MPDATA step: given dL/dpsi^{n+1}, produce
+// dL/dpsi^n and add dL/dGC to the advector adjoints.  The forward step is first
+// recomputed on the staged kernels with every pass's intermediates kept
+// (staged_forward_tape); then each sub-step is reversed, last first:
+//
+//   ka_donor_flux   donor-cell pass k and its fluxes (Eqs. 4-5)      gather
+//   ka_limit        FCT limited advector  V^ = V min(1, a, b)          scatter to beta
+//   ka_beta         FCT factors  G[psi_max - psi]+/in, ...            scatter to the fluxes
+//   ka_flux_u       unlimited fluxes of pass k                         gather
+//   ka_antidiff     antidiffusive advector (Eq. 6 + cross terms)       scatter (atomics)
+//   ka_bounds       FCT bounds over psi^n and psi^(1)                  scatter (atomics)
+//
+// Every adjoint array starts at zero and is only accumulated into, so the order
+// of the kernels is the reverse of the forward sub-steps.  Conventions at the
+// kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0 there), a max/min
+// passes the derivative of the first extremal candidate in the forward
+// candidate order, the limiter's min(1, a, b) that of the first minimum.
+// The third-order terms and the source terms have no adjoint here.
+#include <cuda_runtime.h>
+
 #include "kernels.h"
+
 namespace mpd {
+namespace {
+
+template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T dpos(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(0) : T(0.5)); }
+template <typename T> __device__ __forceinline__ T dneg(T x) { return x < T(0) ? T(1) : (x > T(0) ? T(0) : T(0.5)); }
+template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+
+template <typename T> struct P3 { const T* p[3]; };
+template <typename T> struct W3 { T* p[3]; };
+
+struct Coord { int c[3]; };
+__device__ __forceinline__ Coord coord_of(const Grid& g, long long i) {
+  Coord x;
+  x.c[2] = static_cast<int>(i % g.n[2]);
+  const long long r = i / g.n[2];
+  x.c[1] = static_cast<int>(r % g.n[1]);
+  x.c[0] = static_cast<int>(r / g.n[1]);
+  return x;
+}
+__device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
+  return (static_cast<long long>(x.c[0]) * g.n[1] + x.c[1]) * g.n[2] + x.c[2];
+}
+template <int ND>
+__device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
+  const int a = 3 - ND + d;
+  int v = (x.c[a] + s) % g.n[a];
+  if (v < 0) v += g.n[a];
+  x.c[a] = v;
+  return x;
+}
+
+template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit) {
+  return unit ? V : posp(V) * L + negp(V) * R;
+}
+
+#define CELL_INDEX                                                              \
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; \
+  if (i >= g.N) return;                                                         \
+  const Coord x = coord_of(g, i);
+
+// Reverse of the donor-cell pass k, psi_k = psi_{k-1} + sum_d (F_{i-e_d} - F_i)/G_i with
+// F = flux(psi_{k-1}, V^k): pb_prev += dL/dpsi_{k-1}, vhb[d] += dL/dV^k.
+template <typename T, int ND>
+__global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> V,
+                              const T* __restrict__ G, bool unit, T* __restrict__ pb_prev, W3<T> vhb) {
+  CELL_INDEX
+  const T gi = G ? pb[i] / G[i] : pb[i];
+  T acc = pb[i];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1)), im = lin(g, sh<ND>(g, x, d, -1));
+    const T gp = G ? pb[ip] / G[ip] : pb[ip];
+    const T gm = G ? pb[im] / G[im] : pb[im];
+    const T fp = gp - gi;  // dL/dF on the face (d, i)
+    const T fm = gi - gm;  // dL/dF on the face (d, i - e_d)
+    const T v = V.p[d][i], vm = V.p[d][im];
+    T dv = T(1);
+    if (!unit) {
+      acc += fp * posp(v) + fm * negp(vm);
+      dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
+    }
+    vhb.p[d][i] += fp * dv;
+  }
+  pb_prev[i] += acc;
+}
+
+// Reverse of the limiter V^ = V m, m = min(1, a, b) (a, b the factors the forward chose).
+template <typename T, int ND>
+__global__ void ka_limit(Grid g, P3<T> vhb, P3<T> V, const T* __restrict__ psi, bool unit,
+                         const T* __restrict__ bu, const T* __restrict__ bd, W3<T> vb, T* bub, T* bdb) {
+  CELL_INDEX
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const T v = V.p[d][i];
+    const T F = flux(psi[i], psi[ip], v, unit);
+    const bool right = F > T(0) || (F == T(0) && v > T(0));
+    const T a = right ? bd[i] : bu[i];
+    const T b = right ? bu[ip] : bd[ip];
+    T m = T(1);
+    int sel = 0;
+    if (a < m) { m = a; sel = 1; }
+    if (b < m) { m = b; sel = 2; }
+    const T gq = vhb.p[d][i];
+    vb.p[d][i] += gq * m;
+    if (sel == 1) atomicAdd(right ? &bdb[i] : &bub[i], gq * v);
+    if (sel == 2) atomicAdd(right ? &bub[ip] : &bdb[ip], gq * v);
+  }
+}
+
+// Reverse of the FCT factors beta_up = G[mx - psi]+/in, beta_dn = G[psi - mn]+/out (1 when the
+// sum is 0), in/out the sums of the signed parts of the unlimited fluxes around the cell.
+template <typename T, int ND>
+__global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__ bdb, const T* __restrict__ psi,
+                        P3<T> V, const T* __restrict__ G, bool unit, const T* __restrict__ mx,
+                        const T* __restrict__ mn, W3<T> fb, T* __restrict__ pb, T* __restrict__ mxb,
+                        T* __restrict__ mnb) {
+  CELL_INDEX
+  const T p = psi[i];
+  T Fp[3], Fm[3];
+  long long im[3];
+  T in = T(0), ou = T(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    im[d] = lin(g, sh<ND>(g, x, d, -1));
+    Fp[d] = flux(p, psi[ip], V.p[d][i], unit);
+    Fm[d] = flux(psi[im[d]], p, V.p[d][im[d]], unit);
+    in = in + (posp(Fm[d]) - negp(Fp[d]));
+    ou = ou + (posp(Fp[d]) - negp(Fm[d]));
+  }
+  const T Gi = G ? G[i] : T(1);
+  T gin = T(0), gout = T(0), pacc = T(0);
+  const T gu = bub[i], gd = bdb[i];
+  if (in > T(0) && gu != T(0)) {
+    const T beta = Gi * posp(mx[i] - p) / in;
+    const T t = gu * Gi * dpos(mx[i] - p) / in;
+    mxb[i] += t;
+    pacc -= t;
+    gin = -gu * beta / in;
+  }
+  if (ou > T(0) && gd != T(0)) {
+    const T beta = Gi * posp(p - mn[i]) / ou;
+    const T t = gd * Gi * dpos(p - mn[i]) / ou;
+    pacc += t;
+    mnb[i] -= t;
+    gout = -gd * beta / ou;
+  }
+  if (gin != T(0) || gout != T(0)) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      atomicAdd(&fb.p[d][i], -gin * dneg(Fp[d]) + gout * dpos(Fp[d]));
+      atomicAdd(&fb.p[d][im[d]], gin * dpos(Fm[d]) - gout * dneg(Fm[d]));
+    }
+  }
+  pb[i] += pacc;
+}
+
+// Reverse of the unlimited fluxes F = flux(psi_{k-1}, V^k) that fed the FCT factors.
+template <typename T, int ND>
+__global__ void ka_flux_u(Grid g, P3<T> fb, const T* __restrict__ psi, P3<T> V, bool unit, T* __restrict__ pb,
+                          W3<T> vb) {
+  CELL_INDEX
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = lin(g, sh<ND>(g, x, d, +1)), im = lin(g, sh<ND>(g, x, d, -1));
+    const T fp = fb.p[d][i], fm = fb.p[d][im];
+    const T v = V.p[d][i], vm = V.p[d][im];
+    T dv = T(1);
+    if (!unit) {
+      acc += fp * posp(v) + fm * negp(vm);
+      dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
+    }
+    vb.p[d][i] += fp * dv;
+  }
+  pb[i] += acc;
+}
+
+// Reverse of the antidiffusive advector (Eq. 6 with the multi-D cross terms):
+//   out = (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q,  A = (p1-p0)/(p0+p1),  B = (T-Bt)/(T+Bt)
+// (A = (p1-p0)/2 and B = (T-Bt)/4 under infinite gauge).
+template <typename T, int ND>
+__global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> Vin, const T* __restrict__ G,
+                            bool iga, T* pb, W3<T> vhb) {
+  CELL_INDEX
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const T gout = vb.p[d][i];
+    if (gout == T(0)) continue;
+    const Coord xd = sh<ND>(g, x, d, +1);
+    const long long ip = lin(g, xd);
+    const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
+    const T V = Vin.p[d][i];
+    const T p0 = psi[i], p1 = psi[ip];
+    T A, dA0, dA1;
+    if (iga) {
+      A = (p1 - p0) * T(0.5); dA0 = T(-0.5); dA1 = T(0.5);
+    } else {
+      const T s = p0 + p1;
+      if (s != T(0)) {
+        A = (p1 - p0) / s; dA0 = T(-2) * p1 / (s * s); dA1 = T(2) * p0 / (s * s);
+      } else {
+        A = dA0 = dA1 = T(0);
+      }
+    }
+    const T c = absv(V) - V * V / Gb;
+    T gV = gout * (sgn(V) - T(2) * V / Gb) * A;
+    atomicAdd(&pb[i], gout * c * dA0);
+    atomicAdd(&pb[ip], gout * c * dA1);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      if (q == d) continue;
+      const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
+      const long long iqp = lin(g, xp), idqp = lin(g, sh<ND>(g, xp, d, +1));
+      const long long iqm = lin(g, xm), idqm = lin(g, sh<ND>(g, xm, d, +1));
+      const T* Q = Vin.p[q];
+      const T Vq = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
+      const T Tp = psi[iqp] + psi[idqp], Bt = psi[iqm] + psi[idqm];
+      T B, dBT, dBB;
+      if (iga) {
+        B = (Tp - Bt) * T(0.25); dBT = T(0.25); dBB = T(-0.25);
+      } else {
+        const T S = Tp + Bt;
+        if (S != T(0)) {
+          B = (Tp - Bt) / S; dBT = T(2) * Bt / (S * S); dBB = T(-2) * Tp / (S * S);
+        } else {
+          B = dBT = dBB = T(0);
+        }
+      }
+      gV += gout * (T(-0.5) * Vq / Gb * B);
+      const T gq = gout * (T(-0.5) * V / Gb * B) * T(0.25);
+      atomicAdd(&vhb.p[q][i], gq);
+      atomicAdd(&vhb.p[q][ip], gq);
+      atomicAdd(&vhb.p[q][iqm], gq);
+      atomicAdd(&vhb.p[q][idqm], gq);
+      const T gB = gout * (T(-0.5) * V * Vq / Gb);
+      atomicAdd(&pb[iqp], gB * dBT);
+      atomicAdd(&pb[idqp], gB * dBT);
+      atomicAdd(&pb[iqm], gB * dBB);
+      atomicAdd(&pb[idqm], gB * dBB);
+    }
+    atomicAdd(&vhb.p[d][i], gV);
+  }
+}
+
+// Reverse of the FCT bounds: the adjoint of each extremum goes to its first extremal candidate
+// (order: the cell, then per dimension its -e_d and +e_d neighbours; psi^n before psi^(1)).
+template <typename T, int ND>
+__global__ void ka_bounds(Grid g, const T* __restrict__ mxb, const T* __restrict__ mnb, const T* __restrict__ p0,
+                          const T* __restrict__ p1, T* pb0, T* pb1) {
+  CELL_INDEX
+  long long loc[7];
+  int nl = 0;
+  loc[nl++] = i;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    loc[nl++] = lin(g, sh<ND>(g, x, d, -1));
+    loc[nl++] = lin(g, sh<ND>(g, x, d, +1));
+  }
+  T hi = p0[i], lo = p0[i];
+  int ha = 0, la = 0;
+  long long hj = i, lj = i;
+  for (int j = 0; j < nl; ++j) {
+    const T a = p0[loc[j]], b = p1[loc[j]];
+    if (a > hi) { hi = a; ha = 0; hj = loc[j]; }
+    if (b > hi) { hi = b; ha = 1; hj = loc[j]; }
+    if (a < lo) { lo = a; la = 0; lj = loc[j]; }
+    if (b < lo) { lo = b; la = 1; lj = loc[j]; }
+  }
+  if (mxb[i] != T(0)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], mxb[i]);
+  if (mnb[i] != T(0)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], mnb[i]);
+}
+
 template <typename T>
-int adjoint_step(mpdata_s*, const T*, const void* const*, const T*, T*, void* const*) { return MPDATA_EUNSUPPORTED; }
+__global__ void ka_accumulate(long long n, const T* __restrict__ src, T* __restrict__ dst) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i < n) dst[i] += src[i];
+}
+
+template <typename T>
+struct AdjPlan {
+  int K = 0, D = 0, fct = 0;
+  long long N = 0;
+  size_t arrays = 0;
+};
+
+template <typename T>
+size_t count_arrays(int K, int D, bool fct) {
+  size_t n = 0;
+  n += K - 1;                       // psi levels 1..K-1
+  n += static_cast<size_t>(D) * (K - 1);      // unlimited advectors k = 2..K
+  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + 2 * (K - 1);  // limited advectors, bounds, factors
+  n += K;                           // psi adjoints 0..K-1
+  n += static_cast<size_t>(D) * K;  // advector adjoints k = 1..K
+  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + D + 2;  // unlimited-advector adjoints, factor adj., flux adj., bounds adj.
+  return n;
+}
+
+template <typename T, int ND>
+int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const T* const* gc, const T* G,
+               T* psi_bar, void* const* gc_bar, cudaStream_t st) {
+  const int K = o.n_iters, D = ND;
+  const long long N = g.N;
+  const size_t need = count_arrays<T>(K, D, o.fct) * static_cast<size_t>(N) * sizeof(T);
+  void** slot = handle_adj(h);
+  // the adjoint scratch is allocated on first use and kept with the handle; its size is
+  // stored in front of it
+  struct Hdr { size_t bytes; void* ptr; };
+  Hdr* hdr = static_cast<Hdr*>(*slot);
+  if (hdr == nullptr || hdr->bytes < need) {
+    if (hdr) { cudaFree(hdr->ptr); delete hdr; *slot = nullptr; }
+    hdr = new Hdr{need, nullptr};
+    if (cudaMalloc(&hdr->ptr, need) != cudaSuccess) { delete hdr; return MPDATA_ENOMEM; }
+    *slot = hdr;
+  }
+  T* cur = static_cast<T*>(hdr->ptr);
+  auto take = [&]() { T* q = cur; cur += N; return q; };
+  Tape<T> tp{};
+  T* levels[kTapeMax] = {nullptr, nullptr, nullptr, nullptr};
+  tp.psi[0] = psi_n;
+  for (int k = 1; k < K; ++k) { levels[k] = take(); tp.psi[k] = levels[k]; }
+  for (int d = 0; d < 3; ++d) tp.vh[1][d] = d < D ? gc[d] : nullptr;
+  for (int k = 2; k <= K; ++k)
+    for (int d = 0; d < D; ++d) tp.v[k][d] = take();
+  if (o.fct) {
+    for (int k = 2; k <= K; ++k)
+      for (int d = 0; d < D; ++d) tp.vh[k][d] = take();
+    tp.mx = take();
+    tp.mn = take();
+    for (int k = 2; k <= K; ++k) { tp.bu[k] = take(); tp.bd[k] = take(); }
+  } else {
+    for (int k = 2; k <= K; ++k)
+      for (int d = 0; d < D; ++d) tp.vh[k][d] = tp.v[k][d];
+  }
+  T* const adj_begin = cur;
+  T* pbl[kTapeMax];
+  for (int k = 0; k < K; ++k) pbl[k] = take();
+  T* vhb[kTapeMax + 1][3] = {};
+  for (int k = 1; k <= K; ++k)
+    for (int d = 0; d < D; ++d) vhb[k][d] = take();
+  T* vbk[kTapeMax + 1][3] = {};
+  T *bub = nullptr, *bdb = nullptr, *fb[3] = {nullptr, nullptr, nullptr}, *mxb = nullptr, *mnb = nullptr;
+  if (o.fct) {
+    for (int k = 2; k <= K; ++k)
+      for (int d = 0; d < D; ++d) vbk[k][d] = take();
+    bub = take();
+    bdb = take();
+    for (int d = 0; d < D; ++d) fb[d] = take();
+    mxb = take();
+    mnb = take();
+  }
+  if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(cur - adj_begin) * sizeof(T), st) != cudaSuccess)
+    return MPDATA_ECUDA;
+  if (staged_forward_tape<T>(g, o, gc, G, tp, levels, st) != cudaSuccess) return MPDATA_ECUDA;
+
+  const int bs = 256;
+  const unsigned nb = static_cast<unsigned>((N + bs - 1) / bs);
+  for (int k = K; k >= 2; --k) {
+    const T* pbk = (k == K) ? psi_bar : pbl[k];
+    P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
+    W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
+    ka_donor_flux<T, ND><<<nb, bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1], vhbk);
+    P3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
+    P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
+    if (o.fct) {
+      const size_t nz = static_cast<size_t>(N) * sizeof(T);
+      cudaMemsetAsync(bub, 0, nz, st);
+      cudaMemsetAsync(bdb, 0, nz, st);
+      for (int d = 0; d < D; ++d) cudaMemsetAsync(fb[d], 0, nz, st);
+      P3<T> vhbr{{vhb[k][0], vhb[k][1], vhb[k][2]}};
+      W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
+      ka_limit<T, ND><<<nb, bs, 0, st>>>(g, vhbr, vu, tp.psi[k - 1], o.iga, tp.bu[k], tp.bd[k], vbw, bub, bdb);
+      W3<T> fbw{{fb[0], fb[1], fb[2]}};
+      ka_beta<T, ND><<<nb, bs, 0, st>>>(g, bub, bdb, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, fbw, pbl[k - 1],
+                                        mxb, mnb);
+      P3<T> fbr{{fb[0], fb[1], fb[2]}};
+      ka_flux_u<T, ND><<<nb, bs, 0, st>>>(g, fbr, tp.psi[k - 1], vu, o.iga, pbl[k - 1], vbw);
+      gv = P3<T>{{vbk[k][0], vbk[k][1], vbk[k][2]}};
+    }
+    P3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
+    W3<T> vhbp{{vhb[k - 1][0], vhb[k - 1][1], vhb[k - 1][2]}};
+    ka_antidiff<T, ND><<<nb, bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
+  }
+  if (o.fct && K >= 2) ka_bounds<T, ND><<<nb, bs, 0, st>>>(g, mxb, mnb, tp.psi[0], tp.psi[1], pbl[0], pbl[1]);
+  {
+    const T* pb1 = (K == 1) ? psi_bar : pbl[1];
+    P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
+    W3<T> vhb1{{vhb[1][0], vhb[1][1], vhb[1][2]}};
+    ka_donor_flux<T, ND><<<nb, bs, 0, st>>>(g, pb1, tp.psi[0], v1, G, false, pbl[0], vhb1);
+  }
+  if (cudaMemcpyAsync(psi_bar, pbl[0], static_cast<size_t>(N) * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return MPDATA_ECUDA;
+  if (gc_bar)
+    for (int d = 0; d < D; ++d)
+      if (gc_bar[d]) ka_accumulate<T><<<nb, bs, 0, st>>>(N, vhb[1][d], static_cast<T*>(gc_bar[d]));
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+}  // namespace
+
+void adjoint_free(mpdata_s* h) {
+  struct Hdr { size_t bytes; void* ptr; };
+  void** slot = handle_adj(h);
+  Hdr* hdr = static_cast<Hdr*>(*slot);
+  if (hdr) {
+    cudaFree(hdr->ptr);
+    delete hdr;
+    *slot = nullptr;
+  }
+}
+
+template <typename T>
+int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gcv, const T* g, T* psi_bar, void* const* gc_bar) {
+  Opts o = make_opts(handle_opts(h), handle_n_iters(h));
+  if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+  const Grid& gr = handle_grids(h)[0];
+  const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
+                    gr.nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
+  const T* G = o.nug ? g : nullptr;
+  cudaStream_t st = handle_stream(h);
+  switch (gr.nd) {
+    case 1: return adjoint_nd<T, 1>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
+    case 2: return adjoint_nd<T, 2>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
+    case 3: return adjoint_nd<T, 3>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
+  }
+  return MPDATA_EINVAL;
+}
+
 template int adjoint_step<float>(mpdata_s*, const float*, const void* const*, const float*, float*, void* const*);
 template int adjoint_step<double>(mpdata_s*, const double*, const void* const*, const double*, double*, void* const*);
-}
+
+}  // namespace mpd

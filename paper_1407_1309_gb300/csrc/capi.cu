@@ -129,7 +129,7 @@ int sync_status(mpdata_s* h) {
 void free_all(mpdata_s* h) {
   cudaFree(h->staged);
   cudaFree(h->pingpong);
-  cudaFree(h->adj);
+  mpd::adjoint_free(h);
   cudaFree(h->d_spans);
   cudaFree(h->d_partial);
   cudaFree(h->d_out);
@@ -229,7 +229,8 @@ int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, con
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
                         void* const* gc_bar) {
   if (!h || !psi_bar) return MPDATA_EINVAL;
-  int rc = validate_fields(h, psi_n, gc, g, (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B)) ? psi_n : nullptr);
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT)) return MPDATA_EUNSUPPORTED;
+  int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
   if (!aligned(psi_bar, h->esize)) return MPDATA_EINVAL;
   if (gc_bar)

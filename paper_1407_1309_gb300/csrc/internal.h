@@ -88,6 +88,25 @@ template <typename T>
 cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a,
                         const StagedScratch<T>& s, cudaStream_t st);
 
+// Intermediates of one forward step kept for the adjoint (n_iters <= kTapeMax).
+constexpr int kTapeMax = 4;
+template <typename T>
+struct Tape {
+  const T* psi[kTapeMax];          // psi^(k), k = 0..K-1 (psi[0] is the step input)
+  T* v[kTapeMax + 1][3];           // unlimited antidiffusive advector of pass k >= 2
+  const T* vh[kTapeMax + 1][3];    // advector that drives pass k (gc for k = 1; limited under FCT)
+  T* mx;
+  T* mn;
+  T* bu[kTapeMax + 1];
+  T* bd[kTapeMax + 1];
+};
+
+// Forward step on the staged kernels keeping every pass's intermediates (no sources).
+// Writes psi^(1..K-1), the pseudo-advectors, the FCT bounds and factors into the tape.
+template <typename T>
+cudaError_t staged_forward_tape(const Grid& g, const Opts& o, const T* const* gc, const T* G,
+                                const Tape<T>& tp, T* const* psi_out_levels, cudaStream_t st);
+
 // FP64 reductions (reduce.cu).  partial: device scratch of at least
 // kRedBlocks * n_fields doubles per output.
 constexpr int kRedBlocks = 256;

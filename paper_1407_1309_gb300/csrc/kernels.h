@@ -36,5 +36,6 @@ void batched_free(mpdata_s* h);
 template <typename T>
 int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* psi_bar,
                  void* const* gc_bar);
+void adjoint_free(mpdata_s* h);
 
 }  // namespace mpd

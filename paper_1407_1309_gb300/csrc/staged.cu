@@ -301,6 +301,36 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   return cudaGetLastError();
 }
 
+template <typename T, int ND>
+cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G, const Tape<T>& tp,
+                    T* const* levels, cudaStream_t st) {
+  const int bs = 256;
+  const unsigned nb = static_cast<unsigned>((g.N + bs - 1) / bs);
+  const int K = o.n_iters;
+  In3<T> v1{{gc[0], gc[1], gc[2]}};
+  if (K >= 2) {
+    k_donor<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, levels[1]);
+    if (o.fct) k_bounds<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
+  }
+  for (int k = 2; k <= K; ++k) {
+    In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
+    Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
+    k_antidiff<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
+    In3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
+    if (o.fct) {
+      k_beta<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, tp.bu[k], tp.bd[k]);
+      Out3<T> vl{{const_cast<T*>(tp.vh[k][0]), const_cast<T*>(tp.vh[k][1]), const_cast<T*>(tp.vh[k][2])}};
+      k_limit<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vu, o.iga, tp.bu[k], tp.bd[k], vl);
+    }
+    if (k < K) {
+      In3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
+      k_donor<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vh, T(1), o.iga, G, o.kahan, nullptr, T(0), false,
+                                        levels[k]);
+    }
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 template <typename T>
@@ -332,6 +362,21 @@ cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cons
   return cudaErrorInvalidValue;
 }
 
+template <typename T>
+cudaError_t staged_forward_tape(const Grid& g, const Opts& o, const T* const* gc, const T* G, const Tape<T>& tp,
+                                T* const* levels, cudaStream_t st) {
+  switch (g.nd) {
+    case 1: return tape_nd<T, 1>(g, o, gc, G, tp, levels, st);
+    case 2: return tape_nd<T, 2>(g, o, gc, G, tp, levels, st);
+    case 3: return tape_nd<T, 3>(g, o, gc, G, tp, levels, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t staged_forward_tape<float>(const Grid&, const Opts&, const float* const*, const float*,
+                                                const Tape<float>&, float* const*, cudaStream_t);
+template cudaError_t staged_forward_tape<double>(const Grid&, const Opts&, const double* const*, const double*,
+                                                 const Tape<double>&, double* const*, cudaStream_t);
 template StagedScratch<float> carve_staged<float>(void*, long long);
 template StagedScratch<double> carve_staged<double>(void*, long long);
 template cudaError_t staged_step<float>(const Grid&, const Opts&, const StepArgs<float>&,

@@ -1,0 +1,145 @@
+"""The adjoint kernels against the oracle's adjoint, and autograd gradients against
+central finite differences of the GPU forward.
+
+FP64 GPU adjoint vs FP64 oracle adjoint: max-norm relative error <= 1e-12 on
+generic smooth positive inputs (no flat regions and no ties, where the limiter's
+branches are differentiable).  Gradients of a rollout loss: relative error <= 1e-4
+against central differences along seeded smooth directions.  The FCT limiter makes
+the step only piecewise smooth (min/max switches), so over many steps a
+perturbation of 1e-3, or even 1e-6 on a coarse grid, crosses switches somewhere in
+the field and the difference quotient itself is off; with FCT the check therefore
+uses eps = 1e-7 in FP64 (where the quotient has converged to the adjoint
+gradient), and eps = 1e-3 for the smooth scheme without the limiter.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import nondivergent, smooth_positive
+from paper_1407_1309_gb300 import capi, workloads
+from paper_1407_1309_gb300.autograd import rollout
+from paper_1407_1309_gb300.solver import Mpdata
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "donor": (1, 0),
+    "basic": (2, 0),
+    "fct": (2, capi.FCT),
+    "iga_fct": (2, capi.IGA | capi.FCT),
+    "it3_fct": (3, capi.FCT),
+    "kahan_fct": (2, capi.KAHAN | capi.FCT),
+}
+SHAPES = [(41,), (14, 11), (6, 7, 5)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("nug", [False, True], ids=["g1", "nug"])
+def test_adjoint_matches_oracle(shape, name, nug):
+    n_iters, opts = CASES[name]
+    rng = np.random.default_rng(len(shape) * 10 + n_iters)
+    psi = smooth_positive(shape, rng)
+    if opts & capi.IGA:
+        psi = psi - 2.0
+    gc = nondivergent(shape, rng, 0.3)
+    G = 1.0 + 0.2 * rng.uniform(size=shape) if nug else None
+    y = rng.normal(size=shape)
+    ref_pb, ref_gcb = oracle.adj_step(psi, gc, y, g=G, n_iters=n_iters, opts=opts)
+    dev = torch.device("cuda")
+    t = lambda a: None if a is None else torch.tensor(a, dtype=torch.float64, device=dev)
+    o = opts | (capi.NUG if nug else 0)
+    with Mpdata(shape, dtype=torch.float64, n_iters=n_iters, opts=o) as m:
+        pb = t(y)
+        gcb = [torch.full(shape, 0.5, dtype=torch.float64, device=dev) for _ in shape]  # accumulated onto
+        m.adjoint_step(t(psi), [t(v) for v in gc], pb, g=t(G), gc_bar=gcb)
+        torch.cuda.synchronize()
+        got_pb = pb.cpu().numpy()
+        got_gcb = [v.cpu().numpy() - 0.5 for v in gcb]
+    scale = max(np.abs(ref_pb).max(), max(np.abs(v).max() for v in ref_gcb))
+    assert np.abs(got_pb - ref_pb).max() <= 1e-12 * scale
+    for a, b in zip(got_gcb, ref_gcb):
+        assert np.abs(a - b).max() <= 1e-12 * scale
+
+
+def test_adjoint_fp32_close_to_oracle():
+    shape = (33, 29)
+    rng = np.random.default_rng(3)
+    psi, gc, y = smooth_positive(shape, rng), nondivergent(shape, rng, 0.35), rng.normal(size=shape)
+    r = lambda a: a.astype(np.float32).astype(np.float64)
+    psi, gc, y = r(psi), [r(v) for v in gc], r(y)
+    ref_pb, ref_gcb = oracle.adj_step(psi, gc, y, n_iters=2, opts=oracle.FCT)
+    dev = torch.device("cuda")
+    with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=capi.FCT) as m:
+        pb = torch.tensor(y, dtype=torch.float32, device=dev)
+        gcb = [torch.zeros(shape, device=dev) for _ in shape]
+        m.adjoint_step(torch.tensor(psi, dtype=torch.float32, device=dev),
+                       [torch.tensor(v, dtype=torch.float32, device=dev) for v in gc], pb, gc_bar=gcb)
+        torch.cuda.synchronize()
+    assert np.linalg.norm(pb.cpu().numpy() - ref_pb) <= 1e-5 * np.linalg.norm(ref_pb)
+    for a, b in zip(gcb, ref_gcb):
+        assert np.linalg.norm(a.cpu().numpy() - b) <= 1e-5 * np.linalg.norm(b)
+
+
+def test_adjoint_rejects_unsupported():
+    dev = torch.device("cuda")
+    shape = (8, 8)
+    z = [torch.zeros(shape, device=dev), torch.zeros(shape, device=dev)]
+    with Mpdata(shape, dtype=torch.float32, n_iters=3, opts=capi.TOT) as m:
+        rc = capi.mpdata_adjoint_step(m.h, z[0], z, None, z[1], raw=True)
+        assert rc == capi.EUNSUPPORTED
+
+
+def fd_check(n, steps, every, n_dirs, seed=0, eps=1e-7, opts=capi.FCT):
+    """Loss 0.5 ||psi_T - psi_target||^2; autograd gradient vs central differences."""
+    psi0_np, gc_np, pert = workloads.adjoint_2d(n, seed=seed)
+    dev = torch.device("cuda")
+    f64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    m = Mpdata((n, n), dtype=torch.float64, n_iters=2, opts=opts)
+    gc = [f64(v) for v in gc_np]
+    with torch.no_grad():
+        target = rollout(m, f64(psi0_np + 0.05 * pert), gc, steps, every)
+
+    def loss(p0, g):
+        out = rollout(m, p0, g, steps, every)
+        return 0.5 * ((out - target) ** 2).sum()
+
+    p0 = f64(psi0_np).requires_grad_(True)
+    gg = [v.clone().requires_grad_(True) for v in gc]
+    L = loss(p0, gg)
+    L.backward()
+    rng = np.random.default_rng(seed + 1)
+    errs = []
+    for _ in range(n_dirs):
+        dirs = []
+        for _k in range(3):
+            d = workloads.low_modes(rng, (n, n), 4)
+            dirs.append(d / np.sqrt(np.mean(d ** 2)))
+        dp, dg = f64(dirs[0]), [f64(dirs[1]) * 0.05, f64(dirs[2]) * 0.05]
+        with torch.no_grad():
+            lp = loss(p0 + eps * dp, [a + eps * b for a, b in zip(gc, dg)])
+            lm = loss(p0 - eps * dp, [a - eps * b for a, b in zip(gc, dg)])
+        fd = float((lp - lm) / (2 * eps))
+        an = float((p0.grad * dp).sum() + sum((a.grad * b).sum() for a, b in zip(gg, dg)))
+        errs.append(abs(fd - an) / max(abs(fd), 1e-30))
+    m.close()
+    return errs
+
+
+def test_autograd_gradient_matches_finite_differences_small():
+    errs = fd_check(48, 24, 5, 6)
+    assert max(errs) <= 1e-4, errs
+
+
+def test_autograd_gradient_smooth_scheme_eps_1e3():
+    """Without the limiter the step is smooth and eps = 1e-3 suffices."""
+    errs = fd_check(48, 24, 5, 6, eps=1e-3, opts=0)
+    assert max(errs) <= 1e-4, errs
+
+
+def test_autograd_gradient_adjoint_workload_512():
+    """The adjoint workload (512^2, FCT, two passes, 200 steps, checkpoints every 20) on
+    eight seeded smooth directions over (psi0, GC)."""
+    errs = fd_check(512, 200, 20, 8)
+    assert max(errs) <= 1e-4, errs
