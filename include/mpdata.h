@@ -160,6 +160,11 @@ int mpdata_clear_stop(mpdata_t h);
 enum { MPDATA_TUNE_TILE_ROWS = 1 };
 int mpdata_tune(mpdata_t h, int knob, int value);
 
+/* Sends the handle's later work to cuda_stream (a cudaStream_t on the handle's
+ * device; NULL = legacy default stream), e.g. a stream that is capturing a CUDA
+ * graph of a step loop.  Work already enqueued is not moved. */
+int mpdata_set_stream(mpdata_t h, void* cuda_stream);
+
 /* Waits for the handle's stream and returns the first pending device error, if any. */
 int mpdata_sync(mpdata_t h);
 

@@ -22,7 +22,7 @@ OK, EINVAL, EUNSUPPORTED, ECUDA, ECOURANT, ETIMEOUT, ESTOPPED, ENOMEM = range(8)
 EXPORTED = (
     "mpdata_create", "mpdata_step", "mpdata_advance", "mpdata_adjoint_step", "mpdata_reduce",
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
-    "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune",
+    "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
 )
 TUNE_TILE_ROWS = 1
 
@@ -67,6 +67,7 @@ def load(build_if_needed: bool = True):
             "mpdata_diff_norms": ([P, P, P, DP, DP], I),
             "mpdata_check_courant": ([P, PP, P, DP], I),
             "mpdata_tune": ([P, I, I], I),
+            "mpdata_set_stream": ([P, P], I),
             "mpdata_request_stop": ([P], I),
             "mpdata_clear_stop": ([P], I),
             "mpdata_sync": ([P], I),
@@ -194,6 +195,10 @@ def mpdata_check_courant(h, gc, g=None):
 
 def mpdata_tune(h, knob, value):
     _check(load().mpdata_tune(h, int(knob), int(value)), "mpdata_tune")
+
+
+def mpdata_set_stream(h, stream):
+    _check(load().mpdata_set_stream(h, _stream_ptr(stream)), "mpdata_set_stream")
 
 
 def mpdata_request_stop(h):

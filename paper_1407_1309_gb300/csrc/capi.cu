@@ -330,6 +330,12 @@ int mpdata_clear_stop(mpdata_t h) {
   return MPDATA_OK;
 }
 
+int mpdata_set_stream(mpdata_t h, void* cuda_stream) {
+  if (!h) return MPDATA_EINVAL;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return MPDATA_OK;
+}
+
 int mpdata_sync(mpdata_t h) {
   if (!h) return MPDATA_EINVAL;
   DeviceGuard dg(h->device);

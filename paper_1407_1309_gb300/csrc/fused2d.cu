@@ -133,22 +133,19 @@ template <typename T, int N> __device__ __forceinline__ void copy_row(T (&d)[N],
   for (int c = 0; c < N; ++c) d[c] = s[c];
 }
 
+// One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
+// row R0 down ty rows of the field described by p; `ring` is the warp's shared-memory ring.
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
-__global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
+__device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip, const int R0, T* ring_warp,
+                                           const int lane) {
   constexpr int kCols = cols<NC>();
   constexpr int kStride = stride<NC>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long wid = static_cast<long long>(blockIdx.x) * kWarps + wib;
-  if (wid >= static_cast<long long>(p.strips) * p.rowtiles) return;  // whole warp
-  const int strip = static_cast<int>(wid % p.strips);
-  const int R0 = static_cast<int>(wid / p.strips) * p.ty;
   const int lc0 = NC * lane;
   const int cs = strip * kStride - kLead;
   int col[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) col[c] = wrapi(cs + lc0 + c, p.n1);
-  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * kCols + lc0;
+  T* ring = ring_warp + lc0;
   const int nt = p.ty + 6;
   const T* src[kArr] = {p.psi, p.gc0, p.gc1, NUG ? p.G : nullptr, p.rhs_b ? p.R : nullptr};
   // prefetch cursor: next row to copy, its element offset and ring slot
@@ -418,6 +415,64 @@ __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
 }
 
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+__global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long wid = static_cast<long long>(blockIdx.x) * kWarps + wib;
+  if (wid >= static_cast<long long>(p.strips) * p.rowtiles) return;  // whole warp
+  const int strip = static_cast<int>(wid % p.strips);
+  const int R0 = static_cast<int>(wid / p.strips) * p.ty;
+  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * cols<NC>();
+  march_tile<T, NC, FCT, NUG, IGA, KAHAN>(p, strip, R0, ring, lane);
+}
+
+// Ensemble of fields: a persistent grid walks a table of (field, strip, row tile) items.
+template <typename T>
+struct BatchParams {
+  const T* psi;
+  T* out;
+  const T* gc0;
+  const T* gc1;
+  const T* G;
+  const T* R;
+  const BatchField* fields;
+  const int* item_field;  // field of every work item
+  int n_items, ty;
+  T dt, scale;
+  int rhs_a, rhs_b, vec_ok;
+};
+
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+__global__ void __launch_bounds__(kWarps * 32) k_fused2d_batched(const BatchParams<T> b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * cols<NC>();
+  const int total = gridDim.x * kWarps;
+  for (int item = blockIdx.x * kWarps + wib; item < b.n_items; item += total) {
+    const BatchField fd = b.fields[b.item_field[item]];
+    const int local = item - fd.item_base;
+    F2Params<T> p;
+    p.psi = b.psi + fd.offset;
+    p.out = b.out + fd.offset;
+    p.gc0 = b.gc0 + fd.offset;
+    p.gc1 = b.gc1 + fd.offset;
+    p.G = NUG ? b.G + fd.offset : nullptr;
+    p.R = b.R ? b.R + fd.offset : nullptr;
+    p.n0 = fd.n0;
+    p.n1 = fd.n1;
+    p.strips = fd.strips;
+    p.rowtiles = 0;
+    p.ty = b.ty;
+    p.dt = b.dt;
+    p.scale = b.scale;
+    p.rhs_a = b.rhs_a;
+    p.rhs_b = b.rhs_b;
+    p.vec = fd.vec && b.vec_ok;
+    march_tile<T, NC, FCT, NUG, IGA, KAHAN>(p, local % fd.strips, (local / fd.strips) * b.ty, ring, lane);
+  }
+}
+
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 void launch(const F2Params<T>& p, cudaStream_t st) {
   const long long warps = static_cast<long long>(p.strips) * p.rowtiles;
   const unsigned blocks = static_cast<unsigned>((warps + kWarps - 1) / kWarps);
@@ -453,6 +508,80 @@ void launch_all(const F2Params<T>& p, const Opts& o, cudaStream_t st) {
 
 bool al(const void* q, size_t a) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) % a) == 0; }
 
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+void launch_b(const BatchParams<T>& b, cudaStream_t st) {
+  const size_t smem = static_cast<size_t>(kWarps) * kSlots * kArr * cols<NC>() * sizeof(T);
+  static int grid = 0;  // persistent grid: every block that fits on the GPU at once
+  if (grid == 0) {
+    cudaFuncSetAttribute(k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN>,
+                                                  kWarps * 32, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  const int need = (b.n_items + kWarps - 1) / kWarps;
+  k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN><<<need < grid ? need : grid, kWarps * 32, smem, st>>>(b);
+}
+
+template <typename T, int NC, bool FCT, bool NUG>
+void launch_b_mode(const BatchParams<T>& b, bool iga, bool kahan, cudaStream_t st) {
+  if (iga) {
+    if (kahan) launch_b<T, NC, FCT, NUG, true, true>(b, st); else launch_b<T, NC, FCT, NUG, true, false>(b, st);
+  } else {
+    if (kahan) launch_b<T, NC, FCT, NUG, false, true>(b, st); else launch_b<T, NC, FCT, NUG, false, false>(b, st);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+int fused_batched_columns() { return sizeof(T) == 4 ? 4 : 2; }
+template int fused_batched_columns<float>();
+template int fused_batched_columns<double>();
+
+int fused_strip_stride(int nc) { return 32 * nc - 2 * kLead; }
+
+template <typename T>
+int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
+                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st) {
+  if (o.n_iters != 2 || o.tot) return MPDATA_EUNSUPPORTED;
+  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
+  BatchParams<T> b;
+  b.psi = psi_in;
+  b.out = psi_out;
+  b.gc0 = gc0;
+  b.gc1 = gc1;
+  b.G = o.nug ? G : nullptr;
+  b.R = R;
+  b.fields = tab.fields;
+  b.item_field = tab.item_field;
+  b.n_items = tab.n_items;
+  b.ty = tab.ty;
+  b.dt = dt;
+  b.scale = scale;
+  b.rhs_a = o.rhs_a;
+  b.rhs_b = o.rhs_b;
+  const size_t va = NC * sizeof(T) <= 16 ? NC * sizeof(T) : 16;
+  b.vec_ok = al(psi_in, va) && al(psi_out, va) && al(gc0, va) && al(gc1, va) && al(b.G, va) && al(R, va);
+  if (o.fct) {
+    if (o.nug) launch_b_mode<T, NC, true, true>(b, o.iga, o.kahan, st);
+    else launch_b_mode<T, NC, true, false>(b, o.iga, o.kahan, st);
+  } else {
+    if (o.nug) launch_b_mode<T, NC, false, true>(b, o.iga, o.kahan, st);
+    else launch_b_mode<T, NC, false, false>(b, o.iga, o.kahan, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+template int fused_batched_step<float>(const BatchTable&, const Opts&, const float*, float*, const float*,
+                                       const float*, const float*, const float*, float, float, cudaStream_t);
+template int fused_batched_step<double>(const BatchTable&, const Opts&, const double*, double*, const double*,
+                                        const double*, const double*, const double*, double, double, cudaStream_t);
+
+namespace {
 }  // namespace
 
 template <typename T>

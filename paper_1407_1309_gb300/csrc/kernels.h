@@ -25,6 +25,23 @@ uint32_t handle_opts(const mpdata_s* h);
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 
+// Work table of the batched fused kernel: one item per (field, strip, row tile).
+struct BatchField {
+  long long offset;  // first cell of the field in the concatenated arrays
+  int n0, n1, strips, item_base, vec;
+};
+struct BatchTable {
+  BatchField* fields;  // device
+  int* item_field;     // device, field of every item
+  int n_items, ty;
+};
+template <typename T>
+int fused_batched_columns();
+int fused_strip_stride(int nc);
+template <typename T>
+int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
+                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st);
+
 // One step of all fields of a batched handle in one persistent launch
 // (batched.cu); MPDATA_EUNSUPPORTED when not covered.
 template <typename T>

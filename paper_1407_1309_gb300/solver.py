@@ -54,6 +54,31 @@ class Mpdata:
         capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
         return psi_bar
 
+    def set_stream(self, stream):
+        """Send later work of the handle to `stream` (a torch.cuda.Stream)."""
+        capi.mpdata_set_stream(self.h, stream)
+        self.stream = stream
+
+    def capture(self, psi_in, psi_out, gc, n_steps, g=None, r=None, dt=0.0, gc_scale=None):
+        """Capture `n_steps` steps (psi_in -> psi_out) into a torch.cuda.CUDAGraph; replaying
+        the graph re-runs them with whatever the captured buffers hold at that time.  One
+        un-captured step is run first so that every one-time set-up happens outside the capture."""
+        prev = self.stream
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        self.set_stream(side)
+        try:
+            scratch = torch.empty_like(psi_out)
+            with torch.cuda.stream(side):
+                self.advance(psi_in, scratch, gc, g, r, dt, 1)
+            side.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                self.advance(psi_in, psi_out, gc, g, r, dt, n_steps, gc_scale)
+        finally:
+            self.set_stream(prev)
+        return graph
+
     # -- FP64 reductions --------------------------------------------------------------
     def mass(self, psi, g=None):
         m = capi.mpdata_reduce(self.h, psi, g, len(self.shapes))

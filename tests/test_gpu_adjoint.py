@@ -9,7 +9,9 @@ the step only piecewise smooth (min/max switches), so over many steps a
 perturbation of 1e-3, or even 1e-6 on a coarse grid, crosses switches somewhere in
 the field and the difference quotient itself is off; with FCT the check therefore
 uses eps = 1e-7 in FP64 (where the quotient has converged to the adjoint
-gradient), and eps = 1e-3 for the smooth scheme without the limiter.
+gradient), and eps = 1e-4 for the smooth scheme without the limiter (at 1e-3 the
+O(eps^2) truncation of the quotient reaches ~2e-4 on directions with a small
+derivative).
 """
 import numpy as np
 import pytest
@@ -132,9 +134,9 @@ def test_autograd_gradient_matches_finite_differences_small():
     assert max(errs) <= 1e-4, errs
 
 
-def test_autograd_gradient_smooth_scheme_eps_1e3():
-    """Without the limiter the step is smooth and eps = 1e-3 suffices."""
-    errs = fd_check(48, 24, 5, 6, eps=1e-3, opts=0)
+def test_autograd_gradient_smooth_scheme():
+    """Without the limiter the step is smooth and a much larger eps agrees."""
+    errs = fd_check(48, 24, 5, 6, eps=1e-4, opts=0)
     assert max(errs) <= 1e-4, errs
 
 
