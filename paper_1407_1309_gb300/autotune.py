@@ -1,0 +1,97 @@
+"""Autotuner: picks the tile height of the fused kernels for a handle by timing
+candidates on the caller's own buffers, and remembers the choice in a JSON cache
+keyed by device, field shapes, element type, passes and options.
+
+The cache lives in $MPDATA_GB300_TUNE_CACHE, else
+$XDG_CACHE_HOME/mpdata_gb300/autotune.json (~/.cache/... by default).
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from . import capi
+
+CANDIDATES = (0, 6, 8, 12, 16, 24, 32, 48, 64)
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    p = os.environ.get("MPDATA_GB300_TUNE_CACHE")
+    if p:
+        return p
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "mpdata_gb300", "autotune.json")
+
+
+def _load_cache() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(cache: dict) -> None:
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def key_of(solver) -> str:
+    name = torch.cuda.get_device_name(solver.device)
+    shapes = ";".join("x".join(map(str, s)) for s in solver.shapes[:8])
+    if len(solver.shapes) > 8:
+        shapes += f";+{len(solver.shapes) - 8}fields:{solver.total}"
+    return f"{name}|{shapes}|{solver.dtype}|n_iters={solver.n_iters}|opts={solver.opts}"
+
+
+def time_steps(solver, psi, gc, g=None, r=None, dt=0.0, steps=20, flush_bytes=256 << 20):
+    """Seconds per step, each step timed with CUDA events after an L2 flush."""
+    dev = solver.device
+    a, b = psi.clone(), torch.empty_like(psi)
+    flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev) if flush_bytes else None
+    solver.advance(a, b, gc, g, r, dt, 2)
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream(dev))
+        solver.advance(a, b, gc, g, r, dt, 1)
+        e1.record(torch.cuda.current_stream(dev))
+        a, b = b, a
+        torch.cuda.synchronize(dev)
+        total += e0.elapsed_time(e1) / 1e3
+    return total / steps
+
+
+def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, steps=20, use_cache=True,
+             flush_bytes=256 << 20):
+    """Choose MPDATA_TUNE_TILE_ROWS for `solver` (an Mpdata handle); returns (tile_rows, seconds per
+    step, {candidate: seconds}).  The handle is left tuned to the winner."""
+    key = key_of(solver)
+    if use_cache:
+        with _lock:
+            hit = _load_cache().get(key)
+        if hit is not None:
+            solver.tune(capi.TUNE_TILE_ROWS, int(hit["tile_rows"]))
+            return int(hit["tile_rows"]), float(hit["seconds_per_step"]), {}
+    timings = {}
+    for c in candidates:
+        solver.tune(capi.TUNE_TILE_ROWS, c)
+        timings[c] = time_steps(solver, psi, gc, g, r, dt, steps, flush_bytes)
+    best = min(timings, key=timings.get)
+    solver.tune(capi.TUNE_TILE_ROWS, best)
+    if use_cache:
+        with _lock:
+            cache = _load_cache()
+            cache[key] = {"tile_rows": int(best), "seconds_per_step": timings[best]}
+            _store_cache(cache)
+    return best, timings[best], timings

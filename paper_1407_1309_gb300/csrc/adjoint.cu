@@ -34,34 +34,60 @@ template <typename T> struct P3 { const T* p[3]; };
 template <typename T> struct W3 { T* p[3]; };
 
 struct Coord { int c[3]; };
-__device__ __forceinline__ Coord coord_of(const Grid& g, long long i) {
-  Coord x;
-  x.c[2] = static_cast<int>(i % g.n[2]);
-  const long long r = i / g.n[2];
-  x.c[1] = static_cast<int>(r % g.n[1]);
-  x.c[0] = static_cast<int>(r / g.n[1]);
-  return x;
-}
 __device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
   return (static_cast<long long>(x.c[0]) * g.n[1] + x.c[1]) * g.n[2] + x.c[2];
 }
 template <int ND>
 __device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
   const int a = 3 - ND + d;
-  int v = (x.c[a] + s) % g.n[a];
-  if (v < 0) v += g.n[a];
+  const int n = g.n[a];
+  int v = x.c[a] + s;
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
   x.c[a] = v;
   return x;
 }
+inline dim3 cell_grid(const Grid& g, int bs) {
+  return dim3(static_cast<unsigned>((g.n[2] + bs - 1) / bs), static_cast<unsigned>(g.n[1] < 65535 ? g.n[1] : 65535),
+              static_cast<unsigned>(g.n[0] < 65535 ? g.n[0] : 65535));
+}
+
+// Linear index of a cell and the index offsets of its periodic neighbours (s = -2..2 along d);
+// a diagonal neighbour is the sum of two offsets.
+template <int ND>
+struct Nbr {
+  long long i;
+  long long off[ND][5];
+  __device__ __forceinline__ Nbr(const Grid& g, const Coord& x) {
+    i = lin(g, x);
+    long long stride = 1;
+#pragma unroll
+    for (int a = 2; a >= 0; --a) {
+      const int d = a - (3 - ND);
+      if (d >= 0) {
+#pragma unroll
+        for (int s = -2; s <= 2; ++s) off[d][s + 2] = (sh<ND>(g, x, d, s).c[a] - x.c[a]) * stride;
+      }
+      stride *= g.n[a];
+    }
+  }
+  __device__ __forceinline__ long long at(int d, int s) const { return i + off[d][s + 2]; }
+  __device__ __forceinline__ long long at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
+};
 
 template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit) {
   return unit ? V : posp(V) * L + negp(V) * R;
 }
 
-#define CELL_INDEX                                                              \
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; \
-  if (i >= g.N) return;                                                         \
-  const Coord x = coord_of(g, i);
+// loop over the cells on a (fast, middle, slow) launch grid; closed by CELL_END
+#define CELL_INDEX                                                                    \
+  for (int c0_ = blockIdx.z; c0_ < g.n[0]; c0_ += gridDim.z)                            \
+    for (int c1_ = blockIdx.y; c1_ < g.n[1]; c1_ += gridDim.y)                          \
+      for (int c2_ = blockIdx.x * blockDim.x + threadIdx.x; c2_ < g.n[2];               \
+           c2_ += gridDim.x * blockDim.x) {                                           \
+        const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});                                   \
+        const long long i = nb.i;
+#define CELL_END }
 
 // Reverse of the donor-cell pass k, psi_k = psi_{k-1} + sum_d (F_{i-e_d} - F_i)/G_i with
 // F = flux(psi_{k-1}, V^k): pb_prev += dL/dpsi_{k-1}, vhb[d] += dL/dV^k.
@@ -73,7 +99,7 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
   T acc = pb[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1)), im = lin(g, sh<ND>(g, x, d, -1));
+    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
     const T gp = G ? pb[ip] / G[ip] : pb[ip];
     const T gm = G ? pb[im] / G[im] : pb[im];
     const T fp = gp - gi;  // dL/dF on the face (d, i)
@@ -87,6 +113,7 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
     vhb.p[d][i] += fp * dv;
   }
   pb_prev[i] += acc;
+  CELL_END
 }
 
 // Reverse of the limiter V^ = V m, m = min(1, a, b) (a, b the factors the forward chose).
@@ -96,7 +123,7 @@ __global__ void ka_limit(Grid g, P3<T> vhb, P3<T> V, const T* __restrict__ psi, 
   CELL_INDEX
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const long long ip = nb.at(d, +1);
     const T v = V.p[d][i];
     const T F = flux(psi[i], psi[ip], v, unit);
     const bool right = F > T(0) || (F == T(0) && v > T(0));
@@ -111,6 +138,7 @@ __global__ void ka_limit(Grid g, P3<T> vhb, P3<T> V, const T* __restrict__ psi, 
     if (sel == 1) atomicAdd(right ? &bdb[i] : &bub[i], gq * v);
     if (sel == 2) atomicAdd(right ? &bub[ip] : &bdb[ip], gq * v);
   }
+  CELL_END
 }
 
 // Reverse of the FCT factors beta_up = G[mx - psi]+/in, beta_dn = G[psi - mn]+/out (1 when the
@@ -127,8 +155,8 @@ __global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__
   T in = T(0), ou = T(0);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1));
-    im[d] = lin(g, sh<ND>(g, x, d, -1));
+    const long long ip = nb.at(d, +1);
+    im[d] = nb.at(d, -1);
     Fp[d] = flux(p, psi[ip], V.p[d][i], unit);
     Fm[d] = flux(psi[im[d]], p, V.p[d][im[d]], unit);
     in = in + (posp(Fm[d]) - negp(Fp[d]));
@@ -159,6 +187,7 @@ __global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__
     }
   }
   pb[i] += pacc;
+  CELL_END
 }
 
 // Reverse of the unlimited fluxes F = flux(psi_{k-1}, V^k) that fed the FCT factors.
@@ -169,7 +198,7 @@ __global__ void ka_flux_u(Grid g, P3<T> fb, const T* __restrict__ psi, P3<T> V, 
   T acc = T(0);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1)), im = lin(g, sh<ND>(g, x, d, -1));
+    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
     const T fp = fb.p[d][i], fm = fb.p[d][im];
     const T v = V.p[d][i], vm = V.p[d][im];
     T dv = T(1);
@@ -180,6 +209,7 @@ __global__ void ka_flux_u(Grid g, P3<T> fb, const T* __restrict__ psi, P3<T> V, 
     vb.p[d][i] += fp * dv;
   }
   pb[i] += acc;
+  CELL_END
 }
 
 // Reverse of the antidiffusive advector (Eq. 6 with the multi-D cross terms):
@@ -193,8 +223,7 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
   for (int d = 0; d < ND; ++d) {
     const T gout = vb.p[d][i];
     if (gout == T(0)) continue;
-    const Coord xd = sh<ND>(g, x, d, +1);
-    const long long ip = lin(g, xd);
+    const long long ip = nb.at(d, +1);
     const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
     const T V = Vin.p[d][i];
     const T p0 = psi[i], p1 = psi[ip];
@@ -216,9 +245,8 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
       if (q == d) continue;
-      const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
-      const long long iqp = lin(g, xp), idqp = lin(g, sh<ND>(g, xp, d, +1));
-      const long long iqm = lin(g, xm), idqm = lin(g, sh<ND>(g, xm, d, +1));
+      const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
+      const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
       const T* Q = Vin.p[q];
       const T Vq = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
       const T Tp = psi[iqp] + psi[idqp], Bt = psi[iqm] + psi[idqm];
@@ -247,6 +275,7 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
     }
     atomicAdd(&vhb.p[d][i], gV);
   }
+  CELL_END
 }
 
 // Reverse of the FCT bounds: the adjoint of each extremum goes to its first extremal candidate
@@ -260,8 +289,8 @@ __global__ void ka_bounds(Grid g, const T* __restrict__ mxb, const T* __restrict
   loc[nl++] = i;
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    loc[nl++] = lin(g, sh<ND>(g, x, d, -1));
-    loc[nl++] = lin(g, sh<ND>(g, x, d, +1));
+    loc[nl++] = nb.at(d, -1);
+    loc[nl++] = nb.at(d, +1);
   }
   T hi = p0[i], lo = p0[i];
   int ha = 0, la = 0;
@@ -275,6 +304,7 @@ __global__ void ka_bounds(Grid g, const T* __restrict__ mxb, const T* __restrict
   }
   if (mxb[i] != T(0)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], mxb[i]);
   if (mnb[i] != T(0)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], mnb[i]);
+  CELL_END
 }
 
 template <typename T>
@@ -365,7 +395,7 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     const T* pbk = (k == K) ? psi_bar : pbl[k];
     P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
     W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
-    ka_donor_flux<T, ND><<<nb, bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1], vhbk);
+    ka_donor_flux<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1], vhbk);
     P3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
     if (o.fct) {
@@ -375,24 +405,24 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       for (int d = 0; d < D; ++d) cudaMemsetAsync(fb[d], 0, nz, st);
       P3<T> vhbr{{vhb[k][0], vhb[k][1], vhb[k][2]}};
       W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
-      ka_limit<T, ND><<<nb, bs, 0, st>>>(g, vhbr, vu, tp.psi[k - 1], o.iga, tp.bu[k], tp.bd[k], vbw, bub, bdb);
+      ka_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, vhbr, vu, tp.psi[k - 1], o.iga, tp.bu[k], tp.bd[k], vbw, bub, bdb);
       W3<T> fbw{{fb[0], fb[1], fb[2]}};
-      ka_beta<T, ND><<<nb, bs, 0, st>>>(g, bub, bdb, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, fbw, pbl[k - 1],
+      ka_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, bub, bdb, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, fbw, pbl[k - 1],
                                         mxb, mnb);
       P3<T> fbr{{fb[0], fb[1], fb[2]}};
-      ka_flux_u<T, ND><<<nb, bs, 0, st>>>(g, fbr, tp.psi[k - 1], vu, o.iga, pbl[k - 1], vbw);
+      ka_flux_u<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, fbr, tp.psi[k - 1], vu, o.iga, pbl[k - 1], vbw);
       gv = P3<T>{{vbk[k][0], vbk[k][1], vbk[k][2]}};
     }
     P3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     W3<T> vhbp{{vhb[k - 1][0], vhb[k - 1][1], vhb[k - 1][2]}};
-    ka_antidiff<T, ND><<<nb, bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
+    ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
   }
-  if (o.fct && K >= 2) ka_bounds<T, ND><<<nb, bs, 0, st>>>(g, mxb, mnb, tp.psi[0], tp.psi[1], pbl[0], pbl[1]);
+  if (o.fct && K >= 2) ka_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, mxb, mnb, tp.psi[0], tp.psi[1], pbl[0], pbl[1]);
   {
     const T* pb1 = (K == 1) ? psi_bar : pbl[1];
     P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
     W3<T> vhb1{{vhb[1][0], vhb[1][1], vhb[1][2]}};
-    ka_donor_flux<T, ND><<<nb, bs, 0, st>>>(g, pb1, tp.psi[0], v1, G, false, pbl[0], vhb1);
+    ka_donor_flux<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pb1, tp.psi[0], v1, G, false, pbl[0], vhb1);
   }
   if (cudaMemcpyAsync(psi_bar, pbl[0], static_cast<size_t>(N) * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return MPDATA_ECUDA;

@@ -30,15 +30,6 @@ template <typename T> struct Out3 { T* p[3]; };
 
 struct Coord { int c[3]; };
 
-template <int ND>
-__device__ __forceinline__ Coord coord_of(const Grid& g, long long i) {
-  Coord x;
-  x.c[2] = static_cast<int>(i % g.n[2]);
-  long long r = i / g.n[2];
-  x.c[1] = static_cast<int>(r % g.n[1]);
-  x.c[0] = static_cast<int>(r / g.n[1]);
-  return x;
-}
 __device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
   return (static_cast<long long>(x.c[0]) * g.n[1] + x.c[1]) * g.n[2] + x.c[2];
 }
@@ -46,11 +37,52 @@ __device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
 template <int ND>
 __device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
   const int a = 3 - ND + d;
-  int v = (x.c[a] + s) % g.n[a];
-  if (v < 0) v += g.n[a];
+  const int n = g.n[a];
+  int v = x.c[a] + s;  // |s| <= 2: at most one wrap unless the extent is tiny
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
   x.c[a] = v;
   return x;
 }
+
+// Loop over the cells of a field launched on a (fast, middle, slow) grid: coordinates come
+// from the block indices, so no division is needed.
+#define FOR_CELLS(g)                                                                  \
+  for (int c0_ = blockIdx.z; c0_ < (g).n[0]; c0_ += gridDim.z)                          \
+    for (int c1_ = blockIdx.y; c1_ < (g).n[1]; c1_ += gridDim.y)                        \
+      for (int c2_ = blockIdx.x * blockDim.x + threadIdx.x; c2_ < (g).n[2];             \
+           c2_ += gridDim.x * blockDim.x)
+
+inline dim3 cell_grid(const Grid& g, int bs) {
+  const unsigned gx = static_cast<unsigned>((g.n[2] + bs - 1) / bs);
+  const unsigned gy = static_cast<unsigned>(g.n[1] < 65535 ? g.n[1] : 65535);
+  const unsigned gz = static_cast<unsigned>(g.n[0] < 65535 ? g.n[0] : 65535);
+  return dim3(gx, gy, gz);
+}
+
+// Linear index of a cell and the index offsets of its periodic neighbours: off[d][s+2]
+// moves s = -2..2 cells along dimension d.  Shifts along different dimensions wrap
+// independently, so a diagonal neighbour is the sum of two offsets.
+template <int ND>
+struct Nbr {
+  long long i;
+  long long off[ND][5];
+  __device__ __forceinline__ Nbr(const Grid& g, const Coord& x) {
+    i = lin(g, x);
+    long long stride = 1;
+#pragma unroll
+    for (int a = 2; a >= 0; --a) {
+      const int d = a - (3 - ND);
+      if (d >= 0) {
+#pragma unroll
+        for (int s = -2; s <= 2; ++s) off[d][s + 2] = (sh<ND>(g, x, d, s).c[a] - x.c[a]) * stride;
+      }
+      stride *= g.n[a];
+    }
+  }
+  __device__ __forceinline__ long long at(int d, int s) const { return i + off[d][s + 2]; }
+  __device__ __forceinline__ long long at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
+};
 
 // donor-cell flux of Eq. 5 in advector units; psi -> 1 under infinite gauge
 template <typename T>
@@ -71,16 +103,16 @@ template <typename T, int ND>
 __global__ void k_donor(Grid g, const T* __restrict__ psi, In3<T> V, T vscale, bool unit,
                         const T* __restrict__ G, bool kahan, const T* __restrict__ R, T dt,
                         bool post, T* __restrict__ out) {
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= g.N) return;
-  const Coord x = coord_of<ND>(g, i);
+  FOR_CELLS(g) {
+  const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
+  const long long i = nb.i;
   const T p = psi[i];
   T s = p, comp = T(0);
   const T Gi = G ? G[i] : T(1);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1));
-    const long long im = lin(g, sh<ND>(g, x, d, -1));
+    const long long ip = nb.at(d, +1);
+    const long long im = nb.at(d, -1);
     const T vp = V.p[d][i] * vscale, vm = V.p[d][im] * vscale;
     const T Fp = flux(p, psi[ip], vp, unit);
     const T Fm = flux(psi[im], p, vm, unit);
@@ -102,22 +134,23 @@ __global__ void k_donor(Grid g, const T* __restrict__ psi, In3<T> V, T vscale, b
   }
   if (post) s = s + dt * R[i];
   out[i] = s;
+  }
 }
 
 // FCT bounds (Sect. 3.1.4): extrema of psi0 and psi1 over the cell and its face neighbours.
 template <typename T, int ND>
 __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__ p1,
                          T* __restrict__ mx, T* __restrict__ mn) {
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= g.N) return;
-  const Coord x = coord_of<ND>(g, i);
+  FOR_CELLS(g) {
+  const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
+  const long long i = nb.i;
   T hi = p0[i] > p1[i] ? p0[i] : p1[i];
   T lo = p0[i] < p1[i] ? p0[i] : p1[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
 #pragma unroll
     for (int s = -1; s <= 1; s += 2) {
-      const long long j = lin(g, sh<ND>(g, x, d, s));
+      const long long j = nb.at(d, s);
       const T a = p0[j], b = p1[j];
       hi = a > hi ? a : hi;
       hi = b > hi ? b : hi;
@@ -127,6 +160,7 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
   }
   mx[i] = hi;
   mn[i] = lo;
+  }
 }
 
 // Antidiffusive pseudo-advector of pass k at every face i+1/2 of cell i (Eq. 6 with the
@@ -138,14 +172,13 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
 template <typename T, int ND>
 __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vscale,
                            const T* __restrict__ G, bool iga, bool tot, Out3<T> Vout) {
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= g.N) return;
-  const Coord x = coord_of<ND>(g, i);
+  FOR_CELLS(g) {
+  const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
+  const long long i = nb.i;
   const T p0 = psi[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const Coord xd = sh<ND>(g, x, d, +1);
-    const long long ip = lin(g, xd);
+    const long long ip = nb.at(d, +1);
     const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
     const T V = Vin.p[d][i] * vscale;
     const T p1 = psi[ip];
@@ -155,9 +188,8 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
       if (q == d) continue;
-      const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
-      const long long iqp = lin(g, xp), idqp = lin(g, sh<ND>(g, xp, d, +1));
-      const long long iqm = lin(g, xm), idqm = lin(g, sh<ND>(g, xm, d, +1));
+      const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
+      const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
       const T* Q = Vin.p[q];
       Vq[q] = T(0.25) * ((Q[i] * vscale + Q[ip] * vscale) + (Q[iqm] * vscale + Q[idqm] * vscale));
       const T Tp = psi[iqp] + psi[idqp];
@@ -166,8 +198,8 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       out = out - T(0.5) * V * Vq[q] / Gb * B;
     }
     if (tot) {
-      const T pm = psi[lin(g, sh<ND>(g, x, d, -1))];
-      const T p2 = psi[lin(g, sh<ND>(g, xd, d, +1))];
+      const T pm = psi[nb.at(d, -1)];
+      const T p2 = psi[nb.at(d, +2)];
       const T num = ((p2 - p1) - p0) + pm;
       const T D = iga ? num * T(0.25) : fracg(num, ((p2 + p1) + p0) + pm);
       out = out + ((T(3) * V * absv(V)) / Gb - (T(2) * V * V * V) / (Gb * Gb) - V) / T(3) * D;
@@ -176,9 +208,8 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       for (int q = 0; q < ND; ++q) {
         if (q == d) continue;
         qs[nq++] = q;
-        const Coord xp = sh<ND>(g, x, q, +1), xm = sh<ND>(g, x, q, -1);
-        const T a = psi[lin(g, xp)], b = psi[lin(g, sh<ND>(g, xp, d, +1))];
-        const T e = psi[lin(g, xm)], f = psi[lin(g, sh<ND>(g, xm, d, +1))];
+        const T a = psi[nb.at(q, +1)], b = psi[nb.at2(q, +1, d, +1)];
+        const T e = psi[nb.at(q, -1)], f = psi[nb.at2(q, -1, d, +1)];
         const T n2 = (b - a) - (f - e);
         const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
         out = out + absv(V) * Vq[q] / Gb * (T(1) - T(2) * absv(V) / Gb) * D2;
@@ -190,8 +221,8 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
         for (int s1 = 1; s1 >= -1; s1 -= 2) {
 #pragma unroll
           for (int s2 = 1; s2 >= -1; s2 -= 2) {
-            const Coord y = sh<ND>(g, sh<ND>(g, x, qs[0], s1), qs[1], s2);
-            pr[m++] = psi[lin(g, y)] + psi[lin(g, sh<ND>(g, y, d, +1))];
+            const long long y = nb.i + nb.off[qs[0]][s1 + 2] + nb.off[qs[1]][s2 + 2];
+            pr[m++] = psi[y] + psi[y + nb.off[d][3]];
           }
         }
         // pr = {(+,+), (+,-), (-,+), (-,-)}
@@ -202,6 +233,7 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
     }
     Vout.p[d][i] = out;
   }
+  }
 }
 
 // FCT limiting factors (Sect. 3.1.4): in/out sums of the unlimited fluxes and
@@ -210,15 +242,15 @@ template <typename T, int ND>
 __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __restrict__ G, bool unit,
                        const T* __restrict__ mx, const T* __restrict__ mn, T* __restrict__ bu,
                        T* __restrict__ bd) {
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= g.N) return;
-  const Coord x = coord_of<ND>(g, i);
+  FOR_CELLS(g) {
+  const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
+  const long long i = nb.i;
   const T p = psi[i];
   T in = T(0), out = T(0);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1));
-    const long long im = lin(g, sh<ND>(g, x, d, -1));
+    const long long ip = nb.at(d, +1);
+    const long long im = nb.at(d, -1);
     const T Fp = flux(p, psi[ip], V.p[d][i], unit);
     const T Fm = flux(psi[im], p, V.p[d][im], unit);
     in = in + (posp(Fm) - negp(Fp));
@@ -227,6 +259,7 @@ __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __r
   const T Gi = G ? G[i] : T(1);
   bu[i] = in > T(0) ? Gi * posp(mx[i] - p) / in : T(1);
   bd[i] = out > T(0) ? Gi * posp(p - mn[i]) / out : T(1);
+  }
 }
 
 // Limited advector: V min(1, beta_dn_i, beta_up_{i+e_d}) if the unlimited flux leaves
@@ -234,13 +267,13 @@ __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __r
 template <typename T, int ND>
 __global__ void k_limit(Grid g, const T* __restrict__ psi, In3<T> Vu, bool unit,
                         const T* __restrict__ bu, const T* __restrict__ bd, Out3<T> Vout) {
-  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (i >= g.N) return;
-  const Coord x = coord_of<ND>(g, i);
+  FOR_CELLS(g) {
+  const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
+  const long long i = nb.i;
   const T p = psi[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = lin(g, sh<ND>(g, x, d, +1));
+    const long long ip = nb.at(d, +1);
     const T V = Vu.p[d][i];
     const T F = flux(p, psi[ip], V, unit);
     const bool right = F > T(0) || (F == T(0) && V > T(0));
@@ -250,6 +283,7 @@ __global__ void k_limit(Grid g, const T* __restrict__ psi, In3<T> Vu, bool unit,
     if (a < m) m = a;
     if (b < m) m = b;
     Vout.p[d][i] = V * m;
+  }
   }
 }
 
@@ -269,30 +303,30 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   // pass 1
   const bool inplace1 = (a.psi_out == a.psi_in) && !o.rhs_b;
   T* dst1 = (K == 1 && !inplace1) ? a.psi_out : s.pa;
-  k_donor<T, ND><<<nb, bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
+  k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
                                     K == 1 && o.rhs_a, dst1);
   if (K == 1) {
     if (dst1 != a.psi_out)
       return cudaMemcpyAsync(a.psi_out, dst1, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st);
     return cudaGetLastError();
   }
-  if (o.fct) k_bounds<T, ND><<<nb, bs, 0, st>>>(g, p0, s.pa, s.mx, s.mn);
+  if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, s.pa, s.mx, s.mn);
   const T* prev = s.pa;
   In3<T> vprev = gc;
   T vscale = a.gc_scale;
   for (int k = 2; k <= K; ++k) {
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
-    k_antidiff<T, ND><<<nb, bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+    k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
     if (o.fct) {
-      k_beta<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, G, o.iga, s.mx, s.mn, s.bu, s.bd);
+      k_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vuse, G, o.iga, s.mx, s.mn, s.bu, s.bd);
       Out3<T> vl{{lim[0], lim[1], lim[2]}};
-      k_limit<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, o.iga, s.bu, s.bd, vl);
+      k_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vuse, o.iga, s.bu, s.bd, vl);
       vuse = In3<T>{{lim[0], lim[1], lim[2]}};
     }
     T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
-    k_donor<T, ND><<<nb, bs, 0, st>>>(g, prev, vuse, T(1), o.iga, G, o.kahan, a.r, a.dt,
+    k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vuse, T(1), o.iga, G, o.kahan, a.r, a.dt,
                                       k == K && o.rhs_a, dst);
     prev = dst;
     vprev = vuse;
@@ -309,22 +343,22 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
   const int K = o.n_iters;
   In3<T> v1{{gc[0], gc[1], gc[2]}};
   if (K >= 2) {
-    k_donor<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, levels[1]);
-    if (o.fct) k_bounds<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
+    k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, levels[1]);
+    if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
   }
   for (int k = 2; k <= K; ++k) {
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
-    k_antidiff<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
+    k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
     In3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (o.fct) {
-      k_beta<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, tp.bu[k], tp.bd[k]);
+      k_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, tp.bu[k], tp.bd[k]);
       Out3<T> vl{{const_cast<T*>(tp.vh[k][0]), const_cast<T*>(tp.vh[k][1]), const_cast<T*>(tp.vh[k][2])}};
-      k_limit<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vu, o.iga, tp.bu[k], tp.bd[k], vl);
+      k_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vu, o.iga, tp.bu[k], tp.bd[k], vl);
     }
     if (k < K) {
       In3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
-      k_donor<T, ND><<<nb, bs, 0, st>>>(g, tp.psi[k - 1], vh, T(1), o.iga, G, o.kahan, nullptr, T(0), false,
+      k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vh, T(1), o.iga, G, o.kahan, nullptr, T(0), false,
                                         levels[k]);
     }
   }

@@ -1,0 +1,53 @@
+"""Autotuner: cache round trip (host only) and a GPU run that keeps results unchanged."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1407_1309_gb300 import autotune, capi, workloads
+
+
+class FakeSolver:
+    def __init__(self):
+        self.device = torch.device("cpu")
+        self.shapes = [(8, 8)]
+        self.total = 64
+        self.dtype = torch.float32
+        self.n_iters = 2
+        self.opts = 1
+        self.tuned = []
+
+    def tune(self, knob, value):
+        self.tuned.append((knob, value))
+
+
+def test_cache_hit_applies_stored_tile(tmp_path, monkeypatch):
+    monkeypatch.setenv("MPDATA_GB300_TUNE_CACHE", str(tmp_path / "c.json"))
+    monkeypatch.setattr(autotune.torch.cuda, "get_device_name", lambda d=None: "fake")
+    s = FakeSolver()
+    key = autotune.key_of(s)
+    (tmp_path / "c.json").write_text(json.dumps({key: {"tile_rows": 24, "seconds_per_step": 1e-5}}))
+    best, sec, timings = autotune.autotune(s, None, None)
+    assert best == 24 and sec == 1e-5 and timings == {}
+    assert s.tuned == [(capi.TUNE_TILE_ROWS, 24)]
+
+
+@pytest.mark.gpu
+def test_autotune_picks_a_candidate_and_results_do_not_change(tmp_path, monkeypatch):
+    monkeypatch.setenv("MPDATA_GB300_TUNE_CACHE", str(tmp_path / "c.json"))
+    from paper_1407_1309_gb300.solver import Mpdata
+    psi_np, gc_np, _ = workloads.rotation_2d(256)
+    dev = torch.device("cuda")
+    psi = torch.tensor(psi_np, dtype=torch.float32, device=dev)
+    gc = [torch.tensor(v, dtype=torch.float32, device=dev) for v in gc_np]
+    with Mpdata((256, 256), dtype=torch.float32, n_iters=2, opts=capi.FCT) as m:
+        ref = torch.empty_like(psi)
+        m.advance(psi, ref, gc, n_steps=5)
+        best, sec, timings = autotune.autotune(m, psi, gc, steps=3, flush_bytes=0)
+        assert best in autotune.CANDIDATES and sec > 0 and len(timings) == len(autotune.CANDIDATES)
+        out = torch.empty_like(psi)
+        m.advance(psi, out, gc, n_steps=5)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)  # the tile height changes the schedule, not the arithmetic
+        assert json.loads((tmp_path / "c.json").read_text())[autotune.key_of(m)]["tile_rows"] == best
