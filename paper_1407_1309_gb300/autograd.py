@@ -6,7 +6,10 @@ keeping psi every `checkpoint_every` steps on the device.  Backward: for each
 segment, last first, the states inside the segment are recomputed from its
 checkpoint, then the hand-written adjoint kernels (mpdata_adjoint_step) walk
 the segment backwards, accumulating dL/dGC over all steps.  Memory is one
-field per checkpoint plus one segment of states.
+field per checkpoint plus one segment of states.  With use_graphs (default) the
+work of one segment is captured once as a CUDA graph on static buffers and
+replayed per segment, so the host issues one replay per segment instead of
+tens of launches per step.
 """
 from __future__ import annotations
 
@@ -17,10 +20,10 @@ from .solver import Mpdata
 
 class MPDATAFunction(torch.autograd.Function):
     """psi_T = MPDATA^n_steps(psi0; GC).  Use as
-    ``MPDATAFunction.apply(solver, n_steps, checkpoint_every, psi0, *gc)``."""
+    ``MPDATAFunction.apply(solver, n_steps, checkpoint_every, use_graphs, psi0, *gc)``."""
 
     @staticmethod
-    def forward(ctx, solver: Mpdata, n_steps: int, checkpoint_every: int, psi0, *gc):
+    def forward(ctx, solver: Mpdata, n_steps: int, checkpoint_every: int, use_graphs: bool, psi0, *gc):
         if n_steps < 1 or checkpoint_every < 1:
             raise ValueError("n_steps and checkpoint_every must be >= 1")
         cur = psi0.detach().contiguous().clone()
@@ -36,6 +39,7 @@ class MPDATAFunction(torch.autograd.Function):
         ctx.n_steps = n_steps
         ctx.every = checkpoint_every
         ctx.n_gc = len(gc)
+        ctx.use_graphs = use_graphs
         ctx.save_for_backward(*ckpts, *gcd)
         return cur
 
@@ -47,6 +51,19 @@ class MPDATAFunction(torch.autograd.Function):
         solver, n, every = ctx.solver, ctx.n_steps, ctx.every
         pb = grad_out.detach().contiguous().clone()
         gcb = [torch.zeros_like(g) for g in gc]
+        if ctx.use_graphs:
+            used = []
+            for seg in range(n_ck - 1, -1, -1):
+                start, end = seg * every, min(seg * every + every, n)
+                sg = _segment_graph(solver, end - start, pb, gc)
+                if sg not in used:
+                    sg.load(gc)
+                    used.append(sg)
+                sg.run(ckpts[seg], pb)
+            for sg in used:
+                for acc, b in zip(gcb, sg.gcb):
+                    acc += b
+            return (None, None, None, None, pb, *gcb)
         for seg in range(n_ck - 1, -1, -1):
             start, end = seg * every, min(seg * every + every, n)
             states = [ckpts[seg]]
@@ -56,9 +73,65 @@ class MPDATAFunction(torch.autograd.Function):
                 states.append(nxt)
             for s in range(end - 1, start - 1, -1):
                 solver.adjoint_step(states[s - start], gc, pb, gc_bar=gcb)
-        return (None, None, None, pb, *gcb)
+        return (None, None, None, None, pb, *gcb)
 
 
-def rollout(solver: Mpdata, psi0, gc, n_steps: int, checkpoint_every: int = 20):
+class _SegmentGraph:
+    """The backward work of one checkpoint segment (recompute its states, then the adjoint
+    steps last to first) captured as a CUDA graph on static buffers: the states, psi_bar,
+    the advector and its accumulated adjoint all belong to the graph."""
+
+    def __init__(self, solver: Mpdata, length: int, like, gc_like):
+        self.states = [torch.zeros_like(like) for _ in range(length)]
+        self.pb = torch.empty_like(like)
+        self.gc = [torch.zeros_like(g) for g in gc_like]
+        self.gcb = [torch.zeros_like(g) for g in gc_like]
+        gc, gcb = self.gc, self.gcb
+        dev = like.device
+        prev = solver.stream
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        solver.set_stream(side)
+        try:
+            with torch.cuda.stream(side):  # first use allocates the handle's adjoint scratch
+                tmp = torch.zeros_like(like)
+                scratch = [torch.zeros_like(g) for g in gc]
+                solver.advance(self.states[0], tmp, gc)
+                solver.adjoint_step(self.states[0], gc, tmp, gc_bar=scratch)
+            side.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=side):
+                for s in range(length - 1):
+                    solver.advance(self.states[s], self.states[s + 1], gc)
+                for s in range(length - 1, -1, -1):
+                    solver.adjoint_step(self.states[s], gc, self.pb, gc_bar=gcb)
+        finally:
+            solver.set_stream(prev)
+
+    def load(self, gc):
+        """Start a backward pass: take the advector and clear the accumulated adjoint."""
+        for dst, src in zip(self.gc, gc):
+            dst.copy_(src)
+        for b in self.gcb:
+            b.zero_()
+
+    def run(self, checkpoint, pb):
+        self.states[0].copy_(checkpoint)
+        self.pb.copy_(pb)
+        self.graph.replay()
+        pb.copy_(self.pb)
+
+
+def _segment_graph(solver: Mpdata, length: int, like, gc) -> _SegmentGraph:
+    """The captured segment of this length, kept on the handle (a rollout has at most two
+    segment lengths: checkpoint_every and the remainder)."""
+    cache = solver.__dict__.setdefault("_segment_graphs", {})
+    key = (length, like.dtype, tuple(like.shape))
+    if key not in cache:
+        cache[key] = _SegmentGraph(solver, length, like, gc)
+    return cache[key]
+
+
+def rollout(solver: Mpdata, psi0, gc, n_steps: int, checkpoint_every: int = 20, use_graphs: bool = True):
     """Differentiable n-step rollout (see MPDATAFunction)."""
-    return MPDATAFunction.apply(solver, n_steps, checkpoint_every, psi0, *gc)
+    return MPDATAFunction.apply(solver, n_steps, checkpoint_every, use_graphs, psi0, *gc)
