@@ -154,10 +154,17 @@ int mpdata_clear_stop(mpdata_t h);
 /*
  * Tuning knobs of the handle's kernels (set by the autotuner; no counterpart in
  * the paper, whose tiling is the thread decomposition over dimension 0).
- * MPDATA_TUNE_TILE_ROWS: rows each warp of the fused 2D kernel walks down
- * (0 = automatic; otherwise 4..256).  Returns EINVAL for an unknown knob or value.
+ * MPDATA_TUNE_TILE_ROWS: rows of one tile of the fused 2D kernels: the rows each
+ *   warp walks down (warp march) or the rows of one block's band (band march);
+ *   0 = automatic, otherwise 4..65536.
+ * MPDATA_TUNE_KERNEL: fused 2D kernel family for single-field 2D steps:
+ *   0 = automatic (band march on fields whose warp-march tiles would be 8 rows
+ *   high, i.e. fewer than ~1800 tiles of 16 rows; warp march otherwise),
+ *   1 = warp march, 2 = band march.  Batched
+ *   handles always use the warp march's persistent kernel.
+ * Returns EINVAL for an unknown knob or value.
  */
-enum { MPDATA_TUNE_TILE_ROWS = 1 };
+enum { MPDATA_TUNE_TILE_ROWS = 1, MPDATA_TUNE_KERNEL = 2 };
 int mpdata_tune(mpdata_t h, int knob, int value);
 
 /* Sends the handle's later work to cuda_stream (a cudaStream_t on the handle's

@@ -1,6 +1,7 @@
-"""Autotuner: picks the tile height of the fused kernels for a handle by timing
-candidates on the caller's own buffers, and remembers the choice in a JSON cache
-keyed by device, field shapes, element type, passes and options.
+"""Autotuner: picks the fused 2D kernel family (warp march or band march) and its
+tile height for a handle by timing candidates on the caller's own buffers, and
+remembers the choice in a JSON cache keyed by device, field shapes, element type,
+passes and options.
 
 The cache lives in $MPDATA_GB300_TUNE_CACHE, else
 $XDG_CACHE_HOME/mpdata_gb300/autotune.json (~/.cache/... by default).
@@ -15,7 +16,9 @@ import torch
 
 from . import capi
 
-CANDIDATES = (0, 6, 8, 12, 16, 24, 32, 48, 64)
+# (MPDATA_TUNE_KERNEL, MPDATA_TUNE_TILE_ROWS): warp-march tile heights, band heights
+CANDIDATES = tuple([(1, r) for r in (0, 6, 8, 12, 16, 24, 32, 48, 64)] +
+                   [(2, r) for r in (0, 16, 32, 64, 128, 256)])
 _lock = threading.Lock()
 
 
@@ -72,26 +75,34 @@ def time_steps(solver, psi, gc, g=None, r=None, dt=0.0, steps=20, flush_bytes=25
     return total / steps
 
 
+def _apply(solver, choice):
+    kernel, rows = choice
+    solver.tune(capi.TUNE_KERNEL, int(kernel))
+    solver.tune(capi.TUNE_TILE_ROWS, int(rows))
+
+
 def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, steps=20, use_cache=True,
              flush_bytes=256 << 20):
-    """Choose MPDATA_TUNE_TILE_ROWS for `solver` (an Mpdata handle); returns (tile_rows, seconds per
-    step, {candidate: seconds}).  The handle is left tuned to the winner."""
+    """Choose (MPDATA_TUNE_KERNEL, MPDATA_TUNE_TILE_ROWS) for `solver` (an Mpdata handle); returns
+    ((kernel, tile_rows), seconds per step, {candidate: seconds}).  The handle is left tuned to
+    the winner."""
     key = key_of(solver)
     if use_cache:
         with _lock:
             hit = _load_cache().get(key)
         if hit is not None:
-            solver.tune(capi.TUNE_TILE_ROWS, int(hit["tile_rows"]))
-            return int(hit["tile_rows"]), float(hit["seconds_per_step"]), {}
+            choice = (int(hit.get("kernel", 0)), int(hit["tile_rows"]))
+            _apply(solver, choice)
+            return choice, float(hit["seconds_per_step"]), {}
     timings = {}
     for c in candidates:
-        solver.tune(capi.TUNE_TILE_ROWS, c)
+        _apply(solver, c)
         timings[c] = time_steps(solver, psi, gc, g, r, dt, steps, flush_bytes)
     best = min(timings, key=timings.get)
-    solver.tune(capi.TUNE_TILE_ROWS, best)
+    _apply(solver, best)
     if use_cache:
         with _lock:
             cache = _load_cache()
-            cache[key] = {"tile_rows": int(best), "seconds_per_step": timings[best]}
+            cache[key] = {"kernel": int(best[0]), "tile_rows": int(best[1]), "seconds_per_step": timings[best]}
             _store_cache(cache)
     return best, timings[best], timings

@@ -25,6 +25,7 @@ EXPORTED = (
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
 )
 TUNE_TILE_ROWS = 1
+TUNE_KERNEL = 2
 
 
 class MpdataError(RuntimeError):

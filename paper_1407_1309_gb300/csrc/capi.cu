@@ -30,6 +30,7 @@ struct mpdata_s {
   int* d_status = nullptr;           // device-side error word (bounded waits)
   void* batch = nullptr;             // batched-kernel tables
   int tile_rows = 0;                 // MPDATA_TUNE_TILE_ROWS
+  int kernel = 0;                    // MPDATA_TUNE_KERNEL
   std::atomic<int> stop{0};
 };
 
@@ -53,6 +54,7 @@ int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv
                 double dt, int n_steps, const double* gc_scale) {
   mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
   o.tile_rows = h->tile_rows;
+  o.kernel = h->kernel;
   const T* gc[3] = {static_cast<const T*>(gcv[0]), h->nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
                     h->nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
   const mpd::StagedScratch<T> ss = mpd::carve_staged<T>(h->staged, h->n_max);
@@ -311,8 +313,13 @@ int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, doubl
 int mpdata_tune(mpdata_t h, int knob, int value) {
   if (!h) return MPDATA_EINVAL;
   if (knob == MPDATA_TUNE_TILE_ROWS) {
-    if (value != 0 && (value < 4 || value > 256)) return MPDATA_EINVAL;
+    if (value != 0 && (value < 4 || value > 65536)) return MPDATA_EINVAL;
     h->tile_rows = value;
+    return MPDATA_OK;
+  }
+  if (knob == MPDATA_TUNE_KERNEL) {
+    if (value < 0 || value > 2) return MPDATA_EINVAL;
+    h->kernel = value;
     return MPDATA_OK;
   }
   return MPDATA_EINVAL;

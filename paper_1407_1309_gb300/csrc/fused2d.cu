@@ -24,16 +24,18 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "stencil2d.cuh"
 
 namespace mpd {
 namespace {
+
+using namespace dev;
 
 constexpr int kLead = 4;     // computed columns left of the strip's first output column
 constexpr int kPF = 4;       // rows in flight
 constexpr int kSlots = kPF + 1;
 constexpr int kArr = 5;      // psi, gc0, gc1, G, R
 constexpr int kWarps = 4;    // warps per block
-constexpr unsigned kFull = 0xffffffffu;
 
 template <int NC> constexpr int cols() { return 32 * NC; }
 template <int NC> constexpr int stride() { return 32 * NC - 2 * kLead; }
@@ -50,88 +52,6 @@ struct F2Params {
   T dt, scale;
   int rhs_a, rhs_b, vec;
 };
-
-__device__ __forceinline__ int wrapi(int c, int n) {
-  int r = c % n;
-  return r < 0 ? r + n : r;
-}
-
-template <typename T> __device__ __forceinline__ T fdiv(T a, T b);
-template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
-template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
-
-template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
-template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
-template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
-template <typename T> __device__ __forceinline__ T maxv(T a, T b) { return a > b ? a : b; }
-template <typename T> __device__ __forceinline__ T minv(T a, T b) { return a < b ? a : b; }
-// min(1, x); a NaN x gives 1 (fmin returns the non-NaN operand)
-__device__ __forceinline__ float min1(float x) { return fminf(1.0f, x); }
-__device__ __forceinline__ double min1(double x) { return fmin(1.0, x); }
-// donor-cell flux (Eq. 5) in advector units: [V]+ L + [V]- R, one term of which is zero
-template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return V * (V > T(0) ? L : R); }
-// psi-fraction of Eq. 6 with the zero-denominator guard
-template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return d != T(0) ? fdiv(n, d) : T(0); }
-
-template <int B>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(src), "n"(B) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-template <typename T>
-__device__ __forceinline__ void kahan_add(T& s, T& comp, T t) {
-  const T y = t - comp;
-  const T u = s + y;
-  comp = (u - s) - y;
-  s = u;
-}
-
-// Donor-cell update of Eq. 4 from the four face fluxes, rG = 1/G.  The flux
-// differences are added first and psi last, so only one rounding happens at the
-// scale of psi; with the Kahan option the terms psi - Fp0 + Fm0 - Fp1 + Fm1 are
-// summed in that order with compensation instead.
-template <typename T, bool NUG, bool KAHAN>
-__device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG) {
-  if (KAHAN) {
-    if (NUG) {
-      Fp0 *= rG;
-      Fm0 *= rG;
-      Fp1 *= rG;
-      Fm1 *= rG;
-    }
-    T s = p, comp = T(0);
-    kahan_add(s, comp, -Fp0);
-    kahan_add(s, comp, Fm0);
-    kahan_add(s, comp, -Fp1);
-    kahan_add(s, comp, Fm1);
-    return s;
-  }
-  const T div = (Fm0 - Fp0) + (Fm1 - Fp1);
-  return NUG ? p + div * rG : p + div;
-}
-
-// A row of NC columns held by one lane; the columns just outside come from the
-// neighbouring lanes.
-template <typename T, int NC> __device__ __forceinline__ T from_left(const T (&a)[NC]) {
-  return __shfl_up_sync(kFull, a[NC - 1], 1);
-}
-template <typename T, int NC> __device__ __forceinline__ T from_right(const T (&a)[NC]) {
-  return __shfl_down_sync(kFull, a[0], 1);
-}
-template <typename T, int NC> __device__ __forceinline__ T left_of(const T (&a)[NC], int c, T aL) {
-  return c == 0 ? aL : a[c > 0 ? c - 1 : 0];
-}
-template <typename T, int NC> __device__ __forceinline__ T right_of(const T (&a)[NC], int c, T aR) {
-  return c == NC - 1 ? aR : a[c < NC - 1 ? c + 1 : NC - 1];
-}
-template <typename T, int N> __device__ __forceinline__ void copy_row(T (&d)[N], const T (&s)[N]) {
-#pragma unroll
-  for (int c = 0; c < N; ++c) d[c] = s[c];
-}
 
 // One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
 // row R0 down ty rows of the field described by p; `ring` is the warp's shared-memory ring.
@@ -600,14 +520,16 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   p.n0 = g.n[1];
   p.n1 = g.n[2];
   p.strips = (p.n1 + stride<NC>() - 1) / stride<NC>();
-  if (o.tile_rows > 0) {
-    p.ty = o.tile_rows;
-  } else {  // the tallest tile that still gives 12 warps per SM (152 SMs), at least 8 rows
-    p.ty = 8;
-    for (int ty : {64, 32, 16}) {
-      if (static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty) >= 152LL * 12) { p.ty = ty; break; }
-    }
+  // the tallest tile that still gives 12 warps per SM (152 SMs), at least 8 rows
+  int auto_ty = 8;
+  for (int ty : {64, 32, 16}) {
+    if (static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty) >= 152LL * 12) { auto_ty = ty; break; }
   }
+  // Fields too small for tiles taller than 8 rows lose a third of the warp march's
+  // work to each tile's 6-row ramp; there one front per block of warps (band march)
+  // is faster.
+  if (o.kernel == 2 || (o.kernel == 0 && auto_ty == 8)) return band_step<T>(g, o, a, st);
+  p.ty = o.tile_rows > 0 ? o.tile_rows : auto_ty;
   p.rowtiles = (p.n0 + p.ty - 1) / p.ty;
   p.dt = a.dt;
   p.scale = a.gc_scale;

@@ -34,7 +34,8 @@ inline Grid make_grid(int nd, const int64_t* shape) {
 struct Opts {
   bool fct, tot, iga, nug, kahan, rhs_a, rhs_b, staged;
   int n_iters;
-  int tile_rows;  // fused 2D kernel: rows per warp tile (0 = automatic)
+  int tile_rows;  // fused 2D kernels: rows per warp tile / per block band (0 = automatic)
+  int kernel;     // fused 2D kernel family: 0 automatic, 1 warp march, 2 band march
 };
 
 inline Opts make_opts(uint32_t o, int n_iters) {
@@ -49,6 +50,7 @@ inline Opts make_opts(uint32_t o, int n_iters) {
   p.staged = o & MPDATA_STAGED;
   p.n_iters = n_iters;
   p.tile_rows = 0;
+  p.kernel = 0;
   return p;
 }
 

@@ -25,6 +25,10 @@ uint32_t handle_opts(const mpdata_s* h);
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 
+// The same step with one marching front per block of warps (band2d.cu).
+template <typename T>
+int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t st);
+
 // Work table of the batched fused kernel: one item per (field, strip, row tile).
 struct BatchField {
   long long offset;  // first cell of the field in the concatenated arrays

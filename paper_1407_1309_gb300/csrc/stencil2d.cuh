@@ -1,0 +1,97 @@
+// Device helpers shared by the fused 2D kernels (fused2d.cu, band2d.cu): the
+// donor-cell flux of Eq. 5, the guarded psi-fraction of Eq. 6, the donor update
+// of Eq. 4, cp.async wrappers and the lane-neighbour shuffles of a row held as
+// NC adjacent columns per lane.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mpd {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int wrapi(int c, int n) {
+  int r = c % n;
+  return r < 0 ? r + n : r;
+}
+
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b);
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+
+template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
+template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+template <typename T> __device__ __forceinline__ T maxv(T a, T b) { return a > b ? a : b; }
+template <typename T> __device__ __forceinline__ T minv(T a, T b) { return a < b ? a : b; }
+// min(1, x); a NaN x gives 1 (fmin returns the non-NaN operand)
+__device__ __forceinline__ float min1(float x) { return fminf(1.0f, x); }
+__device__ __forceinline__ double min1(double x) { return fmin(1.0, x); }
+// donor-cell flux (Eq. 5) in advector units: [V]+ L + [V]- R, one term of which is zero
+template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return V * (V > T(0) ? L : R); }
+// psi-fraction of Eq. 6 with the zero-denominator guard
+template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return d != T(0) ? fdiv(n, d) : T(0); }
+
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& comp, T t) {
+  const T y = t - comp;
+  const T u = s + y;
+  comp = (u - s) - y;
+  s = u;
+}
+
+// Donor-cell update of Eq. 4 from the four face fluxes, rG = 1/G.  The flux
+// differences are added first and psi last, so only one rounding happens at the
+// scale of psi; with the Kahan option the terms psi - Fp0 + Fm0 - Fp1 + Fm1 are
+// summed in that order with compensation instead.
+template <typename T, bool NUG, bool KAHAN>
+__device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG) {
+  if (KAHAN) {
+    if (NUG) {
+      Fp0 *= rG;
+      Fm0 *= rG;
+      Fp1 *= rG;
+      Fm1 *= rG;
+    }
+    T s = p, comp = T(0);
+    kahan_add(s, comp, -Fp0);
+    kahan_add(s, comp, Fm0);
+    kahan_add(s, comp, -Fp1);
+    kahan_add(s, comp, Fm1);
+    return s;
+  }
+  const T div = (Fm0 - Fp0) + (Fm1 - Fp1);
+  return NUG ? p + div * rG : p + div;
+}
+
+// A row of NC columns held by one lane; the columns just outside come from the
+// neighbouring lanes.
+template <typename T, int NC> __device__ __forceinline__ T from_left(const T (&a)[NC]) {
+  return __shfl_up_sync(kFull, a[NC - 1], 1);
+}
+template <typename T, int NC> __device__ __forceinline__ T from_right(const T (&a)[NC]) {
+  return __shfl_down_sync(kFull, a[0], 1);
+}
+template <typename T, int NC> __device__ __forceinline__ T left_of(const T (&a)[NC], int c, T aL) {
+  return c == 0 ? aL : a[c > 0 ? c - 1 : 0];
+}
+template <typename T, int NC> __device__ __forceinline__ T right_of(const T (&a)[NC], int c, T aR) {
+  return c == NC - 1 ? aR : a[c < NC - 1 ? c + 1 : NC - 1];
+}
+template <typename T, int N> __device__ __forceinline__ void copy_row(T (&d)[N], const T (&s)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) d[c] = s[c];
+}
+
+}  // namespace dev
+}  // namespace mpd
