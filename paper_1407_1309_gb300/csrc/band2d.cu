@@ -15,7 +15,9 @@
 // other warps are read back from the rings, and a warp keeps the rows it reuses
 // itself in registers.  Only the band's first and last rows carry the stencil's
 // 3-row halo, so a tall band recomputes little while W warps share one front.
-// Input rows are prefetched kDepth chunks ahead with cp.async.
+// Input rows are prefetched kDepth chunks ahead with cp.async.  Pass 2 of one
+// chunk shares a barrier interval with pass 1 of the next (they touch disjoint
+// data), so a chunk costs three block barriers.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -129,10 +131,15 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
       for (int c = 0; c < NC; ++c) cp_async<sizeof(T)>(dst + c, src_row + col[c]);
     }
   };
-  // local row lr of every input array, issued by this warp; one commit group per call
+  // local row lr of every input array, issued by this warp; one commit group per call.
+  // The warp's load rows advance by W per chunk: their global row is kept wrapped
+  // incrementally (the first one with a modulo).
+  int g_row = wrapi(Rs + w, p.n0);
   auto load_row = [&](int lr) {
     if (lr < n_load) {
-      const long long off = static_cast<long long>(wrapi(Rs + lr, p.n0)) * p.n1;
+      const long long off = static_cast<long long>(g_row) * p.n1;
+      g_row += W;
+      while (g_row >= p.n0) g_row -= p.n0;
       copy_in(in_row(s_psi, lr), p.psi + off);
       copy_in(in_row(s_v0, lr), p.gc0 + off);
       copy_in(in_row(s_v1, lr), p.gc1 + off);
@@ -145,13 +152,9 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
 #pragma unroll
   for (int j = 0; j < kDepth; ++j) load_row(j * W + w);
   const bool fix = p.rhs_b || p.scale != T(1);
-  const int n_chunks = (n_load + W - 1) / W;
-
-  for (int j = 0; j < n_chunks; ++j) {
-    // ---- this chunk's input rows are in: euler_b source and advector scale on own row
-    cp_wait<kDepth - 1>();
-    if (fix && j * W + w < n_load) {
-      const int lr = j * W + w;
+  // euler_b source and advector scale on a row this warp loaded itself
+  auto fix_row = [&](int lr) {
+    if (fix && lr < n_load) {
       T* q = in_row(s_psi, lr);
       T* q0 = in_row(s_v0, lr);
       T* q1 = in_row(s_v1, lr);
@@ -162,10 +165,90 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         q1[c] = q1[c] * p.scale;
       }
     }
-    __syncthreads();
-    load_row((j + kDepth) * W + w);
+  };
+  const int n_chunks = (n_load + W - 1) / W;
+  cp_wait<kDepth - 1>();
+  fix_row(w);
+  __syncthreads();
 
-    // ---- pass 1 (Eqs. 4-5) at local row a
+  // Per chunk, three barrier-separated stages: A = pass 2 of the previous chunk and
+  // pass 1 of this one (disjoint data), B = pseudo-advectors, C = limiting factors.
+  // Carried from the previous chunk's stages B and C into its pass 2:
+  T q_m[NC], u0m[NC], bun[NC], bdn[NC];
+  for (int j = 0; j <= n_chunks; ++j) {
+    // ---- stage A, first half: limited fluxes and pass 2 of the previous chunk at local
+    // row r = (j-1)*W + w - 3, from the registers its pseudo-advector and factor stages left
+    const int r = (j - 1) * W + w - 3;
+    if (r >= 3 && r <= Hb + 2) {
+      T u0mm[NC], u1c[NC], h0[NC], h0c[NC], h1[NC];
+      lds(u0mm, mid_row(s_u0, r - 1));  // face r-1/2; face r+1/2 is u0m
+      lds(u1c, mid_row(s_u1, r));
+      if (FCT) {
+        T bu_m[NC], bd_m[NC], bu_c[NC], bd_c[NC];
+        lds(bu_m, mid_row(s_bu, r - 1));
+        lds(bd_m, mid_row(s_bd, r - 1));
+        lds(bu_c, mid_row(s_bu, r));
+        lds(bd_c, mid_row(s_bd, r));
+        const T buR = from_right(bu_c), bdR = from_right(bd_c);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          // With two passes only the limited flux F*m is used, so a zero flux needs no
+          // factor: m = min(beta_dn of the upwind cell, beta_up of the downwind cell).
+          {  // face (r+1/2, c)
+            const T F = u0m[c];
+            const bool right = F > T(0);
+            h0[c] = F * minv(right ? bd_c[c] : bu_c[c], right ? bun[c] : bdn[c]);
+          }
+          {  // face (r-1/2, c)
+            const T F = u0mm[c];
+            const bool right = F > T(0);
+            h0c[c] = F * minv(right ? bd_m[c] : bu_m[c], right ? bu_c[c] : bd_c[c]);
+          }
+          {  // face (r, c+1/2)
+            const T F = u1c[c];
+            const bool right = F > T(0);
+            const T x = right ? bd_c[c] : bu_c[c];
+            const T y = right ? right_of(bu_c, c, buR) : right_of(bd_c, c, bdR);
+            h1[c] = F * minv(x, y);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { h0[c] = u0m[c]; h0c[c] = u0mm[c]; h1[c] = u1c[c]; }
+      }
+      T g_r[NC];
+      if (NUG) lds(g_r, in_row(s_g, r));
+      const T h1L = from_left(h1);
+      T np2[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T rG = NUG ? fdiv(T(1), g_r[c]) : T(1);
+        np2[c] = donor<T, NUG, KAHAN>(q_m[c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
+      }
+      const long long o = static_cast<long long>(Rs + r) * p.n1 + gcol;
+      if (p.rhs_a) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (ok[c]) np2[c] = np2[c] + p.dt * p.R[o + c];
+      }
+      if (p.vec && all_ok) {
+        if constexpr (sizeof(T) == 4 && NC == 4) {
+          *reinterpret_cast<float4*>(p.out + o) = make_float4(np2[0], np2[1], np2[2], np2[3]);
+        } else if constexpr (sizeof(T) == 8 && NC == 2) {
+          *reinterpret_cast<double2*>(p.out + o) = make_double2(np2[0], np2[1]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) p.out[o + c] = np2[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (ok[c]) p.out[o + c] = np2[c];
+      }
+    }
+    if (j == n_chunks) break;
+
+    // ---- stage A, second half: pass 1 (Eqs. 4-5) of this chunk at local row a
     const int a = j * W + w - 1;
     const bool do_p1 = a >= 1 && a <= Hb + 4;
     T pn_m[NC], pn_c[NC], v0_m[NC], v1_c[NC], g_c[NC], p1_c[NC];
@@ -193,6 +276,7 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
       sts(mid_row(s_p1, a), p1_c);
     }
     __syncthreads();
+    load_row((j + kDepth) * W + w);  // after the barrier: the slots it refills are no longer read
 
     // ---- local row b = a - 1: pseudo-advectors (Eq. 6 + cross term) and unlimited fluxes.
     // The face between rows b and b+1 needs psi^(1) on rows b, b+1 only and is computed
@@ -201,7 +285,7 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
     const int b = a - 1;
     const bool do_ad = b >= 1 && b <= Hb + 3;
     const bool do_x = do_ad && b >= 2;
-    T q_m[NC], q_c[NC], g_b[NC], u0n[NC], u1n[NC], mx[NC], mn[NC];
+    T q_c[NC], g_b[NC], u0n[NC], u1n[NC], mx[NC], mn[NC];
     if (do_ad) {
       // row b of psi^(1) from the ring, row b+1 = a is this warp's pass-1 output
       T w1_c[NC];
@@ -279,7 +363,6 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
     __syncthreads();
 
     // ---- limiting factors at row b (the flux through face b-1/2 comes from the ring)
-    T u0m[NC], bun[NC], bdn[NC];
     if (do_x) {
       lds(u0m, mid_row(s_u0, b - 1));
       if (FCT) {
@@ -288,8 +371,11 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         for (int c = 0; c < NC; ++c) {
           const T Fm0 = u0m[c], Fp0 = u0n[c];
           const T Fp1 = u1n[c], Fm1 = left_of(u1n, c, u1L);
-          const T in = (posp(Fm0) - negp(Fp0)) + (posp(Fm1) - negp(Fp1));
-          const T ou = (posp(Fp0) - negp(Fm0)) + (posp(Fp1) - negp(Fm1));
+          // [x]- = x - [x]+ and [x]+ = x - [x]- hold exactly in floating point, so the
+          // outflow sum reuses the inflow sum's four extrema (adds instead of min/max)
+          const T pFm0 = posp(Fm0), nFp0 = negp(Fp0), pFm1 = posp(Fm1), nFp1 = negp(Fp1);
+          const T in = (pFm0 - nFp0) + (pFm1 - nFp1);
+          const T ou = ((Fp0 - nFp0) - (Fm0 - pFm0)) + ((Fp1 - nFp1) - (Fm1 - pFm1));
           const T Gi = NUG ? g_b[c] : T(1);
           const T q = q_c[c];
           // min(1, x / |s|) is 1 for s = 0 (x/0 is inf or NaN, and min ignores NaN)
@@ -300,77 +386,10 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         sts(mid_row(s_bd, b), bdn);
       }
     }
+    // next chunk's input rows
+    cp_wait<kDepth - 1>();
+    fix_row((j + 1) * W + w);
     __syncthreads();
-
-    // ---- local row r = b - 1: limited fluxes and pass 2, stored
-    const int r = b - 1;
-    if (r >= 3 && r <= Hb + 2) {
-      T u0mm[NC], u1c[NC], h0[NC], h0c[NC], h1[NC];
-      lds(u0mm, mid_row(s_u0, r - 1));  // face r-1/2; face r+1/2 is u0m
-      lds(u1c, mid_row(s_u1, r));
-      if (FCT) {
-        T bu_m[NC], bd_m[NC], bu_c[NC], bd_c[NC];
-        lds(bu_m, mid_row(s_bu, r - 1));
-        lds(bd_m, mid_row(s_bd, r - 1));
-        lds(bu_c, mid_row(s_bu, r));
-        lds(bd_c, mid_row(s_bd, r));
-        const T buR = from_right(bu_c), bdR = from_right(bd_c);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          // With two passes only the limited flux F*m is used, so a zero flux needs no
-          // factor: m = min(beta_dn of the upwind cell, beta_up of the downwind cell).
-          {  // face (r+1/2, c)
-            const T F = u0m[c];
-            const bool right = F > T(0);
-            h0[c] = F * minv(right ? bd_c[c] : bu_c[c], right ? bun[c] : bdn[c]);
-          }
-          {  // face (r-1/2, c)
-            const T F = u0mm[c];
-            const bool right = F > T(0);
-            h0c[c] = F * minv(right ? bd_m[c] : bu_m[c], right ? bu_c[c] : bd_c[c]);
-          }
-          {  // face (r, c+1/2)
-            const T F = u1c[c];
-            const bool right = F > T(0);
-            const T x = right ? bd_c[c] : bu_c[c];
-            const T y = right ? right_of(bu_c, c, buR) : right_of(bd_c, c, bdR);
-            h1[c] = F * minv(x, y);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) { h0[c] = u0m[c]; h0c[c] = u0mm[c]; h1[c] = u1c[c]; }
-      }
-      T g_r[NC];
-      if (NUG) lds(g_r, in_row(s_g, r));
-      const T h1L = from_left(h1);
-      T np2[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const T rG = NUG ? fdiv(T(1), g_r[c]) : T(1);
-        np2[c] = donor<T, NUG, KAHAN>(q_m[c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
-      }
-      const long long o = static_cast<long long>(Rs + r) * p.n1 + gcol;
-      if (p.rhs_a) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (ok[c]) np2[c] = np2[c] + p.dt * p.R[o + c];
-      }
-      if (p.vec && all_ok) {
-        if constexpr (sizeof(T) == 4 && NC == 4) {
-          *reinterpret_cast<float4*>(p.out + o) = make_float4(np2[0], np2[1], np2[2], np2[3]);
-        } else if constexpr (sizeof(T) == 8 && NC == 2) {
-          *reinterpret_cast<double2*>(p.out + o) = make_double2(np2[0], np2[1]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) p.out[o + c] = np2[c];
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (ok[c]) p.out[o + c] = np2[c];
-      }
-    }
   }
   cp_wait<0>();
 }

@@ -247,8 +247,11 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
                             right_of(lo[1], c, lR));
           const T Fm0 = u0[0][c], Fp0 = u0[1][c];
           const T Fp1 = u1[1][c], Fm1 = left_of(u1[1], c, u1L);
-          const T in = (posp(Fm0) - negp(Fp0)) + (posp(Fm1) - negp(Fp1));
-          const T ou = (posp(Fp0) - negp(Fm0)) + (posp(Fp1) - negp(Fm1));
+          // [x]- = x - [x]+ and [x]+ = x - [x]- hold exactly in floating point, so the
+          // outflow sum reuses the inflow sum's four extrema (adds instead of min/max)
+          const T pFm0 = posp(Fm0), nFp0 = negp(Fp0), pFm1 = posp(Fm1), nFp1 = negp(Fp1);
+          const T in = (pFm0 - nFp0) + (pFm1 - nFp1);
+          const T ou = ((Fp0 - nFp0) - (Fm0 - pFm0)) + ((Fp1 - nFp1) - (Fm1 - pFm1));
           const T Gi = NUG ? gg[1][c] : T(1);
           const T q = p1[2][c];
           // min(1, x / |s|) is 1 for s = 0 (x/0 is inf or NaN, and min ignores NaN)
