@@ -158,9 +158,10 @@ int mpdata_clear_stop(mpdata_t h);
  *   warp walks down (warp march) or the rows of one block's band (band march);
  *   0 = automatic, otherwise 4..65536.
  * MPDATA_TUNE_KERNEL: fused 2D kernel family for single-field 2D steps:
- *   0 = automatic (band march on fields whose warp-march tiles would be 8 rows
- *   high, i.e. fewer than ~1800 tiles of 16 rows; warp march otherwise),
- *   1 = warp march, 2 = band march.  Batched
+ *   0 = automatic (band march where the warp march cannot fill the GPU: FP32
+ *   fields with fewer than ~600 warp tiles of 8 rows, FP64 fields whose warp
+ *   tiles would be 16 rows or less; warp march otherwise), 1 = warp march,
+ *   2 = band march.  Batched
  *   handles always use the warp march's persistent kernel.
  * Returns EINVAL for an unknown knob or value.
  */

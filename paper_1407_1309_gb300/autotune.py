@@ -56,23 +56,24 @@ def key_of(solver) -> str:
 
 
 def time_steps(solver, psi, gc, g=None, r=None, dt=0.0, steps=20, flush_bytes=256 << 20):
-    """Seconds per step, each step timed with CUDA events after an L2 flush."""
+    """Seconds per step on the device: each step is bracketed by CUDA events after an L2
+    flush, all steps are queued before one synchronisation (so host launch overhead does
+    not fall inside the events), and the per-step times are averaged."""
     dev = solver.device
+    stream = torch.cuda.current_stream(dev)
     a, b = psi.clone(), torch.empty_like(psi)
     flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev) if flush_bytes else None
     solver.advance(a, b, gc, g, r, dt, 2)
-    total = 0.0
-    for _ in range(steps):
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
         if flush is not None:
             flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(torch.cuda.current_stream(dev))
+        e0.record(stream)
         solver.advance(a, b, gc, g, r, dt, 1)
-        e1.record(torch.cuda.current_stream(dev))
+        e1.record(stream)
         a, b = b, a
-        torch.cuda.synchronize(dev)
-        total += e0.elapsed_time(e1) / 1e3
-    return total / steps
+    torch.cuda.synchronize(dev)
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3 / steps
 
 
 def _apply(solver, choice):

@@ -523,15 +523,19 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   p.n0 = g.n[1];
   p.n1 = g.n[2];
   p.strips = (p.n1 + stride<NC>() - 1) / stride<NC>();
-  // the tallest tile that still gives 12 warps per SM (152 SMs), at least 8 rows
+  // the tallest tile that still gives ~7.5 warps per SM (152 SMs), at least 8 rows
+  // (measured on the rotation workload: 8 rows at 1024^2, 32 at 2048^2, 48-64 at 4096^2)
+  auto warps = [&](int ty) { return static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty); };
   int auto_ty = 8;
-  for (int ty : {64, 32, 16}) {
-    if (static_cast<long long>(p.strips) * ((p.n0 + ty - 1) / ty) >= 152LL * 12) { auto_ty = ty; break; }
+  for (int ty : {64, 48, 32, 24, 16, 12}) {
+    if (warps(ty) >= 1140) { auto_ty = ty; break; }
   }
-  // Fields too small for tiles taller than 8 rows lose a third of the warp march's
-  // work to each tile's 6-row ramp; there one front per block of warps (band march)
-  // is faster.
-  if (o.kernel == 2 || (o.kernel == 0 && auto_ty == 8)) return band_step<T>(g, o, a, st);
+  // Where the warp march cannot fill the GPU even with 8-row tiles (FP32: fewer than ~4
+  // warps per SM), or in FP64 (arithmetic-bound: every recomputed halo row costs FP64
+  // issue slots) with tiles of 16 rows or less, one front per block of warps (band
+  // march) is faster.
+  const bool band_auto = sizeof(T) == 4 ? warps(8) < 608 : auto_ty <= 16;
+  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_step<T>(g, o, a, st);
   p.ty = o.tile_rows > 0 ? o.tile_rows : auto_ty;
   p.rowtiles = (p.n0 + p.ty - 1) / p.ty;
   p.dt = a.dt;

@@ -22,8 +22,12 @@ namespace {
 template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
 template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+// n / d: FP32 uses the fast division (rcp and multiply, 2 ulp), FP64 the IEEE one
+template <typename T> __device__ __forceinline__ T qdiv(T n, T d);
+template <> __device__ __forceinline__ float qdiv<float>(float n, float d) { return __fdividef(n, d); }
+template <> __device__ __forceinline__ double qdiv<double>(double n, double d) { return n / d; }
 // psi-fraction with the zero-denominator guard (the ratio of Eq. 6 is 0 when its sum is 0)
-template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return d != T(0) ? n / d : T(0); }
+template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return d != T(0) ? qdiv(n, d) : T(0); }
 
 template <typename T> struct In3 { const T* p[3]; };
 template <typename T> struct Out3 { T* p[3]; };
@@ -116,8 +120,8 @@ __global__ void k_donor(Grid g, const T* __restrict__ psi, In3<T> V, T vscale, b
     const T vp = V.p[d][i] * vscale, vm = V.p[d][im] * vscale;
     const T Fp = flux(p, psi[ip], vp, unit);
     const T Fm = flux(psi[im], p, vm, unit);
-    const T t0 = G ? -Fp / Gi : -Fp;
-    const T t1 = G ? Fm / Gi : Fm;
+    const T t0 = G ? -qdiv(Fp, Gi) : -Fp;
+    const T t1 = G ? qdiv(Fm, Gi) : Fm;
     if (kahan) {
       T y = t0 - comp;
       T u = s + y;
@@ -179,11 +183,12 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
-    const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
+    // every 1/Gb of the face is one reciprocal, multiplied in
+    const T rGb = G ? qdiv(T(1), T(0.5) * (G[i] + G[ip])) : T(1);
     const T V = Vin.p[d][i] * vscale;
     const T p1 = psi[ip];
     const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
-    T out = (absv(V) - V * V / Gb) * A;
+    T out = (absv(V) - V * V * rGb) * A;
     T Vq[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
@@ -195,14 +200,14 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       const T Tp = psi[iqp] + psi[idqp];
       const T Bt = psi[iqm] + psi[idqm];
       const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
-      out = out - T(0.5) * V * Vq[q] / Gb * B;
+      out = out - T(0.5) * V * Vq[q] * rGb * B;
     }
     if (tot) {
       const T pm = psi[nb.at(d, -1)];
       const T p2 = psi[nb.at(d, +2)];
       const T num = ((p2 - p1) - p0) + pm;
       const T D = iga ? num * T(0.25) : fracg(num, ((p2 + p1) + p0) + pm);
-      out = out + ((T(3) * V * absv(V)) / Gb - (T(2) * V * V * V) / (Gb * Gb) - V) / T(3) * D;
+      out = out + ((T(3) * V * absv(V)) * rGb - (T(2) * V * V * V) * (rGb * rGb) - V) * T(1.0 / 3.0) * D;
       int qs[2] = {0, 0}, nq = 0;
 #pragma unroll
       for (int q = 0; q < ND; ++q) {
@@ -212,7 +217,7 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
         const T e = psi[nb.at(q, -1)], f = psi[nb.at2(q, -1, d, +1)];
         const T n2 = (b - a) - (f - e);
         const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
-        out = out + absv(V) * Vq[q] / Gb * (T(1) - T(2) * absv(V) / Gb) * D2;
+        out = out + absv(V) * Vq[q] * rGb * (T(1) - T(2) * absv(V) * rGb) * D2;
       }
       if (ND == 3) {
         T pr[4];
@@ -228,7 +233,7 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
         // pr = {(+,+), (+,-), (-,+), (-,-)}
         const T n3 = (pr[0] - pr[1]) - (pr[2] - pr[3]);
         const T D3 = iga ? n3 * T(0.125) : fracg(n3, (pr[0] + pr[1]) + (pr[2] + pr[3]));
-        out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] / (Gb * Gb) * D3;
+        out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] * (rGb * rGb) * D3;
       }
     }
     Vout.p[d][i] = out;
@@ -257,8 +262,8 @@ __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __r
     out = out + (posp(Fp) - negp(Fm));
   }
   const T Gi = G ? G[i] : T(1);
-  bu[i] = in > T(0) ? Gi * posp(mx[i] - p) / in : T(1);
-  bd[i] = out > T(0) ? Gi * posp(p - mn[i]) / out : T(1);
+  bu[i] = in > T(0) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
+  bd[i] = out > T(0) ? qdiv(Gi * posp(p - mn[i]), out) : T(1);
   }
 }
 
@@ -339,7 +344,6 @@ template <typename T, int ND>
 cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G, const Tape<T>& tp,
                     T* const* levels, cudaStream_t st) {
   const int bs = 256;
-  const unsigned nb = static_cast<unsigned>((g.N + bs - 1) / bs);
   const int K = o.n_iters;
   In3<T> v1{{gc[0], gc[1], gc[2]}};
   if (K >= 2) {
