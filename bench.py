@@ -48,9 +48,13 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / staged / e2e / oracle legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and time the library's automatic kernel choice")
-    ap.add_argument("--workload", choices=["rotation", "ensemble"], default="rotation",
+    ap.add_argument("--kernel", choices=["warp", "band"], default=None,
+                    help="time this fused kernel family (skips the autotuner)")
+    ap.add_argument("--tile-rows", type=int, default=0, help="tile / band rows with --kernel (0 = automatic)")
+    ap.add_argument("--workload", choices=["rotation", "ensemble", "deform3d"], default="rotation",
                     help="rotation: 1024^2 rotating cone (default); ensemble: 512 fields of 64^2..512^2, "
-                         "split over the ranks by cell count")
+                         "split over the ranks by cell count; deform3d: 256^3 deformational flow, "
+                         "n_iters = 3 + tot + fct, G != 1 (replicas under torchrun)")
     return ap.parse_args()
 
 
@@ -126,14 +130,27 @@ def measured_peaks():
 
 
 KERNEL_NAMES = {1: "k_fused2d", 2: "k_band2d"}
+KERNEL_SOURCES = {"k_fused2d": ("fused2d.cu", "stencil2d.cuh"), "k_band2d": ("band2d.cu", "stencil2d.cuh")}
+
+
+def kernel_sources_sha256(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(ROOT, "paper_1407_1309_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def traffic_from_profiles(kernel, n, dtype):
-    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary, if current."""
+    """Per-launch DRAM bytes (read + write) of the timed kernel from the committed ncu summary;
+    None when there is none or when the kernel's sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_rotation{n}_{dtype}.json")
     try:
         with open(path) as f:
             d = json.load(f)
+        if d.get("sources_sha256") != kernel_sources_sha256(kernel):
+            return None
         return d.get("bytes_per_launch")
     except Exception:
         return None
@@ -203,22 +220,31 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     m = Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev)
     stream = torch.cuda.current_stream(dev)
-    if args.no_tune:
+    if args.kernel:
+        choice = (1 if args.kernel == "warp" else 2, args.tile_rows)
+        m.tune(capi.TUNE_KERNEL, choice[0])
+        m.tune(capi.TUNE_TILE_ROWS, choice[1])
+    elif args.no_tune:
         choice = None
     else:  # kernel family and tile height for this workload, timed on these buffers (not cached)
         from paper_1407_1309_gb300 import autotune
         choice, _, _ = autotune.autotune(m, a, gc, steps=8, use_cache=False)
-    tuned = {"kernel": KERNEL_NAMES[choice[0]], "tile_rows": choice[1], "chosen_by": "autotuner"} \
+    tuned = {"kernel": KERNEL_NAMES[choice[0]], "tile_rows": choice[1],
+             "chosen_by": "command line" if args.kernel else "autotuner"} \
         if choice else {"kernel": "automatic", "chosen_by": "library default"}
 
     def timed(K, flush_l2=True):
+        # arguments marshalled once per direction, so the host enqueues a step faster than the
+        # device runs flush + step and no host gap falls between the events
         nonlocal a, b
+        calls = {(a.data_ptr(), b.data_ptr()): capi.prepare_advance(m.h, a, b, gc),
+                 (b.data_ptr(), a.data_ptr()): capi.prepare_advance(m.h, b, a, gc)}
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for e0, e1 in evs:
             if flush_l2:
                 flush.zero_()
             e0.record(stream)
-            m.advance(a, b, gc)
+            calls[(a.data_ptr(), b.data_ptr())]()
             e1.record(stream)
             a, b = b, a
         torch.cuda.synchronize(dev)
@@ -730,12 +756,77 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_deform3d(args, n=256):
+    """The 3D configuration on its own: every step timed with CUDA events (the five input
+    arrays, 335 MB in FP32, exceed the L2, so no flush is needed), one JSON line."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1407_1309_gb300 import capi, workloads
+    from paper_1407_1309_gb300.solver import Mpdata
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    psi, gc, G = workloads.deformational_3d(n)
+    t = lambda x: torch.tensor(x, dtype=dtype, device=dev)
+    K = args.warmup + args.steps
+    scales = [workloads.deformational_scale(s) for s in range(K)]
+    opts = capi.TOT | capi.FCT | capi.NUG
+    with Mpdata((n, n, n), dtype=dtype, n_iters=3, opts=opts, device=dev) as m:
+        a, b, g, Gt = t(psi), torch.empty(n, n, n, dtype=dtype, device=dev), [t(v) for v in gc], t(G)
+        for s in range(args.warmup):
+            m.advance(a, b, g, Gt, None, 0.0, 1, scales[s:s + 1])
+            a, b = b, a
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        evs = []
+        for s in range(args.warmup, K):
+            e0, e1 = _events()
+            e0.record()
+            m.advance(a, b, g, Gt, None, 0.0, 1, scales[s:s + 1])
+            e1.record()
+            evs.append((e0, e1))
+            a, b = b, a
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+    secs = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3, dev)
+    peaks, how = measured_peaks()
+    cells = n ** 3
+    esize = 4 if dtype == torch.float32 else 8
+    bpc = 6 * esize  # psi, gc0..2, G read; psi written
+    achieved = bpc * cells * args.steps / secs / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(job_value(cells, args.steps, ws, secs), 3), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic (seeded deformational flow, no dataset)",
+            "config": {"workload": f"3d_deformational_{n}^3_n_iters3_tot_fct_G", "grid": [n, n, n],
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}",
+                       "path": "staged kernels (one kernel per sub-step)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                         "algorithmic_bytes_per_cell_step": bpc},
+            "gpu_launches": 10 * args.steps, "clocks": clk}), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "deform3d":
+        run_deform3d(args)
     else:
         run_ours(args)
 

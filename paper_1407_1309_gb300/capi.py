@@ -160,6 +160,23 @@ def mpdata_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1, gc
     _check(rc, "mpdata_advance")
 
 
+def prepare_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1):
+    """mpdata_advance with its arguments marshalled once: returns a callable that issues
+    the same call (same buffers) again with no per-call argument conversion, for loops
+    whose host-side cost must stay below the device time of a step.  The caller keeps
+    the tensors alive while the callable is in use."""
+    gcp, keep = _ptr_array(gc)
+    fn = load().mpdata_advance
+    args = (h, _ptr(psi_in), _ptr(psi_out), gcp, _ptr(g), _ptr(r), float(dt), int(n_steps), None)
+
+    def call():
+        rc = fn(*args)
+        if rc != 0:
+            _check(rc, "mpdata_advance")
+    call._keep = keep
+    return call
+
+
 def mpdata_adjoint_step(h, psi_n, gc, g, psi_bar, gc_bar=None, *, raw=False):
     gcp, _k1 = _ptr_array(gc)
     gbp = None
