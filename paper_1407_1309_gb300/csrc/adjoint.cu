@@ -90,10 +90,13 @@ template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit
 #define CELL_END }
 
 // Reverse of the donor-cell pass k, psi_k = psi_{k-1} + sum_d (F_{i-e_d} - F_i)/G_i with
-// F = flux(psi_{k-1}, V^k): pb_prev += dL/dpsi_{k-1}, vhb[d] += dL/dV^k.
-template <typename T, int ND>
+// F = flux(psi_{k-1}, V^k): pb_prev += dL/dpsi_{k-1}, vhb[d] += dL/dV^k.  FINAL (the first
+// pass, reversed last): the step's outputs are written here instead, psi_out = pb_prev +
+// this pass's part, and gc_out[d] += vhb[d] + this pass's part (gc_out[d] may be null).
+template <typename T, int ND, bool FINAL>
 __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> V,
-                              const T* __restrict__ G, bool unit, T* __restrict__ pb_prev, W3<T> vhb) {
+                              const T* __restrict__ G, bool unit, T* __restrict__ pb_prev, W3<T> vhb,
+                              T* __restrict__ psi_out, W3<T> gc_out) {
   CELL_INDEX
   const T gi = G ? pb[i] / G[i] : pb[i];
   T acc = pb[i];
@@ -110,9 +113,17 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
       acc += fp * posp(v) + fm * negp(vm);
       dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
     }
-    vhb.p[d][i] += fp * dv;
+    if (!FINAL) {
+      vhb.p[d][i] += fp * dv;
+    } else if (gc_out.p[d]) {
+      gc_out.p[d][i] += vhb.p[d][i] + fp * dv;
+    }
   }
-  pb_prev[i] += acc;
+  if (FINAL) {
+    psi_out[i] = pb_prev[i] + acc;
+  } else {
+    pb_prev[i] += acc;
+  }
   CELL_END
 }
 
@@ -395,14 +406,14 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     const T* pbk = (k == K) ? psi_bar : pbl[k];
     P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
     W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
-    ka_donor_flux<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1], vhbk);
+    ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1],
+                                                                 vhbk, nullptr, W3<T>{});
     P3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
     if (o.fct) {
-      const size_t nz = static_cast<size_t>(N) * sizeof(T);
-      cudaMemsetAsync(bub, 0, nz, st);
-      cudaMemsetAsync(bdb, 0, nz, st);
-      for (int d = 0; d < D; ++d) cudaMemsetAsync(fb[d], 0, nz, st);
+      // factor and flux adjoints of this pass: bub, bdb, fb[0..D-1] are contiguous and were
+      // zeroed with the rest of the adjoint scratch; later passes clear them again
+      if (k < K) cudaMemsetAsync(bub, 0, static_cast<size_t>(N) * (2 + D) * sizeof(T), st);
       P3<T> vhbr{{vhb[k][0], vhb[k][1], vhb[k][2]}};
       W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
       ka_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, vhbr, vu, tp.psi[k - 1], o.iga, tp.bu[k], tp.bd[k], vbw, bub, bdb);
@@ -418,17 +429,26 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
   }
   if (o.fct && K >= 2) ka_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, mxb, mnb, tp.psi[0], tp.psi[1], pbl[0], pbl[1]);
-  {
-    const T* pb1 = (K == 1) ? psi_bar : pbl[1];
-    P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
-    W3<T> vhb1{{vhb[1][0], vhb[1][1], vhb[1][2]}};
-    ka_donor_flux<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pb1, tp.psi[0], v1, G, false, pbl[0], vhb1);
+  P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
+  W3<T> vhb1{{vhb[1][0], vhb[1][1], vhb[1][2]}};
+  if (K >= 2) {
+    // the first pass, reversed last, writes the step's outputs: psi_bar (consumed by pass K
+    // already) and gc_bar
+    W3<T> out{{nullptr, nullptr, nullptr}};
+    for (int d = 0; d < D; ++d) out.p[d] = gc_bar ? static_cast<T*>(gc_bar[d]) : nullptr;
+    ka_donor_flux<T, ND, true><<<cell_grid(g, bs), bs, 0, st>>>(g, pbl[1], tp.psi[0], v1, G, false, pbl[0], vhb1,
+                                                                psi_bar, out);
+  } else {
+    // one pass: psi_bar is this kernel's input, so the result goes through scratch
+    ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, psi_bar, tp.psi[0], v1, G, false, pbl[0], vhb1,
+                                                                 nullptr, W3<T>{});
+    if (cudaMemcpyAsync(psi_bar, pbl[0], static_cast<size_t>(N) * sizeof(T), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+      return MPDATA_ECUDA;
+    if (gc_bar)
+      for (int d = 0; d < D; ++d)
+        if (gc_bar[d]) ka_accumulate<T><<<nb, bs, 0, st>>>(N, vhb[1][d], static_cast<T*>(gc_bar[d]));
   }
-  if (cudaMemcpyAsync(psi_bar, pbl[0], static_cast<size_t>(N) * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return MPDATA_ECUDA;
-  if (gc_bar)
-    for (int d = 0; d < D; ++d)
-      if (gc_bar[d]) ka_accumulate<T><<<nb, bs, 0, st>>>(N, vhb[1][d], static_cast<T*>(gc_bar[d]));
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
