@@ -315,6 +315,38 @@ def run_ours(args):
         extras["fp64_path"] = {"value": round(cells * k64 / s64 / 1e9, 3), "unit": UNIT, "steps": k64,
                                "l2": "not flushed (ALU-bound: FP64 arithmetic, not HBM, limits it)",
                                "bound": "alu_fp64"}
+        if dtype == torch.float32:
+            # the same K steps on the compensated FP32 state (hi + lo, mpdata_advance_compensated),
+            # from the FP64 initial field split exactly; the first kc steps timed like the headline
+            hi32 = psi_np.astype(np.float32)
+            hi = torch.tensor(hi32, device=dev)
+            lo = torch.tensor((psi_np - hi32.astype(np.float64)).astype(np.float32), device=dev)
+            hn, ln = torch.empty_like(hi), torch.empty_like(lo)
+            kc = min(args.steps, 1000)
+            with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as mc:
+                mc.tune(capi.TUNE_TILE_ROWS, tuned.get("tile_rows", 0) if tuned["kernel"] == "k_fused2d" else 0)
+                evs = []
+                for _ in range(kc):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    capi.mpdata_advance_compensated(mc.h, hi, lo, hn, ln, gc)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+                    hi, hn, lo, ln = hn, hi, ln, lo
+                if args.steps > kc:
+                    capi.mpdata_advance_compensated(mc.h, hi, lo, hi, lo, gc, n_steps=args.steps - kc)
+                torch.cuda.synchronize(dev)
+            sc = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
+            got = hi.double().cpu().numpy() + lo.double().cpu().numpy()
+            ec = got - ref64
+            extras["fp32_compensated_state"] = {
+                "value": round(cells * kc / sc / 1e9, 3), "unit": UNIT, "steps_timed": kc,
+                "bytes_per_cell_step": 24, "kernel": "k_fused2d (compensated)",
+                "err_vs_fp64_gpu_after_K_steps": {
+                    "rel_l2": float(np.linalg.norm(ec) / np.linalg.norm(ref64)),
+                    "max_abs": float(np.abs(ec).max()),
+                    "rel_mass_drift": float(abs(got.sum() - psi_np.sum()) / abs(psi_np.sum()))}}
         try:
             import oracle
             oracle.set_threads(0)

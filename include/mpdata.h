@@ -109,6 +109,28 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
                    const void* g, const void* r, double dt, int n_steps, const double* gc_scale);
 
 /*
+ * mpdata_advance on a compensated FP32 state.  The paper computes in one precision
+ * throughout; this entry point has no counterpart there.  It keeps each cell's value as
+ * the pair psi = hi + lo of FP32 numbers (hi in psi_in / psi_out, the small remainder lo
+ * in lo_in / lo_out, same layout).  Every quantity of the step (donor-cell fluxes,
+ * pseudo-advectors of Eq. 6, FCT bounds and factors) is computed in FP32 from hi, as by
+ * mpdata_advance; both donor-cell passes (Eq. 4) add their four face fluxes with
+ * error-free two-sums whose rounding errors go to lo, and the pair is renormalised.  A
+ * flux leaves one cell and enters its neighbour with the same value, so sum(hi + lo)
+ * is conserved up to the rounding of the lo additions, and the state carries about twice
+ * the FP32 precision across steps.  Start from lo = 0 for an FP32 initial field (or
+ * lo = x - (float)x for an FP64 one).
+ * Requirements: an FP32 handle with one 2D field, n_iters = 2, without MPDATA_TOT or
+ * MPDATA_STAGED (MPDATA_EUNSUPPORTED otherwise); lo_in / lo_out aliased exactly when
+ * psi_in / psi_out are (EINVAL otherwise).  The warp-march kernel runs it (the handle's
+ * MPDATA_TUNE_TILE_ROWS applies unless MPDATA_TUNE_KERNEL selects the band march).  The
+ * first call allocates a second ping-pong buffer (ENOMEM).  Other errors as mpdata_advance.
+ */
+int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in, void* psi_out,
+                               void* lo_out, const void* const* gc, const void* g, const void* r,
+                               double dt, int n_steps, const double* gc_scale);
+
+/*
  * Reverse of ONE step from state psi_n (the derivative of the donor-cell passes,
  * Eqs. 4-5, the antidiffusive advector, Eq. 6 with its multi-D cross terms, and
  * the FCT limiter, Sect. 3.1.4): on entry psi_bar = dL/dpsi^{n+1}, on exit

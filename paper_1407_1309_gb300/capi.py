@@ -23,6 +23,7 @@ EXPORTED = (
     "mpdata_create", "mpdata_step", "mpdata_advance", "mpdata_adjoint_step", "mpdata_reduce",
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
+    "mpdata_advance_compensated",
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
@@ -63,6 +64,7 @@ def load(build_if_needed: bool = True):
             "mpdata_create": ([ctypes.POINTER(ctypes.c_void_p), I, I, ctypes.POINTER(I64), I, I, U, P], I),
             "mpdata_step": ([P, P, PP, P, P, D, I], I),
             "mpdata_advance": ([P, P, P, PP, P, P, D, I, DP], I),
+            "mpdata_advance_compensated": ([P, P, P, P, P, PP, P, P, D, I, DP], I),
             "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
             "mpdata_reduce": ([P, P, P, DP], I),
             "mpdata_diff_norms": ([P, P, P, DP, DP], I),
@@ -158,6 +160,22 @@ def mpdata_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1, gc
     if raw:
         return rc
     _check(rc, "mpdata_advance")
+
+
+def mpdata_advance_compensated(h, psi_in, lo_in, psi_out, lo_out, gc, g=None, r=None, dt=0.0, n_steps=1,
+                               gc_scale=None, *, raw=False):
+    gcp, _keep = _ptr_array(gc)
+    sc = None
+    if gc_scale is not None:
+        if len(gc_scale) < n_steps:
+            raise ValueError("gc_scale needs one factor per step")
+        sc = (ctypes.c_double * len(gc_scale))(*[float(v) for v in gc_scale])
+    rc = load().mpdata_advance_compensated(h, _ptr(psi_in), _ptr(lo_in), _ptr(psi_out), _ptr(lo_out), gcp, _ptr(g),
+                                           _ptr(r), float(dt), int(n_steps),
+                                           ctypes.cast(sc, ctypes.POINTER(ctypes.c_double)) if sc is not None else None)
+    if raw:
+        return rc
+    _check(rc, "mpdata_advance_compensated")
 
 
 def prepare_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1):

@@ -22,6 +22,7 @@ struct mpdata_s {
   size_t esize = 4;
   void* staged = nullptr;            // staged-path scratch
   void* pingpong = nullptr;          // out-of-place buffer for the fused paths (total elements)
+  void* pingpong_lo = nullptr;       // its low-part twin for the compensated state (on first use)
   void* adj = nullptr;               // adjoint scratch
   mpd::FieldSpan* d_spans = nullptr;
   double* d_partial = nullptr;       // 2 * kRedBlocks * n_fields
@@ -131,6 +132,7 @@ int sync_status(mpdata_s* h) {
 void free_all(mpdata_s* h) {
   cudaFree(h->staged);
   cudaFree(h->pingpong);
+  cudaFree(h->pingpong_lo);
   mpd::adjoint_free(h);
   cudaFree(h->d_spans);
   cudaFree(h->d_partial);
@@ -221,6 +223,65 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
                               static_cast<const float*>(g), static_cast<const float*>(r), dt, n_steps, gc_scale);
   return run_advance<double>(h, static_cast<const double*>(psi_in), static_cast<double*>(psi_out), gc,
                              static_cast<const double*>(g), static_cast<const double*>(r), dt, n_steps, gc_scale);
+}
+
+int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in, void* psi_out, void* lo_out,
+                               const void* const* gc, const void* g, const void* r, double dt, int n_steps,
+                               const double* gc_scale) {
+  if (!h || n_steps < 1 || !psi_out || !lo_in || !lo_out) return MPDATA_EINVAL;
+  int rc = validate_fields(h, psi_in, gc, g, r);
+  if (rc != MPDATA_OK) return rc;
+  if (!aligned(psi_out, h->esize) || !aligned(lo_in, h->esize) || !aligned(lo_out, h->esize)) return MPDATA_EINVAL;
+  if ((psi_in == psi_out) != (lo_in == lo_out)) return MPDATA_EINVAL;
+  if (h->dtype != MPDATA_F32 || h->n_fields != 1 || h->nd != 2 || h->n_iters != 2 || (h->opts & MPDATA_TOT) ||
+      (h->opts & MPDATA_STAGED))
+    return MPDATA_EUNSUPPORTED;
+  if (h->stop.load()) return MPDATA_ESTOPPED;
+  DeviceGuard dg(h->device);
+  if (!h->pingpong_lo && cudaMalloc(&h->pingpong_lo, static_cast<size_t>(h->total) * sizeof(float)) != cudaSuccess) {
+    h->pingpong_lo = nullptr;
+    return MPDATA_ENOMEM;
+  }
+  mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
+  o.tile_rows = h->kernel == 1 || h->kernel == 0 ? h->tile_rows : 0;  // band heights do not apply
+  const float* gcf[3] = {static_cast<const float*>(gc[0]), static_cast<const float*>(gc[1]), nullptr};
+  // as in mpdata_advance: the result alternates between the outputs and the ping-pong
+  // pair so that the last step lands in (psi_out, lo_out)
+  float* X = static_cast<float*>(psi_out);
+  float* XL = static_cast<float*>(lo_out);
+  float* P = static_cast<float*>(h->pingpong);
+  float* PL = static_cast<float*>(h->pingpong_lo);
+  const float* cur = static_cast<const float*>(psi_in);
+  const float* curl = static_cast<const float*>(lo_in);
+  const size_t bytes = static_cast<size_t>(h->total) * sizeof(float);
+  if (psi_in == psi_out && n_steps % 2 == 1) {
+    if (cudaMemcpyAsync(P, X, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(PL, XL, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    cur = P;
+    curl = PL;
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
+    const bool last_parity = (n_steps - 1 - s) % 2 == 0;
+    float* dst = last_parity ? X : P;
+    float* dstl = last_parity ? XL : PL;
+    mpd::StepArgs<float> a;
+    a.psi_in = cur;
+    a.psi_out = dst;
+    a.gc[0] = gcf[0];
+    a.gc[1] = gcf[1];
+    a.gc[2] = nullptr;
+    a.g = static_cast<const float*>(g);
+    a.r = static_cast<const float*>(r);
+    a.dt = static_cast<float>(dt);
+    a.gc_scale = gc_scale ? static_cast<float>(gc_scale[s]) : 1.0f;
+    rc = mpd::fused_step_comp(h->grids[0], o, a, curl, dstl, h->stream);
+    if (rc != MPDATA_OK) return rc;
+    cur = dst;
+    curl = dstl;
+  }
+  return cuda_status(cudaGetLastError());
 }
 
 int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, const void* r, double dt,

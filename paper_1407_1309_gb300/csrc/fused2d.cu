@@ -34,7 +34,8 @@ using namespace dev;
 constexpr int kLead = 4;     // computed columns left of the strip's first output column
 constexpr int kPF = 4;       // rows in flight
 constexpr int kSlots = kPF + 1;
-constexpr int kArr = 5;      // psi, gc0, gc1, G, R
+// arrays in a ring slot: psi, gc0, gc1, G, R [, lo of the compensated state]
+template <bool COMP> constexpr int arrs() { return COMP ? 6 : 5; }
 constexpr int kWarps = 4;    // warps per block
 
 template <int NC> constexpr int cols() { return 32 * NC; }
@@ -51,13 +52,19 @@ struct F2Params {
   int n0, n1, strips, rowtiles, ty;
   T dt, scale;
   int rhs_a, rhs_b, vec;
+  const T* lo;   // compensated state: low parts in / out (COMP only)
+  T* lo_out;
 };
 
 // One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
 // row R0 down ty rows of the field described by p; `ring` is the warp's shared-memory ring.
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+// COMP: the state is the pair psi = psi + lo (psi.hi in p.psi, lo in p.lo); every stencil
+// quantity is formed from the hi parts, both donor passes add their fluxes with two-sums
+// (donor_comp) and both parts are stored.
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP>
 __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip, const int R0, T* ring_warp,
                                            const int lane) {
+  constexpr int kArr = arrs<COMP>();
   constexpr int kCols = cols<NC>();
   constexpr int kStride = stride<NC>();
   const int lc0 = NC * lane;
@@ -67,7 +74,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   for (int c = 0; c < NC; ++c) col[c] = wrapi(cs + lc0 + c, p.n1);
   T* ring = ring_warp + lc0;
   const int nt = p.ty + 6;
-  const T* src[kArr] = {p.psi, p.gc0, p.gc1, NUG ? p.G : nullptr, p.rhs_b ? p.R : nullptr};
+  const T* src[6] = {p.psi, p.gc0, p.gc1, NUG ? p.G : nullptr, p.rhs_b ? p.R : nullptr, COMP ? p.lo : nullptr};
   // prefetch cursor: next row to copy, its element offset and ring slot
   int pf_t = 0, pf_row = wrapi(R0 - 3, p.n0), pf_slot = 0;
   long long pf_off = static_cast<long long>(pf_row) * p.n1;
@@ -111,6 +118,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   T hi[3][NC], lo[3][NC];
   T pv0[2][NC], f0c[NC];
   T a0[2][NC], u0[2][NC], a1[2][NC], u1[2][NC], bu[2][NC], bd[2][NC], h0c[NC];
+  T lw[2][NC], l1[3][NC];  // COMP: lo of the loaded rows x-1, x and of pass 1's rows x-3 .. x-1
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
 #pragma unroll
@@ -123,6 +131,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       bu[k][c] = bd[k][c] = T(1);
     }
     f0c[c] = h0c[c] = T(0);
+    lw[0][c] = lw[1][c] = l1[0][c] = l1[1][c] = l1[2][c] = T(0);
   }
   p1r[0] = p1r[1] = p1r[2] = T(0);
 
@@ -140,10 +149,17 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       copy_row(v0[0], v0[1]); copy_row(v0[1], v0[2]);
       copy_row(v1[0], v1[1]); copy_row(v1[1], v1[2]);
       if (NUG) { copy_row(gg[0], gg[1]); copy_row(gg[1], gg[2]); copy_row(gg[2], gg[3]); }
+      if (COMP) copy_row(lw[0], lw[1]);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         T x = slot[c];
-        if (p.rhs_b) x = x + p.dt * slot[4 * kCols + c];
+        if (COMP) {
+          T e = slot[5 * kCols + c];
+          if (p.rhs_b) two_sum_acc(x, e, p.dt * slot[4 * kCols + c]);
+          lw[1][c] = e;
+        } else if (p.rhs_b) {
+          x = x + p.dt * slot[4 * kCols + c];
+        }
         ps[3][c] = x;
         v0[2][c] = slot[kCols + c] * p.scale;
         v1[2][c] = slot[2 * kCols + c] * p.scale;
@@ -162,13 +178,18 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
 #pragma unroll
       for (int c = 0; c < NC; ++c) F1[c] = flux(ps[2][c], right_of(ps[2], c, psR), v1[1][c]);
       const T F1L = from_left(F1);
-      T np1[NC];
+      T np1[NC], nl1[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const T rG = NUG ? fdiv(T(1), gg[2][c]) : T(1);
-        np1[c] = donor<T, NUG, KAHAN>(ps[2][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG);
+        if (COMP) {
+          np1[c] = donor_comp<T, NUG>(ps[2][c], lw[0][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG, nl1[c]);
+        } else {
+          np1[c] = donor<T, NUG, KAHAN>(ps[2][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG);
+        }
       }
       copy_row(p1[0], p1[1]); copy_row(p1[1], p1[2]); copy_row(p1[2], p1[3]); copy_row(p1[3], np1);
+      if (COMP) { copy_row(l1[0], l1[1]); copy_row(l1[1], l1[2]); copy_row(l1[2], nl1); }
       if (FCT) {
         copy_row(hi[0], hi[1]); copy_row(hi[1], hi[2]);
         copy_row(lo[0], lo[1]); copy_row(lo[1], lo[2]);
@@ -292,11 +313,15 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       if (S || t >= 6) {
         const T h1L = from_left(h1);
         const int row = R0 + t - 6;
-        T np2[NC];
+        T np2[NC], nl2[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T rG = NUG ? fdiv(T(1), gg[0][c]) : T(1);
-          np2[c] = donor<T, NUG, KAHAN>(p1[1][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
+          if (COMP) {
+            np2[c] = donor_comp<T, NUG>(p1[1][c], l1[0][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG, nl2[c]);
+          } else {
+            np2[c] = donor<T, NUG, KAHAN>(p1[1][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
+          }
         }
         if (row < p.n0) {
           const int gcol = strip * kStride + lc0 - kLead;
@@ -307,7 +332,19 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
           for (int c = 0; c < NC; ++c) {
             ok[c] = lc0 + c >= kLead && lc0 + c < kLead + kStride && gcol + c < p.n1;
             all = all && ok[c];
-            if (p.rhs_a && ok[c]) np2[c] = np2[c] + p.dt * p.R[o + c];
+            if (p.rhs_a && ok[c]) {
+              if (COMP) {
+                T e = nl2[c];
+                two_sum_acc(np2[c], e, p.dt * p.R[o + c]);
+                const T h = np2[c] + e;  // renormalise
+                const T bp = h - np2[c];
+                nl2[c] = (np2[c] - (h - bp)) + (e - bp);
+                np2[c] = h;
+              } else {
+                np2[c] = np2[c] + p.dt * p.R[o + c];
+              }
+            }
+            if (COMP && ok[c]) p.lo_out[o + c] = nl2[c];
           }
           if (p.vec && all) {
             if constexpr (sizeof(T) == 4 && NC == 4) {
@@ -337,8 +374,9 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   cp_wait<0>();
 }
 
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP>
 __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
+  constexpr int kArr = arrs<COMP>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long wid = static_cast<long long>(blockIdx.x) * kWarps + wib;
@@ -346,7 +384,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
   const int strip = static_cast<int>(wid % p.strips);
   const int R0 = static_cast<int>(wid / p.strips) * p.ty;
   T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * cols<NC>();
-  march_tile<T, NC, FCT, NUG, IGA, KAHAN>(p, strip, R0, ring, lane);
+  march_tile<T, NC, FCT, NUG, IGA, KAHAN, COMP>(p, strip, R0, ring, lane);
 }
 
 // Ensemble of fields: a persistent grid walks a table of (field, strip, row tile) items.
@@ -367,6 +405,7 @@ struct BatchParams {
 
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 __global__ void __launch_bounds__(kWarps * 32) k_fused2d_batched(const BatchParams<T> b) {
+  constexpr int kArr = arrs<false>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * cols<NC>();
@@ -391,22 +430,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_fused2d_batched(const BatchPara
     p.rhs_a = b.rhs_a;
     p.rhs_b = b.rhs_b;
     p.vec = fd.vec && b.vec_ok;
-    march_tile<T, NC, FCT, NUG, IGA, KAHAN>(p, local % fd.strips, (local / fd.strips) * b.ty, ring, lane);
+    p.lo = nullptr;
+    p.lo_out = nullptr;
+    march_tile<T, NC, FCT, NUG, IGA, KAHAN, false>(p, local % fd.strips, (local / fd.strips) * b.ty, ring, lane);
   }
 }
 
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP = false>
 void launch(const F2Params<T>& p, cudaStream_t st) {
   const long long warps = static_cast<long long>(p.strips) * p.rowtiles;
   const unsigned blocks = static_cast<unsigned>((warps + kWarps - 1) / kWarps);
-  const size_t smem = static_cast<size_t>(kWarps) * kSlots * kArr * cols<NC>() * sizeof(T);
+  const size_t smem = static_cast<size_t>(kWarps) * kSlots * arrs<COMP>() * cols<NC>() * sizeof(T);
   static bool attr_set = false;  // large rings exceed the default 48 KB of dynamic shared memory
   if (!attr_set) {
-    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
     attr_set = true;
   }
-  k_fused2d<T, NC, FCT, NUG, IGA, KAHAN><<<blocks, kWarps * 32, smem, st>>>(p);
+  k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP><<<blocks, kWarps * 32, smem, st>>>(p);
 }
 
 template <typename T, int NC, bool FCT, bool NUG>
@@ -433,7 +474,7 @@ bool al(const void* q, size_t a) { return q == nullptr || (reinterpret_cast<uint
 
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 void launch_b(const BatchParams<T>& b, cudaStream_t st) {
-  const size_t smem = static_cast<size_t>(kWarps) * kSlots * kArr * cols<NC>() * sizeof(T);
+  const size_t smem = static_cast<size_t>(kWarps) * kSlots * arrs<false>() * cols<NC>() * sizeof(T);
   static int grid = 0;  // persistent grid: every block that fits on the GPU at once
   if (grid == 0) {
     cudaFuncSetAttribute(k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -507,10 +548,12 @@ template int fused_batched_step<double>(const BatchTable&, const Opts&, const do
 namespace {
 }  // namespace
 
+namespace {
+
+// Warp-march parameters of one step of one field; *band is set when the automatic choice is
+// the band march.
 template <typename T>
-int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot) return MPDATA_EUNSUPPORTED;
-  if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+F2Params<T> warp_params(const Grid& g, const Opts& o, const StepArgs<T>& a, bool* band) {
   // FP32 lanes own 4 columns (16-byte copies), FP64 lanes 2 (register budget)
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   F2Params<T> p;
@@ -534,8 +577,7 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   // warps per SM), or in FP64 (arithmetic-bound: every recomputed halo row costs FP64
   // issue slots) with tiles of 16 rows or less, one front per block of warps (band
   // march) is faster.
-  const bool band_auto = sizeof(T) == 4 ? warps(8) < 608 : auto_ty <= 16;
-  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_step<T>(g, o, a, st);
+  *band = sizeof(T) == 4 ? warps(8) < 608 : auto_ty <= 16;
   p.ty = o.tile_rows > 0 ? o.tile_rows : auto_ty;
   p.rowtiles = (p.n0 + p.ty - 1) / p.ty;
   p.dt = a.dt;
@@ -545,7 +587,45 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   const size_t va = NC * sizeof(T) <= 16 ? NC * sizeof(T) : 16;
   p.vec = (p.n1 % NC == 0) && al(p.psi, va) && al(p.out, va) && al(p.gc0, va) && al(p.gc1, va) &&
           al(p.G, va) && al(p.R, va);
+  p.lo = nullptr;
+  p.lo_out = nullptr;
+  return p;
+}
+
+template <bool FCT, bool NUG>
+void launch_comp(const F2Params<float>& p, bool iga, cudaStream_t st) {
+  if (iga) launch<float, 4, FCT, NUG, true, false, true>(p, st);
+  else launch<float, 4, FCT, NUG, false, false, true>(p, st);
+}
+
+}  // namespace
+
+template <typename T>
+int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStream_t st) {
+  if (g.nd != 2 || o.n_iters != 2 || o.tot) return MPDATA_EUNSUPPORTED;
+  if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
+  bool band_auto = false;
+  const F2Params<T> p = warp_params(g, o, a, &band_auto);
+  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_step<T>(g, o, a, st);
   launch_all<T, NC>(p, o, st);
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, const float* lo_in, float* lo_out,
+                    cudaStream_t st) {
+  if (g.nd != 2 || o.n_iters != 2 || o.tot) return MPDATA_EUNSUPPORTED;
+  if (a.psi_out == a.psi_in || lo_out == lo_in) return MPDATA_EUNSUPPORTED;
+  bool band_auto = false;
+  F2Params<float> p = warp_params(g, o, a, &band_auto);  // the warp march carries the low parts
+  p.lo = lo_in;
+  p.lo_out = lo_out;
+  p.vec = p.vec && al(lo_in, 16) && al(lo_out, 16);
+  if (o.fct) {
+    if (o.nug) launch_comp<true, true>(p, o.iga, st); else launch_comp<true, false>(p, o.iga, st);
+  } else {
+    if (o.nug) launch_comp<false, true>(p, o.iga, st); else launch_comp<false, false>(p, o.iga, st);
+  }
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 

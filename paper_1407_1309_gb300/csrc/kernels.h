@@ -25,6 +25,12 @@ uint32_t handle_opts(const mpdata_s* h);
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 
+// The fused 2D step on a compensated FP32 state psi = hi + lo (fused2d.cu, warp march):
+// hi in a.psi_in / a.psi_out, lo in lo_in / lo_out.  MPDATA_EUNSUPPORTED outside 2D,
+// n_iters = 2, no tot, out of place.
+int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, const float* lo_in, float* lo_out,
+                    cudaStream_t st);
+
 // The same step with one marching front per block of warps (band2d.cu).
 template <typename T>
 int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t st);

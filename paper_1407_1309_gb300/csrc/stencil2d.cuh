@@ -74,6 +74,42 @@ __device__ __forceinline__ T donor(T p, T Fp0, T Fm0, T Fp1, T Fm1, T rG) {
   return NUG ? p + div * rG : p + div;
 }
 
+// s + t = u + err exactly (Knuth's two-sum, no magnitude condition); s <- u, e += err.
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& s, T& e, T t) {
+  const T u = s + t;
+  const T bp = u - s;
+  const T err = (s - (u - bp)) + (t - bp);
+  s = u;
+  e = e + err;
+}
+
+// Donor-cell update of Eq. 4 on a compensated state psi = hi + lo: the four face fluxes
+// (the same terms, in the same order, as the Kahan form) are added with two-sums whose
+// rounding errors collect in lo, and the pair is renormalised so that the returned hi is
+// the value of the representable sum nearest hi + lo.  A flux leaves one cell and enters
+// its neighbour with the same value, so sum(hi + lo) changes only by the rounding of the
+// small lo additions.
+template <typename T, bool NUG>
+__device__ __forceinline__ T donor_comp(T p, T lo, T Fp0, T Fm0, T Fp1, T Fm1, T rG, T& lo_out) {
+  if (NUG) {
+    Fp0 *= rG;
+    Fm0 *= rG;
+    Fp1 *= rG;
+    Fm1 *= rG;
+  }
+  T s = p, e = lo;
+  two_sum_acc(s, e, -Fp0);
+  two_sum_acc(s, e, Fm0);
+  two_sum_acc(s, e, -Fp1);
+  two_sum_acc(s, e, Fm1);
+  // renormalise with a full two-sum: after cancellation |e| may exceed |s|
+  const T h = s + e;
+  const T bp = h - s;
+  lo_out = (s - (h - bp)) + (e - bp);
+  return h;
+}
+
 // A row of NC columns held by one lane; the columns just outside come from the
 // neighbouring lanes.
 template <typename T, int NC> __device__ __forceinline__ T from_left(const T (&a)[NC]) {

@@ -49,6 +49,13 @@ class Mpdata:
         capi.mpdata_advance(self.h, psi_in, psi_out, gc, g, r, dt, n_steps, gc_scale)
         return psi_out
 
+    def advance_compensated(self, psi_in, lo_in, psi_out, lo_out, gc, g=None, r=None, dt=0.0, n_steps=1,
+                            gc_scale=None):
+        """advance() on the compensated FP32 state psi = hi + lo (FP32 handles, one 2D field,
+        n_iters = 2): hi in psi_*, lo in lo_*; returns (psi_out, lo_out)."""
+        capi.mpdata_advance_compensated(self.h, psi_in, lo_in, psi_out, lo_out, gc, g, r, dt, n_steps, gc_scale)
+        return psi_out, lo_out
+
     def adjoint_step(self, psi_n, gc, psi_bar, g=None, gc_bar=None):
         """psi_bar (in place): dL/dpsi^{n+1} -> dL/dpsi^n; gc_bar[d] += dL/dgc_d."""
         capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
