@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / staged / e2e / oracle legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and time the library's automatic kernel choice")
+    ap.add_argument("--n3d", type=int, default=256, help="side length of the deform3d workload")
     ap.add_argument("--kernel", choices=["warp", "band"], default=None,
                     help="time this fused kernel family (skips the autotuner)")
     ap.add_argument("--tile-rows", type=int, default=0, help="tile / band rows with --kernel (0 = automatic)")
@@ -858,7 +859,7 @@ def main():
     elif args.workload == "ensemble":
         run_ensemble(args)
     elif args.workload == "deform3d":
-        run_deform3d(args)
+        run_deform3d(args, args.n3d)
     else:
         run_ours(args)
 

@@ -41,9 +41,12 @@ template <int ND>
 __device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
   const int a = 3 - ND + d;
   const int n = g.n[a];
+  // |s| <= 2: two corrections each way wrap any extent n >= 1 (no loop)
   int v = x.c[a] + s;
-  while (v < 0) v += n;
-  while (v >= n) v -= n;
+  if (v < 0) v += n;
+  if (v < 0) v += n;
+  if (v >= n) v -= n;
+  if (v >= n) v -= n;
   x.c[a] = v;
   return x;
 }

@@ -42,9 +42,12 @@ template <int ND>
 __device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
   const int a = 3 - ND + d;
   const int n = g.n[a];
-  int v = x.c[a] + s;  // |s| <= 2: at most one wrap unless the extent is tiny
-  while (v < 0) v += n;
-  while (v >= n) v -= n;
+  // |s| <= 2: two corrections each way wrap any extent n >= 1 (no loop)
+  int v = x.c[a] + s;
+  if (v < 0) v += n;
+  if (v < 0) v += n;
+  if (v >= n) v -= n;
+  if (v >= n) v -= n;
   x.c[a] = v;
   return x;
 }
@@ -63,6 +66,8 @@ inline dim3 cell_grid(const Grid& g, int bs) {
   const unsigned gz = static_cast<unsigned>(g.n[0] < 65535 ? g.n[0] : 65535);
   return dim3(gx, gy, gz);
 }
+
+inline dim3 march3_grid(const Grid& g);
 
 // Linear index of a cell and the index offsets of its periodic neighbours: off[d][s+2]
 // moves s = -2..2 cells along dimension d.  Shifts along different dimensions wrap
@@ -241,6 +246,172 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
   }
 }
 
+// The same pseudo-advector for 3D fields as a z-march: a block owns a 32 x 8 tile of
+// (x, y) and walks down a chunk of z-planes, keeping rings of planes with their halos in
+// shared memory: psi on planes z-1 .. z+2 with x, y in [-1, +2] around the tile (the
+// third-order stencil reaches psi_{i-1} .. psi_{i+2} along the face's dimension and one
+// cell across it), the advector components and G on two planes with a one-cell halo.
+// Each cell's three faces are formed from the planes with the arithmetic of k_antidiff
+// (same expressions, same order).
+constexpr int kAx = 32, kAy = 8, kAz = 16;  // tile and z-chunk of the 3D march
+constexpr int kPw = kAx + 3, kPh = kAy + 3;  // psi plane with halo [-1, +2]
+constexpr int kVw = kAx + 2, kVh = kAy + 2;  // advector / G plane with halo [-1, +1]
+
+inline dim3 march3_grid(const Grid& g) {
+  return dim3(static_cast<unsigned>((g.n[2] + kAx - 1) / kAx), static_cast<unsigned>((g.n[1] + kAy - 1) / kAy),
+              static_cast<unsigned>((g.n[0] + kAz - 1) / kAz));
+}
+
+__device__ __forceinline__ int wrapc(int v, int n) {
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __restrict__ psi, In3<T> Vin,
+                                                         T vscale, const T* __restrict__ G, bool iga, bool tot,
+                                                         Out3<T> Vout) {
+  __shared__ T sP[4][kPh * kPw];
+  __shared__ T sV[3][2][kVh * kVw];  // [dimension][ring slot]
+  __shared__ T sG[2][kVh * kVw];
+  const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAx + tx;
+  constexpr int kT = kAx * kAy;
+  const int x0 = blockIdx.x * kAx, y0 = blockIdx.y * kAy;
+  const int zb = blockIdx.z * kAz;
+  const int ze = zb + kAz < nz ? zb + kAz : nz;
+  const long long plane = static_cast<long long>(ny) * nx;
+
+  // Every plane is copied with the same element assignment: this thread copies tile
+  // elements tid and tid + kT (when they exist); their in-plane source offsets are fixed.
+  static_assert(kPw * kPh <= 2 * kT && kVw * kVh <= 2 * kT, "two elements per thread cover a plane");
+  int offP[2], offV[2];
+  bool hasP1 = tid + kT < kPw * kPh, hasV1 = tid + kT < kVw * kVh;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = tid + r * kT;
+    {
+      const int yy = k / kPw, xx = k - yy * kPw;
+      offP[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + xx, nx);
+    }
+    {
+      const int yy = k / kVw, xx = k - yy * kVw;
+      offV[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + xx, nx);
+    }
+  }
+  auto zoff = [&](int z) { return static_cast<long long>(wrapc(z, nz)) * plane; };
+  auto loadP = [&](T* dst, int z) {
+    const T* src = psi + zoff(z);
+    dst[tid] = src[offP[0]];
+    if (hasP1) dst[tid + kT] = src[offP[1]];
+  };
+  auto loadV = [&](T* dst, const T* base, int z, T scale) {
+    const T* src = base + zoff(z);
+    dst[tid] = src[offV[0]] * scale;
+    if (hasV1) dst[tid + kT] = src[offV[1]] * scale;
+  };
+  // ring slots: psi planes zb-1 .., the z-component planes z-1 and z, the y and x components
+  // and G planes z and z+1
+  auto slotP = [&](int z) { return (z - zb + 1) & 3; };
+  auto slotVz = [&](int z) { return (z - zb + 1) & 1; };
+  auto slotVq = [&](int z) { return (z - zb) & 1; };
+
+  loadP(sP[slotP(zb - 1)], zb - 1);
+  loadP(sP[slotP(zb)], zb);
+  loadP(sP[slotP(zb + 1)], zb + 1);
+  loadV(sV[0][slotVz(zb - 1)], Vin.p[0], zb - 1, vscale);
+  loadV(sV[1][slotVq(zb)], Vin.p[1], zb, vscale);
+  loadV(sV[2][slotVq(zb)], Vin.p[2], zb, vscale);
+  if (G) loadV(sG[slotVq(zb)], G, zb, T(1));
+
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < nx && y < ny;
+  const int cP = (ty + 1) * kPw + (tx + 1), cV = (ty + 1) * kVw + (tx + 1);  // this cell in a plane
+  for (int z = zb; z < ze; ++z) {
+    loadP(sP[slotP(z + 2)], z + 2);
+    loadV(sV[0][slotVz(z)], Vin.p[0], z, vscale);
+    loadV(sV[1][slotVq(z + 1)], Vin.p[1], z + 1, vscale);
+    loadV(sV[2][slotVq(z + 1)], Vin.p[2], z + 1, vscale);
+    if (G) loadV(sG[slotVq(z + 1)], G, z + 1, T(1));
+    __syncthreads();
+    if (inside) {
+      // this cell's position in each plane of the rings; every neighbour below is a fixed
+      // offset from one of these
+      const T* pz[4] = {sP[slotP(z - 1)] + cP, sP[slotP(z)] + cP, sP[slotP(z + 1)] + cP, sP[slotP(z + 2)] + cP};
+      const T* vz[2] = {sV[0][slotVz(z - 1)] + cV, sV[0][slotVz(z)] + cV};      // z component, planes z-1, z
+      const T* vy[2] = {sV[1][slotVq(z)] + cV, sV[1][slotVq(z + 1)] + cV};      // y component, planes z, z+1
+      const T* vx[2] = {sV[2][slotVq(z)] + cV, sV[2][slotVq(z + 1)] + cV};      // x component, planes z, z+1
+      const T* gz[2] = {sG[slotVq(z)] + cV, sG[slotVq(z + 1)] + cV};
+      auto P = [&](int dz, int dy, int dx) { return pz[dz + 1][dy * kPw + dx]; };
+      auto Q = [&](int q, int dz, int dy, int dx) {
+        return q == 0 ? vz[dz + 1][dy * kVw + dx] : (q == 1 ? vy[dz][dy * kVw + dx] : vx[dz][dy * kVw + dx]);
+      };
+      auto Gv = [&](int dz, int dy, int dx) { return gz[dz][dy * kVw + dx]; };
+      const long long i = static_cast<long long>(z) * plane + static_cast<long long>(y) * nx + x;
+      const T p0 = P(0, 0, 0);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        // unit offsets of dimension d (0 = z, 1 = y, 2 = x)
+        const int dz = d == 0, dy = d == 1, dx = d == 2;
+        const T rGb = G ? qdiv(T(1), T(0.5) * (Gv(0, 0, 0) + Gv(dz, dy, dx))) : T(1);
+        const T V = Q(d, 0, 0, 0);
+        const T p1 = P(dz, dy, dx);
+        const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
+        T out = (absv(V) - V * V * rGb) * A;
+        T Vq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q == d) continue;
+          const int qz = q == 0, qy = q == 1, qx = q == 2;
+          Vq[q] = T(0.25) * ((Q(q, 0, 0, 0) + Q(q, dz, dy, dx)) + (Q(q, -qz, -qy, -qx) + Q(q, dz - qz, dy - qy, dx - qx)));
+          const T Tp = P(qz, qy, qx) + P(qz + dz, qy + dy, qx + dx);
+          const T Bt = P(-qz, -qy, -qx) + P(dz - qz, dy - qy, dx - qx);
+          const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
+          out = out - T(0.5) * V * Vq[q] * rGb * B;
+        }
+        if (tot) {
+          const T pm = P(-dz, -dy, -dx);
+          const T p2 = P(2 * dz, 2 * dy, 2 * dx);
+          const T num = ((p2 - p1) - p0) + pm;
+          const T D = iga ? num * T(0.25) : fracg(num, ((p2 + p1) + p0) + pm);
+          out = out + ((T(3) * V * absv(V)) * rGb - (T(2) * V * V * V) * (rGb * rGb) - V) * T(1.0 / 3.0) * D;
+          int qs[2] = {0, 0}, nq = 0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if (q == d) continue;
+            qs[nq++] = q;
+            const int qz = q == 0, qy = q == 1, qx = q == 2;
+            const T a = P(qz, qy, qx), b = P(qz + dz, qy + dy, qx + dx);
+            const T e = P(-qz, -qy, -qx), f = P(dz - qz, dy - qy, dx - qx);
+            const T n2 = (b - a) - (f - e);
+            const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
+            out = out + absv(V) * Vq[q] * rGb * (T(1) - T(2) * absv(V) * rGb) * D2;
+          }
+          T pr[4];
+          int m = 0;
+#pragma unroll
+          for (int s1 = 1; s1 >= -1; s1 -= 2) {
+#pragma unroll
+            for (int s2 = 1; s2 >= -1; s2 -= 2) {
+              const int oz = s1 * (qs[0] == 0) + s2 * (qs[1] == 0);
+              const int oy = s1 * (qs[0] == 1) + s2 * (qs[1] == 1);
+              const int ox = s1 * (qs[0] == 2) + s2 * (qs[1] == 2);
+              pr[m++] = P(oz, oy, ox) + P(oz + dz, oy + dy, ox + dx);
+            }
+          }
+          // pr = {(+,+), (+,-), (-,+), (-,-)}
+          const T n3 = (pr[0] - pr[1]) - (pr[2] - pr[3]);
+          const T D3 = iga ? n3 * T(0.125) : fracg(n3, (pr[0] + pr[1]) + (pr[2] + pr[3]));
+          out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] * (rGb * rGb) * D3;
+        }
+        Vout.p[d][i] = out;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // FCT limiting factors (Sect. 3.1.4): in/out sums of the unlimited fluxes and
 // beta_up = G [psi_max - psi]+ / in, beta_dn = G [psi - psi_min]+ / out (1 when the sum is 0).
 template <typename T, int ND>
@@ -322,7 +493,11 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   for (int k = 2; k <= K; ++k) {
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
-    k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+    if (ND == 3) {
+      k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+    } else {
+      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+    }
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
     if (o.fct) {
       k_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vuse, G, o.iga, s.mx, s.mn, s.bu, s.bd);
@@ -353,7 +528,12 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
   for (int k = 2; k <= K; ++k) {
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
-    k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
+    if (ND == 3) {
+      k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot,
+                                                                 vk);
+    } else {
+      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
+    }
     In3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (o.fct) {
       k_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, tp.bu[k], tp.bd[k]);
