@@ -432,7 +432,7 @@ def bench_config1(dev):
             "value": round(500 * 1000 / secs / 1e9, 4), "unit": UNIT,
             "err_vs_oracle_max_rel": float(np.abs(out - ref).max() / np.abs(ref).max()),
             "one_transit_rms_err_vs_initial": float(np.sqrt(np.mean((out - psi) ** 2))),
-            "path": "staged kernels (6 launches per step)"}
+            "path": "one launch of one block for all steps (field and intermediates in shared memory; FP64 rate of one SM)"}
 
 
 def bench_config3(dev, n=256, steps=20):

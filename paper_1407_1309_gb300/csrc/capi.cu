@@ -62,6 +62,13 @@ int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv
   // Every step reads one buffer and writes another: the result alternates between
   // psi_out and the handle's ping-pong buffer so that the last step lands in psi_out.
   // In place with an odd step count, psi is first copied to the ping-pong buffer.
+  // a small 1D field runs every step of the call in one launch of one block (it reads the
+  // whole field before writing, so in place needs no copy)
+  if (h->nd == 1 && h->n_fields == 1 && !o.staged && !gc_scale) {
+    const int rc = mpd::steps1d<T>(h->grids[0], o, psi_in, psi_out, gc[0], g, r, static_cast<T>(dt), n_steps,
+                                   h->stream);
+    if (rc != MPDATA_EUNSUPPORTED) return rc;
+  }
   T* X = psi_out;
   T* P = static_cast<T*>(h->pingpong);
   const T* cur = psi_in;

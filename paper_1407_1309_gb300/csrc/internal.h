@@ -90,6 +90,12 @@ template <typename T>
 cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a,
                         const StagedScratch<T>& s, cudaStream_t st);
 
+// Every step of a call for a 1D field in one launch of one block, when the field and its
+// intermediates fit in shared memory (13 arrays of n); MPDATA_EUNSUPPORTED otherwise.
+template <typename T>
+int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc, const T* G, const T* R, T dt,
+            int n_steps, cudaStream_t st);
+
 // Intermediates of one forward step kept for the adjoint (n_iters <= kTapeMax).
 constexpr int kTapeMax = 4;
 template <typename T>

@@ -463,6 +463,174 @@ __global__ void k_limit(Grid g, const T* __restrict__ psi, In3<T> Vu, bool unit,
   }
 }
 
+// Every step of a call for a 1D field small enough for shared memory: one block holds the
+// field and all intermediates in shared memory and runs the sub-steps above (same
+// expressions, same order) as passes over the field separated by block barriers, so the
+// call is one launch instead of several per step.  Advector scale 1 (no per-step factors).
+constexpr int kSteps1dThreads = 1024;
+constexpr int kSteps1dArrays = 13;  // state, psi^(0), two levels, gc, two advectors, unlimited, bounds, factors, G, R
+
+template <typename T>
+__global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps, Opts o, const T* __restrict__ psi_in,
+                                                             T* __restrict__ psi_out, const T* __restrict__ gc,
+                                                             const T* __restrict__ Gin, const T* __restrict__ Rin,
+                                                             T dt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const sm = reinterpret_cast<T*>(smem_raw);
+  T* st = sm;          // state psi^n
+  T* p0 = sm + n;      // psi^n + dt R (euler_b)
+  T* lev[2] = {sm + 2 * n, sm + 3 * n};
+  T* v0 = sm + 4 * n;  // the advector
+  T* vl[2] = {sm + 5 * n, sm + 6 * n};
+  T* vu = sm + 7 * n;
+  T* mx = sm + 8 * n;
+  T* mn = sm + 9 * n;
+  T* bu = sm + 10 * n;
+  T* bd = sm + 11 * n;
+  T* Gs = sm + 12 * n;
+  const T* G = o.nug ? Gs : nullptr;
+  const int K = o.n_iters;
+  auto L = [&](int i) { return i == 0 ? n - 1 : i - 1; };
+  auto Rt = [&](int i) { return i == n - 1 ? 0 : i + 1; };
+  auto R2 = [&](int i) { int j = i + 2; if (j >= n) j -= n; if (j >= n) j -= n; return j; };
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    st[i] = psi_in[i];
+    v0[i] = gc[i];
+    if (o.nug) Gs[i] = Gin[i];
+  }
+  __syncthreads();
+  // donor-cell pass of k_donor: src with advector v (flux of psi unless unit), to dst
+  auto donor = [&](const T* src, const T* v, bool unit, bool post, T* dst) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const T p = src[i];
+      T s = p, comp = T(0);
+      const T Gi = G ? G[i] : T(1);
+      const int ip = Rt(i), im = L(i);
+      const T vp = v[i], vm = v[im];
+      const T Fp = flux(p, src[ip], vp, unit);
+      const T Fm = flux(src[im], p, vm, unit);
+      const T t0 = G ? -qdiv(Fp, Gi) : -Fp;
+      const T t1 = G ? qdiv(Fm, Gi) : Fm;
+      if (o.kahan) {
+        T y = t0 - comp;
+        T u = s + y;
+        comp = (u - s) - y;
+        s = u;
+        y = t1 - comp;
+        u = s + y;
+        comp = (u - s) - y;
+        s = u;
+      } else {
+        s = s + t0;
+        s = s + t1;
+      }
+      if (post) s = s + dt * Rin[i];
+      dst[i] = s;
+    }
+  };
+  for (int step = 0; step < n_steps; ++step) {
+    const T* q0 = st;
+    if (o.rhs_b) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) p0[i] = st[i] + dt * Rin[i];
+      q0 = p0;
+      __syncthreads();
+    }
+    T* dst1 = K == 1 ? st : lev[0];  // with one pass the result is the new state
+    if (K == 1 && !o.rhs_b) dst1 = lev[0];
+    donor(q0, v0, false, K == 1 && o.rhs_a, dst1);
+    __syncthreads();
+    if (K == 1) {
+      if (dst1 != st) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) st[i] = dst1[i];
+        __syncthreads();
+      }
+      continue;
+    }
+    if (o.fct) {  // k_bounds
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T hi = q0[i] > lev[0][i] ? q0[i] : lev[0][i];
+        T lo = q0[i] < lev[0][i] ? q0[i] : lev[0][i];
+        const int js[2] = {L(i), Rt(i)};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const T a = q0[js[t]], b = lev[0][js[t]];
+          hi = a > hi ? a : hi;
+          hi = b > hi ? b : hi;
+          lo = a < lo ? a : lo;
+          lo = b < lo ? b : lo;
+        }
+        mx[i] = hi;
+        mn[i] = lo;
+      }
+    }
+    const T* prev = lev[0];
+    const T* vprev = v0;
+    for (int k = 2; k <= K; ++k) {
+      T* lim = vl[k % 2];
+      T* vk = o.fct ? vu : lim;
+      // k_antidiff (1D: no cross terms; third-order D_dd term)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const T pp0 = prev[i];
+        const int ip = Rt(i);
+        const T rGb = G ? qdiv(T(1), T(0.5) * (G[i] + G[ip])) : T(1);
+        const T V = vprev[i];
+        const T p1 = prev[ip];
+        const T A = o.iga ? (p1 - pp0) * T(0.5) : fracg(p1 - pp0, pp0 + p1);
+        T out = (absv(V) - V * V * rGb) * A;
+        if (o.tot) {
+          const T pm = prev[L(i)];
+          const T p2 = prev[R2(i)];
+          const T num = ((p2 - p1) - pp0) + pm;
+          const T D = o.iga ? num * T(0.25) : fracg(num, ((p2 + p1) + pp0) + pm);
+          out = out + ((T(3) * V * absv(V)) * rGb - (T(2) * V * V * V) * (rGb * rGb) - V) * T(1.0 / 3.0) * D;
+        }
+        vk[i] = out;
+      }
+      __syncthreads();
+      const T* vuse = vk;
+      if (o.fct) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {  // k_beta
+          const T p = prev[i];
+          T in = T(0), ou = T(0);
+          const int ip = Rt(i), im = L(i);
+          const T Fp = flux(p, prev[ip], vk[i], o.iga);
+          const T Fm = flux(prev[im], p, vk[im], o.iga);
+          in = in + (posp(Fm) - negp(Fp));
+          ou = ou + (posp(Fp) - negp(Fm));
+          const T Gi = G ? G[i] : T(1);
+          bu[i] = in > T(0) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
+          bd[i] = ou > T(0) ? qdiv(Gi * posp(p - mn[i]), ou) : T(1);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {  // k_limit
+          const T p = prev[i];
+          const int ip = Rt(i);
+          const T V = vk[i];
+          const T F = flux(p, prev[ip], V, o.iga);
+          const bool right = F > T(0) || (F == T(0) && V > T(0));
+          const T a = right ? bd[i] : bu[i];
+          const T b = right ? bu[ip] : bd[ip];
+          T m = T(1);
+          if (a < m) m = a;
+          if (b < m) m = b;
+          lim[i] = V * m;
+        }
+        __syncthreads();
+        vuse = lim;
+      }
+      T* dst = k == K ? st : (prev == lev[0] ? lev[1] : lev[0]);
+      donor(prev, vuse, o.iga, k == K && o.rhs_a, dst);
+      __syncthreads();
+      prev = dst;
+      vprev = vuse;
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) psi_out[i] = st[i];
+}
+
+template <typename T>
+size_t steps1d_smem(long long n) { return static_cast<size_t>(kSteps1dArrays) * static_cast<size_t>(n) * sizeof(T); }
+
 template <typename T, int ND>
 cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const StagedScratch<T>& s,
                       cudaStream_t st) {
@@ -597,6 +765,28 @@ template cudaError_t staged_forward_tape<double>(const Grid&, const Opts&, const
                                                  const Tape<double>&, double* const*, cudaStream_t);
 template StagedScratch<float> carve_staged<float>(void*, long long);
 template StagedScratch<double> carve_staged<double>(void*, long long);
+template <typename T>
+int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc, const T* G, const T* R, T dt,
+            int n_steps, cudaStream_t st) {
+  if (g.nd != 1 || o.n_iters > 64) return MPDATA_EUNSUPPORTED;
+  const size_t smem = steps1d_smem<T>(g.N);
+  static int max_smem = -1;
+  if (max_smem < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(k_steps1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  }
+  if (smem > static_cast<size_t>(max_smem)) return MPDATA_EUNSUPPORTED;
+  k_steps1d<T><<<1, kSteps1dThreads, smem, st>>>(static_cast<int>(g.N), n_steps, o, psi_in, psi_out, gc, G, R, dt);
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+template int steps1d<float>(const Grid&, const Opts&, const float*, float*, const float*, const float*,
+                            const float*, float, int, cudaStream_t);
+template int steps1d<double>(const Grid&, const Opts&, const double*, double*, const double*, const double*,
+                             const double*, double, int, cudaStream_t);
+
 template cudaError_t staged_step<float>(const Grid&, const Opts&, const StepArgs<float>&,
                                         const StagedScratch<float>&, cudaStream_t);
 template cudaError_t staged_step<double>(const Grid&, const Opts&, const StepArgs<double>&,

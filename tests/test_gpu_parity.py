@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from helpers import boxes, nondivergent, smooth_positive
-from paper_1407_1309_gb300 import capi
+from paper_1407_1309_gb300 import capi, workloads
 from paper_1407_1309_gb300.solver import Mpdata
 
 pytestmark = pytest.mark.gpu
@@ -188,3 +188,32 @@ def test_stop_flag_and_errors():
         assert capi.mpdata_step(m.h, psi, gc, n_steps=0, raw=True) == capi.EINVAL
         assert capi.mpdata_step(m.h, psi.data_ptr() + 2, gc, raw=True) == capi.EINVAL
         m.sync()
+
+
+@pytest.mark.parametrize("n", [7, 500, 2235, 3000])
+@pytest.mark.parametrize("name", ["basic", "fct", "tot3_fct", "iga_fct", "kahan_fct", "donor"])
+def test_1d_one_launch_path_matches_staged_and_oracle(n, name):
+    """1D fields small enough for shared memory run every step of a call in one launch of one
+    block (2235 FP64 cells is the largest; 3000 falls back to the per-sub-step kernels): same
+    arithmetic as the staged kernels, checked against them and against the oracle."""
+    n_iters, opts = {"basic": (2, 0), "fct": (2, capi.FCT), "tot3_fct": (3, capi.TOT | capi.FCT),
+                     "iga_fct": (2, capi.IGA | capi.FCT), "kahan_fct": (2, capi.KAHAN | capi.FCT),
+                     "donor": (1, 0)}[name]
+    rng = np.random.default_rng(n)
+    psi = workloads.hello_1d(n)[0] if n >= 400 else 1.0 + rng.uniform(size=n)
+    if opts & capi.IGA:
+        psi = psi - 0.5
+    gc = [np.full(n, 0.5) if n >= 400 else rng.uniform(-0.6, 0.6, size=n)]
+    dev = torch.device("cuda")
+    outs = []
+    for staged in (False, True):
+        with Mpdata((n,), dtype=torch.float64, n_iters=n_iters, opts=opts | (capi.STAGED if staged else 0)) as m:
+            a = torch.tensor(psi, dtype=torch.float64, device=dev)
+            b = torch.empty_like(a)
+            m.advance(a, b, [torch.tensor(gc[0], dtype=torch.float64, device=dev)], n_steps=40)
+            torch.cuda.synchronize()
+            outs.append(b.cpu().numpy())
+    ref = oracle.step(psi, gc, n_iters=n_iters, opts=opts, n_steps=40)
+    scale = np.abs(ref).max()
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-13 * scale
+    assert np.abs(outs[0] - ref).max() <= 1e-12 * scale
