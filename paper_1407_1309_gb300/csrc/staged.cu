@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "stencil2d.cuh"
 
 namespace mpd {
 namespace {
@@ -268,13 +269,23 @@ __device__ __forceinline__ int wrapc(int v, int n) {
   return v;
 }
 
+// rings of the z-march, one slot more than the planes in use so that the next step's
+// planes can be copied (cp.async) while this step computes
+constexpr int kA3P = 5, kA3V = 3;
+template <typename T>
+constexpr size_t antidiff3_smem() {
+  return sizeof(T) * (kA3P * kPw * kPh + (3 + 1) * kA3V * kVw * kVh);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __restrict__ psi, In3<T> Vin,
                                                          T vscale, const T* __restrict__ G, bool iga, bool tot,
                                                          Out3<T> Vout) {
-  __shared__ T sP[4][kPh * kPw];
-  __shared__ T sV[3][2][kVh * kVw];  // [dimension][ring slot]
-  __shared__ T sG[2][kVh * kVw];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int nP = kPw * kPh, nV = kVw * kVh;
+  T* const sP = reinterpret_cast<T*>(smem_raw);  // [kA3P][nP]
+  T* const sV = sP + kA3P * nP;                   // [3 dimensions][kA3V][nV]
+  T* const sG = sV + 3 * kA3V * nV;               // [kA3V][nV]
   const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAx + tx;
   constexpr int kT = kAx * kAy;
@@ -285,64 +296,89 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
 
   // Every plane is copied with the same element assignment: this thread copies tile
   // elements tid and tid + kT (when they exist); their in-plane source offsets are fixed.
-  static_assert(kPw * kPh <= 2 * kT && kVw * kVh <= 2 * kT, "two elements per thread cover a plane");
+  static_assert(nP <= 2 * kT && nV <= 2 * kT, "two elements per thread cover a plane");
   int offP[2], offV[2];
-  bool hasP1 = tid + kT < kPw * kPh, hasV1 = tid + kT < kVw * kVh;
+  const bool hasP1 = tid + kT < nP, hasV1 = tid + kT < nV;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int k = tid + r * kT;
-    {
-      const int yy = k / kPw, xx = k - yy * kPw;
-      offP[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + xx, nx);
-    }
-    {
-      const int yy = k / kVw, xx = k - yy * kVw;
-      offV[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + xx, nx);
-    }
+    int yy = k / kPw;
+    offP[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + (k - yy * kPw), nx);
+    yy = k / kVw;
+    offV[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + (k - yy * kVw), nx);
   }
   auto zoff = [&](int z) { return static_cast<long long>(wrapc(z, nz)) * plane; };
-  auto loadP = [&](T* dst, int z) {
+  auto copyP = [&](T* dst, int z) {
     const T* src = psi + zoff(z);
-    dst[tid] = src[offP[0]];
-    if (hasP1) dst[tid + kT] = src[offP[1]];
+    dev::cp_async<sizeof(T)>(dst + tid, src + offP[0]);
+    if (hasP1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + offP[1]);
   };
-  auto loadV = [&](T* dst, const T* base, int z, T scale) {
+  auto copyV = [&](T* dst, const T* base, int z) {
     const T* src = base + zoff(z);
-    dst[tid] = src[offV[0]] * scale;
-    if (hasV1) dst[tid + kT] = src[offV[1]] * scale;
+    dev::cp_async<sizeof(T)>(dst + tid, src + offV[0]);
+    if (hasV1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + offV[1]);
   };
-  // ring slots: psi planes zb-1 .., the z-component planes z-1 and z, the y and x components
-  // and G planes z and z+1
-  auto slotP = [&](int z) { return (z - zb + 1) & 3; };
-  auto slotVz = [&](int z) { return (z - zb + 1) & 1; };
-  auto slotVq = [&](int z) { return (z - zb) & 1; };
+  // after its copy has landed, this thread scales the advector elements it copied
+  auto scaleV = [&](T* dst) {
+    dst[tid] *= vscale;
+    if (hasV1) dst[tid + kT] *= vscale;
+  };
+  // ring slots: psi planes zb-1 ..; the z component planes z-1, z; the y, x components and G
+  // planes z, z+1
+  auto slotP = [&](int z) { return (z - zb + 1 + kA3P) % kA3P; };
+  auto slotVz = [&](int z) { return (z - zb + 1 + kA3V) % kA3V; };
+  auto slotVq = [&](int z) { return (z - zb + kA3V) % kA3V; };
+  auto Vp = [&](int d, int z) { return sV + (d * kA3V + (d == 0 ? slotVz(z) : slotVq(z))) * nV; };
+  auto Gp = [&](int z) { return sG + slotVq(z) * nV; };
+  // the planes that become needed at step z: psi z+2, z component z, y and x components and G z+1
+  auto copy_step = [&](int z) {
+    copyP(sP + slotP(z + 2) * nP, z + 2);
+    copyV(Vp(0, z), Vin.p[0], z);
+    copyV(Vp(1, z + 1), Vin.p[1], z + 1);
+    copyV(Vp(2, z + 1), Vin.p[2], z + 1);
+    if (G) copyV(Gp(z + 1), G, z + 1);
+  };
+  auto scale_step = [&](int z) {
+    if (vscale != T(1)) {
+      scaleV(Vp(0, z));
+      scaleV(Vp(1, z + 1));
+      scaleV(Vp(2, z + 1));
+    }
+  };
 
-  loadP(sP[slotP(zb - 1)], zb - 1);
-  loadP(sP[slotP(zb)], zb);
-  loadP(sP[slotP(zb + 1)], zb + 1);
-  loadV(sV[0][slotVz(zb - 1)], Vin.p[0], zb - 1, vscale);
-  loadV(sV[1][slotVq(zb)], Vin.p[1], zb, vscale);
-  loadV(sV[2][slotVq(zb)], Vin.p[2], zb, vscale);
-  if (G) loadV(sG[slotVq(zb)], G, zb, T(1));
+  copyP(sP + slotP(zb - 1) * nP, zb - 1);
+  copyP(sP + slotP(zb) * nP, zb);
+  copyP(sP + slotP(zb + 1) * nP, zb + 1);
+  copyV(Vp(0, zb - 1), Vin.p[0], zb - 1);
+  copyV(Vp(1, zb), Vin.p[1], zb);
+  copyV(Vp(2, zb), Vin.p[2], zb);
+  if (G) copyV(Gp(zb), G, zb);
+  copy_step(zb);
+  dev::cp_commit();
+  dev::cp_wait<0>();
+  if (vscale != T(1)) {
+    scaleV(Vp(0, zb - 1));
+    scaleV(Vp(1, zb));
+    scaleV(Vp(2, zb));
+  }
+  scale_step(zb);
 
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < nx && y < ny;
   const int cP = (ty + 1) * kPw + (tx + 1), cV = (ty + 1) * kVw + (tx + 1);  // this cell in a plane
   for (int z = zb; z < ze; ++z) {
-    loadP(sP[slotP(z + 2)], z + 2);
-    loadV(sV[0][slotVz(z)], Vin.p[0], z, vscale);
-    loadV(sV[1][slotVq(z + 1)], Vin.p[1], z + 1, vscale);
-    loadV(sV[2][slotVq(z + 1)], Vin.p[2], z + 1, vscale);
-    if (G) loadV(sG[slotVq(z + 1)], G, z + 1, T(1));
-    __syncthreads();
+    __syncthreads();  // step z's planes are in (each thread waited for its own copies)
+    if (z + 1 < ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    dev::cp_commit();
     if (inside) {
       // this cell's position in each plane of the rings; every neighbour below is a fixed
       // offset from one of these
-      const T* pz[4] = {sP[slotP(z - 1)] + cP, sP[slotP(z)] + cP, sP[slotP(z + 1)] + cP, sP[slotP(z + 2)] + cP};
-      const T* vz[2] = {sV[0][slotVz(z - 1)] + cV, sV[0][slotVz(z)] + cV};      // z component, planes z-1, z
-      const T* vy[2] = {sV[1][slotVq(z)] + cV, sV[1][slotVq(z + 1)] + cV};      // y component, planes z, z+1
-      const T* vx[2] = {sV[2][slotVq(z)] + cV, sV[2][slotVq(z + 1)] + cV};      // x component, planes z, z+1
-      const T* gz[2] = {sG[slotVq(z)] + cV, sG[slotVq(z + 1)] + cV};
+      const T* pz[4] = {sP + slotP(z - 1) * nP + cP, sP + slotP(z) * nP + cP, sP + slotP(z + 1) * nP + cP,
+                        sP + slotP(z + 2) * nP + cP};
+      const T* vz[2] = {Vp(0, z - 1) + cV, Vp(0, z) + cV};      // z component, planes z-1, z
+      const T* vy[2] = {Vp(1, z) + cV, Vp(1, z + 1) + cV};      // y component, planes z, z+1
+      const T* vx[2] = {Vp(2, z) + cV, Vp(2, z + 1) + cV};      // x component, planes z, z+1
+      const T* gz[2] = {Gp(z) + cV, Gp(z + 1) + cV};
       auto P = [&](int dz, int dy, int dx) { return pz[dz + 1][dy * kPw + dx]; };
       auto Q = [&](int q, int dz, int dy, int dx) {
         return q == 0 ? vz[dz + 1][dy * kVw + dx] : (q == 1 ? vy[dz][dy * kVw + dx] : vx[dz][dy * kVw + dx]);
@@ -408,7 +444,217 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
         Vout.p[d][i] = out;
       }
     }
+    dev::cp_wait<0>();
+    if (z + 1 < ze) scale_step(z + 1);  // only planes copied in this step are scaled
+  }
+}
+
+// One FCT corrective pass of a 3D field as a z-march (the work of k_beta, k_limit and
+// k_donor, same expressions, same order): at plane z the limiting factors of plane z are
+// formed on the tile and a one-cell halo into a ring of three planes; then plane z-1 is
+// limited (its faces' factors are all there) and advanced by the donor-cell pass.  The
+// limited advector is written out only when another pass follows (lim != null).
+// Shared tiles: psi with halo [-2, +2] on planes z-2 .. z+1; the x and y pseudo-advector
+// components with halo [-2, +1] on planes z-1, z; the z component, the factors, the bounds
+// and G with halo [-1, +1] (z component on planes z-2 .. z, factors on z-2 .. z, G on z-1, z).
+constexpr int kCPw = kAx + 4, kCPh = kAy + 4;  // psi
+constexpr int kCVw = kAx + 3, kCVh = kAy + 3;  // x, y components
+constexpr int kCBw = kAx + 2, kCBh = kAy + 2;  // z component, factors, bounds, G
+// ring depths: planes in use plus one being copied (cp.async) for the next step
+constexpr int kC3P = 5, kC3Vq = 3, kC3Vz = 4, kC3B = 3, kC3M = 2, kC3G = 3;
+template <typename T>
+constexpr size_t corr3_smem() {
+  return sizeof(T) * (kC3P * kCPw * kCPh + 2 * kC3Vq * kCVw * kCVh +
+                      (kC3Vz + 2 * kC3B + 2 * kC3M + kC3G) * kCBw * kCBh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict__ psi, In3<T> Vu,
+                                                     const T* __restrict__ G, bool unit, bool kahan,
+                                                     const T* __restrict__ mxg, const T* __restrict__ mng,
+                                                     const T* __restrict__ R, T dt, bool post, Out3<T> lim,
+                                                     T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const sm = reinterpret_cast<T*>(smem_raw);
+  constexpr int nP = kCPw * kCPh, nV = kCVw * kCVh, nB = kCBw * kCBh;
+  T* const sP = sm;                    // [kC3P][nP]
+  T* const sVx = sP + kC3P * nP;       // [kC3Vq][nV]
+  T* const sVy = sVx + kC3Vq * nV;     // [kC3Vq][nV]
+  T* const sVz = sVy + kC3Vq * nV;     // [kC3Vz][nB]
+  T* const sBu = sVz + kC3Vz * nB;     // [kC3B][nB]
+  T* const sBd = sBu + kC3B * nB;      // [kC3B][nB]
+  T* const sMx = sBd + kC3B * nB;      // [kC3M][nB]
+  T* const sMn = sMx + kC3M * nB;      // [kC3M][nB]
+  T* const sG = sMn + kC3M * nB;       // [kC3G][nB]
+  const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAx + tx;
+  constexpr int kT = kAx * kAy;
+  const int x0 = blockIdx.x * kAx, y0 = blockIdx.y * kAy;
+  const int zb = blockIdx.z * kAz;
+  const int ze = zb + kAz < nz ? zb + kAz : nz;
+  const long long plane = static_cast<long long>(ny) * nx;
+  static_assert(nP <= 2 * kT && nV <= 2 * kT && nB <= 2 * kT, "two elements per thread cover a plane");
+
+  // fixed in-plane source offsets of the (at most two) tile elements this thread copies
+  int offP[2], offV[2], offB[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = tid + r * kT;
+    int yy = k / kCPw;
+    offP[r] = wrapc(y0 - 2 + yy, ny) * nx + wrapc(x0 - 2 + (k - yy * kCPw), nx);
+    yy = k / kCVw;
+    offV[r] = wrapc(y0 - 2 + yy, ny) * nx + wrapc(x0 - 2 + (k - yy * kCVw), nx);
+    yy = k / kCBw;
+    offB[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + (k - yy * kCBw), nx);
+  }
+  auto zoff = [&](int z) { return static_cast<long long>(wrapc(z, nz)) * plane; };
+  auto copy = [&](T* dst, const T* src, const int (&off)[2], int count) {
+    dev::cp_async<sizeof(T)>(dst + tid, src + off[0]);
+    if (tid + kT < count) dev::cp_async<sizeof(T)>(dst + tid + kT, src + off[1]);
+  };
+  auto slot = [&](int z, int n) { return (z - zb + 4 * n) % n; };
+  auto P_ = [&](int z) { return sP + slot(z, kC3P) * nP; };
+  auto Vx_ = [&](int z) { return sVx + slot(z, kC3Vq) * nV; };
+  auto Vy_ = [&](int z) { return sVy + slot(z, kC3Vq) * nV; };
+  auto Vz_ = [&](int z) { return sVz + slot(z, kC3Vz) * nB; };
+  auto Bu_ = [&](int z) { return sBu + slot(z, kC3B) * nB; };
+  auto Bd_ = [&](int z) { return sBd + slot(z, kC3B) * nB; };
+  auto Mx_ = [&](int z) { return sMx + slot(z, kC3M) * nB; };
+  auto Mn_ = [&](int z) { return sMn + slot(z, kC3M) * nB; };
+  auto G_ = [&](int z) { return sG + slot(z, kC3G) * nB; };
+  // the planes that become needed at step z: psi z+1, the components, bounds and G of plane z
+  auto copy_step = [&](int z) {
+    copy(P_(z + 1), psi + zoff(z + 1), offP, nP);
+    copy(Vx_(z), Vu.p[2] + zoff(z), offV, nV);
+    copy(Vy_(z), Vu.p[1] + zoff(z), offV, nV);
+    copy(Vz_(z), Vu.p[0] + zoff(z), offB, nB);
+    copy(Mx_(z), mxg + zoff(z), offB, nB);
+    copy(Mn_(z), mng + zoff(z), offB, nB);
+    if (G) copy(G_(z), G + zoff(z), offB, nB);
+  };
+
+  // prologue: psi planes zb-2, zb-1, the z component of plane zb-2, then step zb-1's planes
+  copy(P_(zb - 2), psi + zoff(zb - 2), offP, nP);
+  copy(P_(zb - 1), psi + zoff(zb - 1), offP, nP);
+  copy(Vz_(zb - 2), Vu.p[0] + zoff(zb - 2), offB, nB);
+  copy_step(zb - 1);
+  dev::cp_commit();
+  dev::cp_wait<0>();
+
+  for (int z = zb - 1; z <= ze; ++z) {
+    __syncthreads();  // step z's planes are in (each thread waited for its own copies)
+    if (z + 1 <= ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    dev::cp_commit();
+    const T* sMxz = Mx_(z);
+    const T* sMnz = Mn_(z);
+    {  // limiting factors of plane z on the tile and a one-cell halo (k_beta)
+      const T* pm = P_(z - 1);
+      const T* p0 = P_(z);
+      const T* pp = P_(z + 1);
+      const T* vx = Vx_(z);
+      const T* vy = Vy_(z);
+      const T* vzm = Vz_(z - 1);
+      const T* vz0 = Vz_(z);
+      const T* gz = G_(z);
+      T* bu = Bu_(z);
+      T* bd = Bd_(z);
+      for (int r = tid; r < nB; r += kT) {
+        const int by = r / kCBw, bx = r - by * kCBw;  // cell (bx - 1, by - 1) of the tile
+        const int cp = (by + 1) * kCPw + (bx + 1);    // in the psi tile
+        const int cv = (by + 1) * kCVw + (bx + 1);    // in the x, y component tiles
+        const T p = p0[cp];
+        T in = T(0), ou = T(0);
+        {  // dimension 0 (z)
+          const T Fp = flux(p, pp[cp], vz0[r], unit);
+          const T Fm = flux(pm[cp], p, vzm[r], unit);
+          in = in + (posp(Fm) - negp(Fp));
+          ou = ou + (posp(Fp) - negp(Fm));
+        }
+        {  // dimension 1 (y)
+          const T Fp = flux(p, p0[cp + kCPw], vy[cv], unit);
+          const T Fm = flux(p0[cp - kCPw], p, vy[cv - kCVw], unit);
+          in = in + (posp(Fm) - negp(Fp));
+          ou = ou + (posp(Fp) - negp(Fm));
+        }
+        {  // dimension 2 (x)
+          const T Fp = flux(p, p0[cp + 1], vx[cv], unit);
+          const T Fm = flux(p0[cp - 1], p, vx[cv - 1], unit);
+          in = in + (posp(Fm) - negp(Fp));
+          ou = ou + (posp(Fp) - negp(Fm));
+        }
+        const T Gi = G ? gz[r] : T(1);
+        bu[r] = in > T(0) ? qdiv(Gi * posp(sMxz[r] - p), in) : T(1);
+        bd[r] = ou > T(0) ? qdiv(Gi * posp(p - sMnz[r]), ou) : T(1);
+      }
+    }
     __syncthreads();
+    const int q = z - 1;
+    const int x = x0 + tx, y = y0 + ty;
+    if (q >= zb && x < nx && y < ny) {  // limit and donor of plane q (k_limit, k_donor)
+      const T* ps[3] = {P_(q - 1), P_(q), P_(q + 1)};
+      const T* bus[3] = {Bu_(q - 1), Bu_(q), Bu_(q + 1)};
+      const T* bds[3] = {Bd_(q - 1), Bd_(q), Bd_(q + 1)};
+      const T* vx = Vx_(q);
+      const T* vy = Vy_(q);
+      const T* vzm = Vz_(q - 1);
+      const T* vz0 = Vz_(q);
+      const int cp = (ty + 2) * kCPw + (tx + 2), cv = (ty + 2) * kCVw + (tx + 2), cb = (ty + 1) * kCBw + (tx + 1);
+      const T p = ps[1][cp];
+      // limited advector at a face: V m, m = min(1, factor of the upwind side, factor of the downwind side)
+      auto limit = [&](T L, T Rr, T V, T buL, T bdL, T buR, T bdR) {
+        const T F = flux(L, Rr, V, unit);
+        const bool right = F > T(0) || (F == T(0) && V > T(0));
+        const T a = right ? bdL : buL;
+        const T b = right ? buR : bdR;
+        T m = T(1);
+        if (a < m) m = a;
+        if (b < m) m = b;
+        return V * m;
+      };
+      // faces (d, +) and (d, -) of this cell: psi, limited advector
+      const T pz_p = ps[2][cp], pz_m = ps[0][cp];
+      const T py_p = ps[1][cp + kCPw], py_m = ps[1][cp - kCPw];
+      const T px_p = ps[1][cp + 1], px_m = ps[1][cp - 1];
+      const T hz_p = limit(p, pz_p, vz0[cb], bus[1][cb], bds[1][cb], bus[2][cb], bds[2][cb]);
+      const T hz_m = limit(pz_m, p, vzm[cb], bus[0][cb], bds[0][cb], bus[1][cb], bds[1][cb]);
+      const T hy_p = limit(p, py_p, vy[cv], bus[1][cb], bds[1][cb], bus[1][cb + kCBw], bds[1][cb + kCBw]);
+      const T hy_m = limit(py_m, p, vy[cv - kCVw], bus[1][cb - kCBw], bds[1][cb - kCBw], bus[1][cb], bds[1][cb]);
+      const T hx_p = limit(p, px_p, vx[cv], bus[1][cb], bds[1][cb], bus[1][cb + 1], bds[1][cb + 1]);
+      const T hx_m = limit(px_m, p, vx[cv - 1], bus[1][cb - 1], bds[1][cb - 1], bus[1][cb], bds[1][cb]);
+      const long long i = static_cast<long long>(q) * plane + static_cast<long long>(y) * nx + x;
+      if (lim.p[0]) {
+        lim.p[0][i] = hz_p;
+        lim.p[1][i] = hy_p;
+        lim.p[2][i] = hx_p;
+      }
+      const T Gi = G ? G_(q)[cb] : T(1);
+      T s = p, comp = T(0);
+      const T hp[3] = {hz_p, hy_p, hx_p}, hm[3] = {hz_m, hy_m, hx_m};
+      const T np_[3] = {pz_p, py_p, px_p}, nm_[3] = {pz_m, py_m, px_m};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T Fp = flux(p, np_[d], hp[d], unit);
+        const T Fm = flux(nm_[d], p, hm[d], unit);
+        const T t0 = G ? -qdiv(Fp, Gi) : -Fp;
+        const T t1 = G ? qdiv(Fm, Gi) : Fm;
+        if (kahan) {
+          T yk = t0 - comp;
+          T u = s + yk;
+          comp = (u - s) - yk;
+          s = u;
+          yk = t1 - comp;
+          u = s + yk;
+          comp = (u - s) - yk;
+          s = u;
+        } else {
+          s = s + t0;
+          s = s + t1;
+        }
+      }
+      if (post) s = s + dt * R[i];
+      out[i] = s;
+    }
+    dev::cp_wait<0>();
   }
 }
 
@@ -631,6 +877,30 @@ __global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps,
 template <typename T>
 size_t steps1d_smem(long long n) { return static_cast<size_t>(kSteps1dArrays) * static_cast<size_t>(n) * sizeof(T); }
 
+template <typename T>
+void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, Out3<T> out,
+                      cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_antidiff3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(antidiff3_smem<T>()));
+    attr = true;
+  }
+  k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, out);
+}
+
+template <typename T>
+void launch_corr3(const Grid& g, const T* psi, In3<T> vu, const T* G, bool unit, bool kahan, const T* mx,
+                  const T* mn, const T* R, T dt, bool post, Out3<T> lim, T* out, cudaStream_t st) {
+  static bool attr = false;  // the FP64 rings exceed the default 48 KB of dynamic shared memory
+  if (!attr) {
+    cudaFuncSetAttribute(k_corr3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(corr3_smem<T>()));
+    attr = true;
+  }
+  k_corr3<T><<<march3_grid(g), dim3(kAx, kAy), corr3_smem<T>(), st>>>(g, psi, vu, G, unit, kahan, mx, mn, R, dt,
+                                                                      post, lim, out);
+}
+
 template <typename T, int ND>
 cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const StagedScratch<T>& s,
                       cudaStream_t st) {
@@ -662,11 +932,21 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
     if (ND == 3) {
-      k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+      launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
     }
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
+    if (ND == 3 && o.fct) {  // factors, limiter and donor pass in one z-march
+      T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
+      Out3<T> lk{{nullptr, nullptr, nullptr}};
+      if (k < K) lk = Out3<T>{{lim[0], lim[1], lim[2]}};
+      launch_corr3<T>(g, prev, vuse, G, o.iga, o.kahan, s.mx, s.mn, a.r, a.dt, k == K && o.rhs_a, lk, dst, st);
+      prev = dst;
+      vprev = In3<T>{{lim[0], lim[1], lim[2]}};
+      vscale = T(1);
+      continue;
+    }
     if (o.fct) {
       k_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vuse, G, o.iga, s.mx, s.mn, s.bu, s.bd);
       Out3<T> vl{{lim[0], lim[1], lim[2]}};
@@ -697,8 +977,7 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (ND == 3) {
-      k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot,
-                                                                 vk);
+      launch_antidiff3<T>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
     }
