@@ -937,7 +937,10 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
     }
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
-    if (ND == 3 && o.fct) {  // factors, limiter and donor pass in one z-march
+    // FP32: factors, limiter and donor pass in one z-march (it limits each face from both sides
+    // and forms the factors on a one-cell halo: cheaper than the array traffic it saves in
+    // FP32, dearer in FP64, which the arithmetic bounds)
+    if (ND == 3 && o.fct && sizeof(T) == 4) {
       T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
       Out3<T> lk{{nullptr, nullptr, nullptr}};
       if (k < K) lk = Out3<T>{{lim[0], lim[1], lim[2]}};
