@@ -231,6 +231,16 @@ int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, int n_iters,
                         const void* psi_in, void* psi_out, const void* const* gc, const void* g,
                         const void* r, double dt, void* cuda_stream);
 
+/*
+ * Diagnostic (no counterpart in the paper): q[i] = n[i] / d[i] for count device doubles,
+ * computed with the FP64 division the kernels use (Newton-Raphson reciprocal iteration from
+ * the approximate FP64 reciprocal, two iterations, remainder-corrected quotient: within one
+ * unit in the last place for normal operands; a zero, infinite or NaN divisor gives NaN).
+ * Asynchronous on cuda_stream.  EINVAL for a negative count or null pointers.
+ */
+int mpdata_selftest_division(const double* n, const double* d, double* q, int64_t count,
+                             void* cuda_stream);
+
 /* Static description of a status code. */
 const char* mpdata_strerror(int code);
 

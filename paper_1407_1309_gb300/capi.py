@@ -23,7 +23,7 @@ EXPORTED = (
     "mpdata_create", "mpdata_step", "mpdata_advance", "mpdata_adjoint_step", "mpdata_reduce",
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
-    "mpdata_advance_compensated",
+    "mpdata_advance_compensated", "mpdata_selftest_division",
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
@@ -65,6 +65,7 @@ def load(build_if_needed: bool = True):
             "mpdata_step": ([P, P, PP, P, P, D, I], I),
             "mpdata_advance": ([P, P, P, PP, P, P, D, I, DP], I),
             "mpdata_advance_compensated": ([P, P, P, P, P, PP, P, P, D, I, DP], I),
+            "mpdata_selftest_division": ([P, P, P, I64, P], I),
             "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
             "mpdata_reduce": ([P, P, P, DP], I),
             "mpdata_diff_norms": ([P, P, P, DP, DP], I),
@@ -176,6 +177,12 @@ def mpdata_advance_compensated(h, psi_in, lo_in, psi_out, lo_out, gc, g=None, r=
     if raw:
         return rc
     _check(rc, "mpdata_advance_compensated")
+
+
+def mpdata_selftest_division(n, d, q, stream=None):
+    """q = n / d elementwise with the kernels' FP64 division (device float64 tensors)."""
+    _check(load().mpdata_selftest_division(_ptr(n), _ptr(d), _ptr(q), int(q.numel()), _ptr(stream)),
+           "mpdata_selftest_division")
 
 
 def prepare_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1):

@@ -23,10 +23,12 @@ namespace {
 template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
 template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
-// n / d: FP32 uses the fast division (rcp and multiply, 2 ulp), FP64 the IEEE one
+// n / d: FP32 uses the fast division (rcp and multiply, 2 ulp), FP64 the Newton-Raphson
+// division with remainder correction of stencil2d.cuh (within 1 ulp; NaN for a zero divisor,
+// which the callers guard or map to a factor of 1)
 template <typename T> __device__ __forceinline__ T qdiv(T n, T d);
 template <> __device__ __forceinline__ float qdiv<float>(float n, float d) { return __fdividef(n, d); }
-template <> __device__ __forceinline__ double qdiv<double>(double n, double d) { return n / d; }
+template <> __device__ __forceinline__ double qdiv<double>(double n, double d) { return dev::nr_div(n, d); }
 // psi-fraction with the zero-denominator guard (the ratio of Eq. 6 is 0 when its sum is 0)
 template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return d != T(0) ? qdiv(n, d) : T(0); }
 

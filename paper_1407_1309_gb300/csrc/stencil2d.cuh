@@ -18,7 +18,24 @@ __device__ __forceinline__ int wrapi(int c, int n) {
 
 template <typename T> __device__ __forceinline__ T fdiv(T a, T b);
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
-template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+// FP64 n / d for the arithmetic-bound FP64 kernels: Newton-Raphson reciprocal iteration
+// r <- r + r (1 - d r) (quadratic convergence) from the PTX approximate FP64 reciprocal
+// (rcp.approx.ftz.f64, full exponent range), two iterations, and Markstein's remainder
+// correction q <- q + r (n - d q) of the quotient: within one unit in the last place of the
+// exact quotient for normal operands.  A zero, infinite or NaN divisor gives NaN (the
+// kernels never rely on it: the psi-ratio guards zero sums, and the FCT factors' min(1, x)
+// maps the inf or NaN of a zero flux sum to 1 alike).
+__device__ __forceinline__ double nr_div(double n, double d) {
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(d));
+  double e = fma(-d, r0, 1.0);
+  double r = fma(r0, e, r0);
+  e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  const double q = n * r;
+  return fma(r, fma(-d, q, n), q);
+}
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return nr_div(a, b); }
 
 template <typename T> __device__ __forceinline__ T posp(T x) { return x > T(0) ? x : T(0); }
 template <typename T> __device__ __forceinline__ T negp(T x) { return x < T(0) ? x : T(0); }
