@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "stencil2d.cuh"
 
 namespace mpd {
 namespace {
@@ -29,6 +30,11 @@ template <typename T> __device__ __forceinline__ T dpos(T x) { return x > T(0) ?
 template <typename T> __device__ __forceinline__ T dneg(T x) { return x < T(0) ? T(1) : (x > T(0) ? T(0) : T(0.5)); }
 template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+// n / d as in the forward kernels: fast division in FP32, Newton-Raphson division (within one
+// ulp) in FP64; every divisor here is a G, a nonzero psi sum or a nonzero flux sum
+template <typename T> __device__ __forceinline__ T adiv(T n, T d);
+template <> __device__ __forceinline__ float adiv<float>(float n, float d) { return __fdividef(n, d); }
+template <> __device__ __forceinline__ double adiv<double>(double n, double d) { return dev::nr_div(n, d); }
 
 template <typename T> struct P3 { const T* p[3]; };
 template <typename T> struct W3 { T* p[3]; };
@@ -101,13 +107,13 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
                               const T* __restrict__ G, bool unit, T* __restrict__ pb_prev, W3<T> vhb,
                               T* __restrict__ psi_out, W3<T> gc_out) {
   CELL_INDEX
-  const T gi = G ? pb[i] / G[i] : pb[i];
+  const T gi = G ? adiv(pb[i], G[i]) : pb[i];
   T acc = pb[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1), im = nb.at(d, -1);
-    const T gp = G ? pb[ip] / G[ip] : pb[ip];
-    const T gm = G ? pb[im] / G[im] : pb[im];
+    const T gp = G ? adiv(pb[ip], G[ip]) : pb[ip];
+    const T gm = G ? adiv(pb[im], G[im]) : pb[im];
     const T fp = gp - gi;  // dL/dF on the face (d, i)
     const T fm = gi - gm;  // dL/dF on the face (d, i - e_d)
     const T v = V.p[d][i], vm = V.p[d][im];
@@ -180,18 +186,18 @@ __global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__
   T gin = T(0), gout = T(0), pacc = T(0);
   const T gu = bub[i], gd = bdb[i];
   if (in > T(0) && gu != T(0)) {
-    const T beta = Gi * posp(mx[i] - p) / in;
-    const T t = gu * Gi * dpos(mx[i] - p) / in;
+    const T beta = adiv(Gi * posp(mx[i] - p), in);
+    const T t = adiv(gu * Gi * dpos(mx[i] - p), in);
     mxb[i] += t;
     pacc -= t;
-    gin = -gu * beta / in;
+    gin = adiv(-gu * beta, in);
   }
   if (ou > T(0) && gd != T(0)) {
-    const T beta = Gi * posp(p - mn[i]) / ou;
-    const T t = gd * Gi * dpos(p - mn[i]) / ou;
+    const T beta = adiv(Gi * posp(p - mn[i]), ou);
+    const T t = adiv(gd * Gi * dpos(p - mn[i]), ou);
     pacc += t;
     mnb[i] -= t;
-    gout = -gd * beta / ou;
+    gout = adiv(-gd * beta, ou);
   }
   if (gin != T(0) || gout != T(0)) {
 #pragma unroll
@@ -247,13 +253,15 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
     } else {
       const T s = p0 + p1;
       if (s != T(0)) {
-        A = (p1 - p0) / s; dA0 = T(-2) * p1 / (s * s); dA1 = T(2) * p0 / (s * s);
+        const T r = adiv(T(1), s);
+        A = (p1 - p0) * r; dA0 = T(-2) * p1 * (r * r); dA1 = T(2) * p0 * (r * r);
       } else {
         A = dA0 = dA1 = T(0);
       }
     }
-    const T c = absv(V) - V * V / Gb;
-    T gV = gout * (sgn(V) - T(2) * V / Gb) * A;
+    const T rGb = G ? adiv(T(1), Gb) : T(1);
+    const T c = absv(V) - V * V * rGb;
+    T gV = gout * (sgn(V) - T(2) * V * rGb) * A;
     atomicAdd(&pb[i], gout * c * dA0);
     atomicAdd(&pb[ip], gout * c * dA1);
 #pragma unroll
@@ -270,18 +278,19 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
       } else {
         const T S = Tp + Bt;
         if (S != T(0)) {
-          B = (Tp - Bt) / S; dBT = T(2) * Bt / (S * S); dBB = T(-2) * Tp / (S * S);
+          const T r = adiv(T(1), S);
+          B = (Tp - Bt) * r; dBT = T(2) * Bt * (r * r); dBB = T(-2) * Tp * (r * r);
         } else {
           B = dBT = dBB = T(0);
         }
       }
-      gV += gout * (T(-0.5) * Vq / Gb * B);
-      const T gq = gout * (T(-0.5) * V / Gb * B) * T(0.25);
+      gV += gout * (T(-0.5) * Vq * rGb * B);
+      const T gq = gout * (T(-0.5) * V * rGb * B) * T(0.25);
       atomicAdd(&vhb.p[q][i], gq);
       atomicAdd(&vhb.p[q][ip], gq);
       atomicAdd(&vhb.p[q][iqm], gq);
       atomicAdd(&vhb.p[q][idqm], gq);
-      const T gB = gout * (T(-0.5) * V * Vq / Gb);
+      const T gB = gout * (T(-0.5) * V * Vq * rGb);
       atomicAdd(&pb[iqp], gB * dBT);
       atomicAdd(&pb[idqp], gB * dBT);
       atomicAdd(&pb[iqm], gB * dBB);
