@@ -32,9 +32,10 @@
  * Errors: every call returns MPDATA_OK or an MPDATA_E* code; no call aborts the
  * process or throws (the C analogue of the library's std::runtime_error,
  * Sect. 2.4).  All device work is enqueued on the handle's stream and is
- * asynchronous; a device-side failure (for example a persistent-kernel barrier
- * that timed out) is reported by the next call on the handle that synchronises
- * (mpdata_reduce, mpdata_sync) and then cleared.
+ * asynchronous; a device-side failure is reported by the next call on the
+ * handle that synchronises (mpdata_reduce, mpdata_sync).  No kernel of this
+ * library waits on another block (block barriers only), so no call can hang on
+ * a device-side wait.
  */
 #ifndef MPDATA_GB300_H
 #define MPDATA_GB300_H
@@ -71,7 +72,7 @@ enum {
   MPDATA_EUNSUPPORTED = 2, /* valid but not supported by this build */
   MPDATA_ECUDA = 3,        /* a CUDA runtime call failed */
   MPDATA_ECOURANT = 4,     /* Courant check failed (sum of outflow advectors / G > 1) */
-  MPDATA_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  MPDATA_ETIMEOUT = 5,     /* reserved for bounded device waits (no kernel of this build waits) */
   MPDATA_ESTOPPED = 6,     /* stopped after a step by mpdata_request_stop */
   MPDATA_ENOMEM = 7        /* device or host allocation failed */
 };
@@ -90,6 +91,9 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
 
 /*
  * Advances psi in place by n_steps >= 1 steps (the paper's advance(), Sect. 3.2.5).
+ * 2D steps with n_iters = 2 run fused kernels (one launch per step), 1D fields of up
+ * to 2235 (FP64) / 4470 (FP32) cells run the whole call in one launch, the rest run
+ * one kernel per sub-step.
  * gc (host array of ndims device pointers): advector components, constant over
  * the call.  g: G field (required iff MPDATA_NUG, else NULL).  r: source term R
  * (required iff an RHS bit is set, else NULL), dt its time step.
@@ -167,8 +171,10 @@ int mpdata_check_courant(mpdata_t h, const void* const* gc, const void* g, doubl
 /*
  * Asks the handle to stop: later mpdata_step / mpdata_advance calls return
  * MPDATA_ESTOPPED without enqueuing work, and a multi-step call stops after the
- * step in progress (the paper's panic flag, Sect. 3.2.5).  Thread-safe.
- * mpdata_clear_stop re-arms the handle.
+ * step in progress (the paper's panic flag, Sect. 3.2.5).  A 1D field small
+ * enough for shared memory runs every step of a call in one launch; for it the
+ * request takes effect at the next call.  Thread-safe.  mpdata_clear_stop
+ * re-arms the handle.
  */
 int mpdata_request_stop(mpdata_t h);
 int mpdata_clear_stop(mpdata_t h);
@@ -183,8 +189,7 @@ int mpdata_clear_stop(mpdata_t h);
  *   0 = automatic (band march where the warp march cannot fill the GPU: FP32
  *   fields with fewer than ~600 warp tiles of 8 rows, FP64 fields whose warp
  *   tiles would be 16 rows or less; warp march otherwise), 1 = warp march,
- *   2 = band march.  Batched
- *   handles always use the warp march's persistent kernel.
+ *   2 = band march.  Batched handles always use the warp march's persistent kernel.
  * Returns EINVAL for an unknown knob or value.
  */
 enum { MPDATA_TUNE_TILE_ROWS = 1, MPDATA_TUNE_KERNEL = 2 };

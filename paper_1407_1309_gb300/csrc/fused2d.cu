@@ -546,9 +546,6 @@ template int fused_batched_step<double>(const BatchTable&, const Opts&, const do
                                         const double*, const double*, const double*, double, double, cudaStream_t);
 
 namespace {
-}  // namespace
-
-namespace {
 
 // Warp-march parameters of one step of one field; *band is set when the automatic choice is
 // the band march.
