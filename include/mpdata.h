@@ -119,9 +119,10 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
  * in lo_in / lo_out, same layout).  Every quantity of the step (donor-cell fluxes,
  * pseudo-advectors of Eq. 6, FCT bounds and factors) is computed in FP32 from hi, as by
  * mpdata_advance; both donor-cell passes (Eq. 4) add their four face fluxes with
- * error-free two-sums whose rounding errors go to lo, and the pair is renormalised.  A
- * flux leaves one cell and enters its neighbour with the same value, so sum(hi + lo)
- * is conserved up to the rounding of the lo additions, and the state carries about twice
+ * error-free two-sums whose rounding errors go to lo, the first pass also moves the low
+ * parts with their own donor-cell fluxes, and the pair is renormalised.  Every flux
+ * leaves one cell and enters its neighbour with the same value, so sum(hi + lo) is
+ * conserved up to the rounding of the lo additions, and the state carries about twice
  * the FP32 precision across steps.  Start from lo = 0 for an FP32 initial field (or
  * lo = x - (float)x for an FP64 one).
  * Requirements: an FP32 handle with one 2D field, n_iters = 2, without MPDATA_TOT or

@@ -58,9 +58,11 @@ struct F2Params {
 
 // One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
 // row R0 down ty rows of the field described by p; `ring` is the warp's shared-memory ring.
-// COMP: the state is the pair psi = psi + lo (psi.hi in p.psi, lo in p.lo); every stencil
+// COMP: the state is the pair psi = hi + lo (hi in p.psi, lo in p.lo); every stencil
 // quantity is formed from the hi parts, both donor passes add their fluxes with two-sums
-// (donor_comp) and both parts are stored.
+// (donor_comp), the first pass also moves the low parts with their own donor-cell fluxes
+// (the corrective pass's low-part fluxes are of the order of FP32 rounding and omitted),
+// and both parts are stored.
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP>
 __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip, const int R0, T* ring_warp,
                                            const int lane) {
@@ -118,7 +120,9 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   T hi[3][NC], lo[3][NC];
   T pv0[2][NC], f0c[NC];
   T a0[2][NC], u0[2][NC], a1[2][NC], u1[2][NC], bu[2][NC], bd[2][NC], h0c[NC];
-  T lw[2][NC], l1[3][NC];  // COMP: lo of the loaded rows x-1, x and of pass 1's rows x-3 .. x-1
+  // COMP: lo of the loaded rows x-2 .. x, the low-part flux through face (x-2)+1/2, and lo of
+  // pass 1's rows x-3 .. x-1
+  T lw[3][NC], flc[NC], l1[3][NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
 #pragma unroll
@@ -131,7 +135,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       bu[k][c] = bd[k][c] = T(1);
     }
     f0c[c] = h0c[c] = T(0);
-    lw[0][c] = lw[1][c] = l1[0][c] = l1[1][c] = l1[2][c] = T(0);
+    lw[0][c] = lw[1][c] = lw[2][c] = flc[c] = l1[0][c] = l1[1][c] = l1[2][c] = T(0);
   }
   p1r[0] = p1r[1] = p1r[2] = T(0);
 
@@ -149,14 +153,14 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       copy_row(v0[0], v0[1]); copy_row(v0[1], v0[2]);
       copy_row(v1[0], v1[1]); copy_row(v1[1], v1[2]);
       if (NUG) { copy_row(gg[0], gg[1]); copy_row(gg[1], gg[2]); copy_row(gg[2], gg[3]); }
-      if (COMP) copy_row(lw[0], lw[1]);
+      if (COMP) { copy_row(lw[0], lw[1]); copy_row(lw[1], lw[2]); }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         T x = slot[c];
         if (COMP) {
           T e = slot[5 * kCols + c];
           if (p.rhs_b) two_sum_acc(x, e, p.dt * slot[4 * kCols + c]);
-          lw[1][c] = e;
+          lw[2][c] = e;
         } else if (p.rhs_b) {
           x = x + p.dt * slot[4 * kCols + c];
         }
@@ -169,21 +173,33 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
     issue();
 
     // ---- pass 1 (Eqs. 4-5) at row r = x-1
-    T fnew[NC];
+    T fnew[NC], flnew[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) fnew[c] = flux(ps[2][c], ps[3][c], v0[1][c]);  // face (x-1)+1/2
+    for (int c = 0; c < NC; ++c) {
+      fnew[c] = flux(ps[2][c], ps[3][c], v0[1][c]);  // face (x-1)+1/2
+      if (COMP) flnew[c] = flux(lw[1][c], lw[2][c], v0[1][c]);  // the low parts through it
+    }
     if (S || t >= 2) {
       const T psR = from_right(ps[2]);
       T F1[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) F1[c] = flux(ps[2][c], right_of(ps[2], c, psR), v1[1][c]);
       const T F1L = from_left(F1);
-      T np1[NC], nl1[NC];
+      T np1[NC], nl1[NC], FL1[NC];
+      T FL1L = T(0);
+      if (COMP) {  // low-part fluxes through the faces (x-1, c+1/2)
+        const T loR = from_right(lw[1]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) FL1[c] = flux(lw[1][c], right_of(lw[1], c, loR), v1[1][c]);
+        FL1L = from_left(FL1);
+      }
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const T rG = NUG ? fdiv(T(1), gg[2][c]) : T(1);
         if (COMP) {
-          np1[c] = donor_comp<T, NUG>(ps[2][c], lw[0][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG, nl1[c]);
+          const T lo_div = (flc[c] - flnew[c]) + (left_of(FL1, c, FL1L) - FL1[c]);
+          np1[c] = donor_comp<T, NUG>(ps[2][c], lw[1][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG, lo_div,
+                                      nl1[c]);
         } else {
           np1[c] = donor<T, NUG, KAHAN>(ps[2][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG);
         }
@@ -199,6 +215,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
       p1r[0] = p1r[1]; p1r[1] = p1r[2]; p1r[2] = from_right(p1[3]);
     }
     copy_row(f0c, fnew);
+    if (COMP) copy_row(flc, flnew);
 
     // ---- row r = x-2: pseudo-advectors (Eq. 6 + cross term), unlimited fluxes, FCT factors
     if (S || t >= 3) {
@@ -318,7 +335,8 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
         for (int c = 0; c < NC; ++c) {
           const T rG = NUG ? fdiv(T(1), gg[0][c]) : T(1);
           if (COMP) {
-            np2[c] = donor_comp<T, NUG>(p1[1][c], l1[0][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG, nl2[c]);
+            np2[c] = donor_comp<T, NUG>(p1[1][c], l1[0][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG, T(0),
+                                        nl2[c]);
           } else {
             np2[c] = donor<T, NUG, KAHAN>(p1[1][c], h0[c], h0c[c], h1[c], left_of(h1, c, h1L), rG);
           }

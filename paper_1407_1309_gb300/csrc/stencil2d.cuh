@@ -102,20 +102,23 @@ __device__ __forceinline__ void two_sum_acc(T& s, T& e, T t) {
 }
 
 // Donor-cell update of Eq. 4 on a compensated state psi = hi + lo: the four face fluxes
-// (the same terms, in the same order, as the Kahan form) are added with two-sums whose
-// rounding errors collect in lo, and the pair is renormalised so that the returned hi is
-// the value of the representable sum nearest hi + lo.  A flux leaves one cell and enters
-// its neighbour with the same value, so sum(hi + lo) changes only by the rounding of the
-// small lo additions.
+// of the high parts (the same terms, in the same order, as the Kahan form) are added with
+// two-sums whose rounding errors collect in lo, the low parts move with their own face
+// fluxes (lo_div), and the pair is renormalised so that the returned hi is the value of
+// the representable sum nearest hi + lo.  Every flux leaves one cell and enters its
+// neighbour with the same value, so sum(hi + lo) changes only by the rounding of the small
+// lo additions.
+// lo_div: the divergence of the low parts' own face fluxes (added to lo, scaled by 1/G).
 template <typename T, bool NUG>
-__device__ __forceinline__ T donor_comp(T p, T lo, T Fp0, T Fm0, T Fp1, T Fm1, T rG, T& lo_out) {
+__device__ __forceinline__ T donor_comp(T p, T lo, T Fp0, T Fm0, T Fp1, T Fm1, T rG, T lo_div, T& lo_out) {
   if (NUG) {
     Fp0 *= rG;
     Fm0 *= rG;
     Fp1 *= rG;
     Fm1 *= rG;
+    lo_div *= rG;
   }
-  T s = p, e = lo;
+  T s = p, e = lo + lo_div;
   two_sum_acc(s, e, -Fp0);
   two_sum_acc(s, e, Fm0);
   two_sum_acc(s, e, -Fp1);

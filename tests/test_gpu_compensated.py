@@ -98,9 +98,9 @@ def test_mass_conserved_to_roundoff_of_the_low_parts():
 
 def test_long_run_error_below_plain_fp32():
     """Rotation 256^2, FCT, 1500 steps against the FP64 oracle on the same (FP32-representable)
-    advector: the compensated state's error is below the plain FP32 state's (measured 9.5e-7
-    against 1.7e-6: what remains is the FP32 arithmetic of the fluxes and the limiter, which
-    the compensation leaves as it is; its gain is mass conservation)."""
+    advector: the compensated state's error is below the plain FP32 state's (what remains is
+    the FP32 arithmetic of the fluxes and the limiter, which the compensation leaves as it is;
+    its main gain is mass conservation)."""
     psi, gc, _ = workloads.rotation_2d(256)
     gc = [r32(v) for v in gc]
     oracle.set_threads(0)
