@@ -143,18 +143,45 @@ def kernel_sources_sha256(kernel):
     return h.hexdigest()
 
 
-def traffic_from_profiles(kernel, n, dtype):
-    """Per-launch DRAM bytes (read + write) of the timed kernel from the committed ncu summary;
-    None when there is none or when the kernel's sources changed since it was taken."""
+def traffic_from_profiles(kernel, n, dtype, key="bytes_per_launch"):
+    """Per-launch DRAM bytes (read + write) of the timed kernel from the committed ncu summary
+    (or another per-launch counter stored there, by `key`); None when there is none or when the
+    kernel's sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_rotation{n}_{dtype}.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("sources_sha256") != kernel_sources_sha256(kernel):
             return None
-        return d.get("bytes_per_launch")
+        return d.get(key)
     except Exception:
         return None
+
+
+# Algorithmic FP32 instructions per cell-step of the 2D step (n_iters = 2, FCT, G = 1), counted
+# from the scheme with every quantity computed once: pass 1 (Eq. 4-5) 12, pseudo-velocities with
+# the cross term (Eq. 6 and its 2D form) 19 per face, FCT bounds, in/out sums and factors 32,
+# limited pseudo-velocities 10, pass 2 12; each of the 6 divisions is a reciprocal + multiply.
+ALU_INST_PER_CELL_STEP = 104
+
+
+def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count):
+    """The second bound of the step: FP32 lane-instructions against the SMs' issue rate
+    (4 schedulers x 32 lanes per SM per clock at the highest SM clock)."""
+    if dtype != "f32" or not sm_max_mhz:
+        return None
+    peak = sm_count * 128 * sm_max_mhz * 1e6 / 1e12
+    achieved = ALU_INST_PER_CELL_STEP * cells / seconds_per_step / 1e12
+    warp_inst = traffic_from_profiles(kernel, n, dtype, "smsp__inst_executed.sum")
+    out = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tinst/s",
+           "frac": round(achieved / peak, 4), "algorithmic_inst_per_cell_step": ALU_INST_PER_CELL_STEP,
+           "peak_source": f"{sm_count} SMs x 128 lanes x {sm_max_mhz:.0f} MHz",
+           "executed_lane_slots_per_cell_step": None, "issue_frac_of_executed": None}
+    if warp_inst:
+        per_cell = warp_inst * 32 / cells
+        out["executed_lane_slots_per_cell_step"] = round(per_cell, 1)
+        out["issue_frac_of_executed"] = round(per_cell * cells / seconds_per_step / 1e12 / peak, 4)
+    return out
 
 
 def dist_env():
@@ -286,7 +313,11 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
            "data": "synthetic (seeded rotating-cone workload, no dataset)",
            "config": config(args, {"wall_s_timed_region_incl_flushes": round(wall, 3), "kernel": tuned}),
-           "roofline": roofline, "gpu_launches": args.steps, "clocks": clk}
+           "roofline": roofline,
+           "alu_roofline": alu_roofline(cells, secs / args.steps, tuned["kernel"], n, args.dtype,
+                                        clk.get("sm_max_mhz"),
+                                        torch.cuda.get_device_properties(dev).multi_processor_count),
+           "gpu_launches": args.steps, "clocks": clk}
 
     if rank == 0 and not args.no_extras:
         extras = {}
