@@ -572,6 +572,7 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
     import torch
 
     from paper_1407_1309_gb300 import capi, workloads
+    from paper_1407_1309_gb300 import autograd
     from paper_1407_1309_gb300.autograd import rollout
     from paper_1407_1309_gb300.solver import Mpdata
     psi0, gc_np, pert = workloads.adjoint_2d(n)
@@ -593,8 +594,18 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
             for _ in range(50):
                 m.adjoint_step(a, g, pb, gc_bar=gb)
             e2.record()
+            # the split reverse step of the taped rollout backward: tape + result, then the sweep
+            tape = torch.empty(m.tape_numel(), dtype=dt, device=dev)
+            e3, e4 = _events()
+            for _ in range(50):
+                m.adjoint_record(a, g, tape, psi_next=b)
+            e3.record()
+            for _ in range(50):
+                m.adjoint_replay(a, g, tape, pb, gc_bar=gb)
+            e4.record()
             torch.cuda.synchronize(dev)
             fwd, adj = e0.elapsed_time(e1) / 50, e1.elapsed_time(e2) / 50
+            rec, rep = e2.elapsed_time(e3) / 50, e3.elapsed_time(e4) / 50
             # whole rollout: forward vs backward (recompute + adjoint)
             p0 = t(psi0).requires_grad_(True)
             gg = [v.clone().requires_grad_(True) for v in g]
@@ -618,6 +629,8 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
             key = "f32" if dt == torch.float32 else "f64"
             res[key] = {"forward_step_ms": round(fwd, 4), "adjoint_step_ms": round(adj, 4),
                         "adjoint_over_forward_step": round(adj / fwd, 2),
+                        "record_step_ms": round(rec, 4), "replay_step_ms": round(rep, 4),
+                        "backward_records_tapes": autograd._tapes_fit(m, every, a),
                         "rollout_forward_ms": round((tf1 - tf0) * 1e3, 2),
                         "rollout_backward_ms": round((tb1 - tf1) * 1e3, 2),
                         "backward_over_forward": round((tb1 - tf1) / (tf1 - tf0), 2)}

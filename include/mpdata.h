@@ -151,6 +151,31 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
                         void* psi_bar, void* const* gc_bar);
 
 /*
+ * mpdata_adjoint_step split in two, so that a caller holding the forward states of several
+ * steps (a checkpointed rollout) records each step's tape while it recomputes the states and
+ * then runs only the reverse sweeps:
+ *
+ * mpdata_adjoint_tape_bytes: *bytes = size of one step's tape (device memory the caller
+ *   allocates; element-aligned).  It holds psi^(1..K-1) of the donor-cell passes (Eqs. 4-5),
+ *   the pseudo-advectors of Eq. 6 and, with MPDATA_FCT, the limited advectors, the bounds and
+ *   the factors of Sect. 3.1.4: (K-1)(1+d) arrays of N elements, plus d(K-1) + 2 + 2(K-1)
+ *   with FCT (K = n_iters, d = ndims, N = cells).
+ * mpdata_adjoint_record: the forward step from psi_n on the staged kernels, writing its tape
+ *   into `tape` and, when psi_next is not NULL, psi^{n+1} into psi_next (which must not be
+ *   psi_n).  The tape refers to psi_n and gc, which must hold the same values at replay.
+ * mpdata_adjoint_replay: the reverse sweep of the step recorded in `tape`, with the arguments
+ *   and result of mpdata_adjoint_step (psi_bar in place, gc_bar accumulated).  Record + replay
+ *   gives the result of mpdata_adjoint_step up to the order of the atomic additions of
+ *   its scatter kernels.
+ * Errors as mpdata_adjoint_step; EINVAL also for a NULL or misaligned tape.
+ */
+int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes);
+int mpdata_adjoint_record(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
+                          void* tape, void* psi_next);
+int mpdata_adjoint_replay(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
+                          const void* tape, void* psi_bar, void* const* gc_bar);
+
+/*
  * FP64 reductions over each field (host outputs, n_fields entries each):
  * mass_out[f] = sum G psi (G = 1 when g is NULL).  Synchronises the stream.
  */

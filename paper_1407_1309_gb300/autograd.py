@@ -4,12 +4,18 @@ the initial field psi0 and the advector components GC.
 Forward: n_steps steps through the C ABI (fused kernels where they apply),
 keeping psi every `checkpoint_every` steps on the device.  Backward: for each
 segment, last first, the states inside the segment are recomputed from its
-checkpoint, then the hand-written adjoint kernels (mpdata_adjoint_step) walk
-the segment backwards, accumulating dL/dGC over all steps.  Memory is one
-field per checkpoint plus one segment of states.  With use_graphs (default) the
-work of one segment is captured once as a CUDA graph on static buffers and
-replayed per segment, so the host issues one replay per segment instead of
-tens of launches per step.
+checkpoint, then the hand-written adjoint kernels walk the segment backwards,
+accumulating dL/dGC over all steps.  When one segment's tapes fit in device
+memory (`tape_budget`), the recomputation records every step's tape
+(mpdata_adjoint_record: states and intermediates in one forward sweep) and the
+walk back runs only the reverse sweeps (mpdata_adjoint_replay); otherwise each
+step's tape is recomputed inside mpdata_adjoint_step.  The recomputed states then
+come from the staged kernels, which round differently from the fused forward:
+the gradient is that of the staged trajectory from each checkpoint.  Memory is
+one field per checkpoint plus one segment of states (and tapes).  With
+use_graphs (default) the work of one segment is captured once as a CUDA graph
+on static buffers and replayed per segment, so the host issues one replay per
+segment instead of tens of launches per step.
 """
 from __future__ import annotations
 
@@ -51,11 +57,12 @@ class MPDATAFunction(torch.autograd.Function):
         solver, n, every = ctx.solver, ctx.n_steps, ctx.every
         pb = grad_out.detach().contiguous().clone()
         gcb = [torch.zeros_like(g) for g in gc]
+        taped = _tapes_fit(solver, min(every, n), pb)
         if ctx.use_graphs:
             used = []
             for seg in range(n_ck - 1, -1, -1):
                 start, end = seg * every, min(seg * every + every, n)
-                sg = _segment_graph(solver, end - start, pb, gc)
+                sg = _segment_graph(solver, end - start, pb, gc, taped)
                 if sg not in used:
                     sg.load(gc)
                     used.append(sg)
@@ -67,6 +74,16 @@ class MPDATAFunction(torch.autograd.Function):
         for seg in range(n_ck - 1, -1, -1):
             start, end = seg * every, min(seg * every + every, n)
             states = [ckpts[seg]]
+            if taped:
+                tapes = torch.empty((end - start, solver.tape_numel()), dtype=pb.dtype, device=pb.device)
+                for s in range(end - start):
+                    nxt = torch.empty_like(states[-1]) if s + 1 < end - start else None
+                    solver.adjoint_record(states[-1], gc, tapes[s], psi_next=nxt)
+                    if nxt is not None:
+                        states.append(nxt)
+                for s in range(end - start - 1, -1, -1):
+                    solver.adjoint_replay(states[s], gc, tapes[s], pb, gc_bar=gcb)
+                continue
             for _ in range(start, end - 1):
                 nxt = torch.empty_like(states[-1])
                 solver.advance(states[-1], nxt, gc)
@@ -76,17 +93,32 @@ class MPDATAFunction(torch.autograd.Function):
         return (None, None, None, None, pb, *gcb)
 
 
+# Device memory one segment's tapes may take (bytes); None: a quarter of the free memory.
+tape_budget = None
+
+
+def _tapes_fit(solver: Mpdata, length: int, like) -> bool:
+    need = length * solver.tape_numel() * like.element_size()
+    if tape_budget is not None:
+        return need <= tape_budget
+    free, _total = torch.cuda.mem_get_info(like.device)
+    return need <= free // 4
+
+
 class _SegmentGraph:
     """The backward work of one checkpoint segment (recompute its states, then the adjoint
     steps last to first) captured as a CUDA graph on static buffers: the states, psi_bar,
-    the advector and its accumulated adjoint all belong to the graph."""
+    the advector and its accumulated adjoint (and, when taped, every step's tape) all belong
+    to the graph."""
 
-    def __init__(self, solver: Mpdata, length: int, like, gc_like):
+    def __init__(self, solver: Mpdata, length: int, like, gc_like, taped: bool):
         self.states = [torch.zeros_like(like) for _ in range(length)]
         self.pb = torch.empty_like(like)
         self.gc = [torch.zeros_like(g) for g in gc_like]
         self.gcb = [torch.zeros_like(g) for g in gc_like]
-        gc, gcb = self.gc, self.gcb
+        self.tapes = torch.zeros((length, solver.tape_numel()), dtype=like.dtype, device=like.device) \
+            if taped else None
+        gc, gcb, tapes = self.gc, self.gcb, self.tapes
         dev = like.device
         prev = solver.stream
         side = torch.cuda.Stream(dev)
@@ -98,13 +130,23 @@ class _SegmentGraph:
                 scratch = [torch.zeros_like(g) for g in gc]
                 solver.advance(self.states[0], tmp, gc)
                 solver.adjoint_step(self.states[0], gc, tmp, gc_bar=scratch)
+                if taped:
+                    solver.adjoint_record(self.states[0], gc, tapes[0], psi_next=tmp)
+                    solver.adjoint_replay(self.states[0], gc, tapes[0], tmp, gc_bar=scratch)
             side.synchronize()
             self.graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(self.graph, stream=side):
-                for s in range(length - 1):
-                    solver.advance(self.states[s], self.states[s + 1], gc)
-                for s in range(length - 1, -1, -1):
-                    solver.adjoint_step(self.states[s], gc, self.pb, gc_bar=gcb)
+                if taped:
+                    for s in range(length):
+                        nxt = self.states[s + 1] if s + 1 < length else None
+                        solver.adjoint_record(self.states[s], gc, tapes[s], psi_next=nxt)
+                    for s in range(length - 1, -1, -1):
+                        solver.adjoint_replay(self.states[s], gc, tapes[s], self.pb, gc_bar=gcb)
+                else:
+                    for s in range(length - 1):
+                        solver.advance(self.states[s], self.states[s + 1], gc)
+                    for s in range(length - 1, -1, -1):
+                        solver.adjoint_step(self.states[s], gc, self.pb, gc_bar=gcb)
         finally:
             solver.set_stream(prev)
 
@@ -122,13 +164,13 @@ class _SegmentGraph:
         pb.copy_(self.pb)
 
 
-def _segment_graph(solver: Mpdata, length: int, like, gc) -> _SegmentGraph:
+def _segment_graph(solver: Mpdata, length: int, like, gc, taped: bool) -> _SegmentGraph:
     """The captured segment of this length, kept on the handle (a rollout has at most two
     segment lengths: checkpoint_every and the remainder)."""
     cache = solver.__dict__.setdefault("_segment_graphs", {})
-    key = (length, like.dtype, tuple(like.shape))
+    key = (length, like.dtype, tuple(like.shape), taped)
     if key not in cache:
-        cache[key] = _SegmentGraph(solver, length, like, gc)
+        cache[key] = _SegmentGraph(solver, length, like, gc, taped)
     return cache[key]
 
 

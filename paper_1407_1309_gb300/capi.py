@@ -24,6 +24,7 @@ EXPORTED = (
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
     "mpdata_advance_compensated", "mpdata_selftest_division",
+    "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay",
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
@@ -67,6 +68,9 @@ def load(build_if_needed: bool = True):
             "mpdata_advance_compensated": ([P, P, P, P, P, PP, P, P, D, I, DP], I),
             "mpdata_selftest_division": ([P, P, P, I64, P], I),
             "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
+            "mpdata_adjoint_tape_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
+            "mpdata_adjoint_record": ([P, P, PP, P, P, P], I),
+            "mpdata_adjoint_replay": ([P, P, PP, P, P, P, PP], I),
             "mpdata_reduce": ([P, P, P, DP], I),
             "mpdata_diff_norms": ([P, P, P, DP, DP], I),
             "mpdata_check_courant": ([P, PP, P, DP], I),
@@ -211,6 +215,31 @@ def mpdata_adjoint_step(h, psi_n, gc, g, psi_bar, gc_bar=None, *, raw=False):
     if raw:
         return rc
     _check(rc, "mpdata_adjoint_step")
+
+
+def mpdata_adjoint_tape_bytes(h):
+    out = ctypes.c_size_t(0)
+    _check(load().mpdata_adjoint_tape_bytes(h, ctypes.byref(out)), "mpdata_adjoint_tape_bytes")
+    return out.value
+
+
+def mpdata_adjoint_record(h, psi_n, gc, g, tape, psi_next=None, *, raw=False):
+    gcp, _k1 = _ptr_array(gc)
+    rc = load().mpdata_adjoint_record(h, _ptr(psi_n), gcp, _ptr(g), _ptr(tape), _ptr(psi_next))
+    if raw:
+        return rc
+    _check(rc, "mpdata_adjoint_record")
+
+
+def mpdata_adjoint_replay(h, psi_n, gc, g, tape, psi_bar, gc_bar=None, *, raw=False):
+    gcp, _k1 = _ptr_array(gc)
+    gbp = None
+    if gc_bar is not None:
+        gbp, _k2 = _ptr_array(gc_bar)
+    rc = load().mpdata_adjoint_replay(h, _ptr(psi_n), gcp, _ptr(g), _ptr(tape), _ptr(psi_bar), gbp)
+    if raw:
+        return rc
+    _check(rc, "mpdata_adjoint_replay")
 
 
 def mpdata_reduce(h, psi, g=None, n_fields=1):

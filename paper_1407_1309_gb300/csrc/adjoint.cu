@@ -336,31 +336,67 @@ __global__ void ka_accumulate(long long n, const T* __restrict__ src, T* __restr
   if (i < n) dst[i] += src[i];
 }
 
-template <typename T>
-struct AdjPlan {
-  int K = 0, D = 0, fct = 0;
-  long long N = 0;
-  size_t arrays = 0;
-};
-
-template <typename T>
-size_t count_arrays(int K, int D, bool fct) {
-  size_t n = 0;
-  n += K - 1;                       // psi levels 1..K-1
-  n += static_cast<size_t>(D) * (K - 1);      // unlimited advectors k = 2..K
-  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + 2 * (K - 1);  // limited advectors, bounds, factors
-  n += K;                           // psi adjoints 0..K-1
-  n += static_cast<size_t>(D) * K;  // advector adjoints k = 1..K
-  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + D + 2;  // unlimited-advector adjoints, factor adj., flux adj., bounds adj.
+// Arrays of one step's tape: psi levels 1..K-1, the unlimited pseudo-advectors of passes
+// 2..K and, under FCT, the limited ones, the bounds and the factors.
+size_t tape_arrays(int K, int D, bool fct) {
+  size_t n = static_cast<size_t>(K - 1) * (1 + D);
+  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + 2 * (K - 1);
   return n;
 }
 
+// Arrays of the reverse sweep: psi adjoints 0..K-1, advector adjoints of passes 1..K and,
+// under FCT, the unlimited-advector, factor, flux and bounds adjoints.
+size_t adj_arrays(int K, int D, bool fct) {
+  size_t n = static_cast<size_t>(K) * (1 + D);
+  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + D + 2;
+  return n;
+}
+
+// The tape of one step carved from `base` (tape_arrays(...) arrays of N elements).
+template <typename T>
+void carve_tape(T* base, long long N, int K, int D, bool fct, const T* psi_n, const T* const* gc, Tape<T>& tp,
+                T** levels) {
+  T* cur = base;
+  auto take = [&]() { T* q = cur; cur += N; return q; };
+  tp = Tape<T>{};
+  for (int k = 0; k < kTapeMax; ++k) levels[k] = nullptr;
+  tp.psi[0] = psi_n;
+  for (int k = 1; k < K; ++k) { levels[k] = take(); tp.psi[k] = levels[k]; }
+  for (int d = 0; d < 3; ++d) tp.vh[1][d] = d < D ? gc[d] : nullptr;
+  for (int k = 2; k <= K; ++k)
+    for (int d = 0; d < D; ++d) tp.v[k][d] = take();
+  if (fct) {
+    for (int k = 2; k <= K; ++k)
+      for (int d = 0; d < D; ++d) tp.vh[k][d] = take();
+    tp.mx = take();
+    tp.mn = take();
+    for (int k = 2; k <= K; ++k) { tp.bu[k] = take(); tp.bd[k] = take(); }
+  } else {
+    for (int k = 2; k <= K; ++k)
+      for (int d = 0; d < D; ++d) tp.vh[k][d] = tp.v[k][d];
+  }
+}
+
+// What one call does: the whole reverse step (tape recomputed into the handle's scratch),
+// only the tape (into the caller's buffer, plus the step's result), or only the reverse
+// sweep from a tape the caller recorded.
+enum class AdjMode { kStep, kRecord, kReplay };
+
 template <typename T, int ND>
 int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const T* const* gc, const T* G,
-               T* psi_bar, void* const* gc_bar, cudaStream_t st) {
+               T* psi_bar, void* const* gc_bar, cudaStream_t st, AdjMode mode = AdjMode::kStep,
+               T* tape = nullptr, T* psi_next = nullptr) {
   const int K = o.n_iters, D = ND;
   const long long N = g.N;
-  const size_t need = count_arrays<T>(K, D, o.fct) * static_cast<size_t>(N) * sizeof(T);
+  Tape<T> tp{};
+  T* levels[kTapeMax];
+  if (mode == AdjMode::kRecord) {
+    carve_tape<T>(tape, N, K, D, o.fct, psi_n, gc, tp, levels);
+    if (staged_forward_tape<T>(g, o, gc, G, tp, levels, psi_next, st) != cudaSuccess) return MPDATA_ECUDA;
+    return MPDATA_OK;
+  }
+  const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) : 0;
+  const size_t need = (tape_n + adj_arrays(K, D, o.fct)) * static_cast<size_t>(N) * sizeof(T);
   void** slot = handle_adj(h);
   // the adjoint scratch is allocated on first use and kept with the handle; its size is
   // stored in front of it
@@ -373,24 +409,9 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     *slot = hdr;
   }
   T* cur = static_cast<T*>(hdr->ptr);
+  carve_tape<T>(mode == AdjMode::kStep ? cur : tape, N, K, D, o.fct, psi_n, gc, tp, levels);
+  cur += tape_n * static_cast<size_t>(N);
   auto take = [&]() { T* q = cur; cur += N; return q; };
-  Tape<T> tp{};
-  T* levels[kTapeMax] = {nullptr, nullptr, nullptr, nullptr};
-  tp.psi[0] = psi_n;
-  for (int k = 1; k < K; ++k) { levels[k] = take(); tp.psi[k] = levels[k]; }
-  for (int d = 0; d < 3; ++d) tp.vh[1][d] = d < D ? gc[d] : nullptr;
-  for (int k = 2; k <= K; ++k)
-    for (int d = 0; d < D; ++d) tp.v[k][d] = take();
-  if (o.fct) {
-    for (int k = 2; k <= K; ++k)
-      for (int d = 0; d < D; ++d) tp.vh[k][d] = take();
-    tp.mx = take();
-    tp.mn = take();
-    for (int k = 2; k <= K; ++k) { tp.bu[k] = take(); tp.bd[k] = take(); }
-  } else {
-    for (int k = 2; k <= K; ++k)
-      for (int d = 0; d < D; ++d) tp.vh[k][d] = tp.v[k][d];
-  }
   T* const adj_begin = cur;
   T* pbl[kTapeMax];
   for (int k = 0; k < K; ++k) pbl[k] = take();
@@ -410,7 +431,8 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   }
   if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(cur - adj_begin) * sizeof(T), st) != cudaSuccess)
     return MPDATA_ECUDA;
-  if (staged_forward_tape<T>(g, o, gc, G, tp, levels, st) != cudaSuccess) return MPDATA_ECUDA;
+  if (mode == AdjMode::kStep && staged_forward_tape<T>(g, o, gc, G, tp, levels, nullptr, st) != cudaSuccess)
+    return MPDATA_ECUDA;
 
   const int bs = 256;
   const unsigned nb = static_cast<unsigned>((N + bs - 1) / bs);
@@ -464,6 +486,24 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
+template <typename T>
+int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const T* g, T* psi_bar,
+                     void* const* gc_bar, AdjMode mode, T* tape, T* psi_next) {
+  Opts o = make_opts(handle_opts(h), handle_n_iters(h));
+  if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+  const Grid& gr = handle_grids(h)[0];
+  const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
+                    gr.nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
+  const T* G = o.nug ? g : nullptr;
+  cudaStream_t st = handle_stream(h);
+  switch (gr.nd) {
+    case 1: return adjoint_nd<T, 1>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
+    case 2: return adjoint_nd<T, 2>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
+    case 3: return adjoint_nd<T, 3>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
+  }
+  return MPDATA_EINVAL;
+}
+
 }  // namespace
 
 void adjoint_free(mpdata_s* h) {
@@ -477,24 +517,35 @@ void adjoint_free(mpdata_s* h) {
   }
 }
 
-template <typename T>
-int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gcv, const T* g, T* psi_bar, void* const* gc_bar) {
-  Opts o = make_opts(handle_opts(h), handle_n_iters(h));
-  if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+size_t adjoint_tape_bytes(mpdata_s* h, size_t esize) {
+  const Opts o = make_opts(handle_opts(h), handle_n_iters(h));
   const Grid& gr = handle_grids(h)[0];
-  const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
-                    gr.nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
-  const T* G = o.nug ? g : nullptr;
-  cudaStream_t st = handle_stream(h);
-  switch (gr.nd) {
-    case 1: return adjoint_nd<T, 1>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
-    case 2: return adjoint_nd<T, 2>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
-    case 3: return adjoint_nd<T, 3>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st);
-  }
-  return MPDATA_EINVAL;
+  return tape_arrays(o.n_iters, gr.nd, o.fct) * static_cast<size_t>(gr.N) * esize;
+}
+
+template <typename T>
+int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* psi_bar, void* const* gc_bar) {
+  return adjoint_dispatch<T>(h, psi_n, gc, g, psi_bar, gc_bar, AdjMode::kStep, nullptr, nullptr);
+}
+
+template <typename T>
+int adjoint_record(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* tape, T* psi_next) {
+  return adjoint_dispatch<T>(h, psi_n, gc, g, nullptr, nullptr, AdjMode::kRecord, tape, psi_next);
+}
+
+template <typename T>
+int adjoint_replay(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, const T* tape, T* psi_bar,
+                   void* const* gc_bar) {
+  return adjoint_dispatch<T>(h, psi_n, gc, g, psi_bar, gc_bar, AdjMode::kReplay, const_cast<T*>(tape), nullptr);
 }
 
 template int adjoint_step<float>(mpdata_s*, const float*, const void* const*, const float*, float*, void* const*);
 template int adjoint_step<double>(mpdata_s*, const double*, const void* const*, const double*, double*, void* const*);
+template int adjoint_record<float>(mpdata_s*, const float*, const void* const*, const float*, float*, float*);
+template int adjoint_record<double>(mpdata_s*, const double*, const void* const*, const double*, double*, double*);
+template int adjoint_replay<float>(mpdata_s*, const float*, const void* const*, const float*, const float*, float*,
+                                   void* const*);
+template int adjoint_replay<double>(mpdata_s*, const double*, const void* const*, const double*, const double*,
+                                    double*, void* const*);
 
 }  // namespace mpd

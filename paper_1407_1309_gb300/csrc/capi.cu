@@ -315,6 +315,57 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
                                    static_cast<double*>(psi_bar), gc_bar);
 }
 
+// Checks shared by the reverse-step entry points: options, fields, a single-field handle.
+static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
+  if (!h) return MPDATA_EINVAL;
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT)) return MPDATA_EUNSUPPORTED;
+  int rc = validate_fields(h, psi_n, gc, g, nullptr);
+  if (rc != MPDATA_OK) return rc;
+  if (h->n_fields != 1) return MPDATA_EUNSUPPORTED;
+  if (h->n_iters > 4) return MPDATA_EUNSUPPORTED;
+  return MPDATA_OK;
+}
+
+int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes) {
+  if (!h || !bytes) return MPDATA_EINVAL;
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT)) return MPDATA_EUNSUPPORTED;
+  if (h->n_fields != 1 || h->n_iters > 4) return MPDATA_EUNSUPPORTED;
+  *bytes = mpd::adjoint_tape_bytes(h, h->esize);
+  return MPDATA_OK;
+}
+
+int mpdata_adjoint_record(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* tape,
+                          void* psi_next) {
+  int rc = adjoint_checks(h, psi_n, gc, g);
+  if (rc != MPDATA_OK) return rc;
+  if (!aligned(tape, h->esize) || (psi_next && (!aligned(psi_next, h->esize) || psi_next == psi_n)))
+    return MPDATA_EINVAL;
+  if (!tape && mpd::adjoint_tape_bytes(h, h->esize) > 0) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32)
+    return mpd::adjoint_record<float>(h, static_cast<const float*>(psi_n), gc, static_cast<const float*>(g),
+                                      static_cast<float*>(tape), static_cast<float*>(psi_next));
+  return mpd::adjoint_record<double>(h, static_cast<const double*>(psi_n), gc, static_cast<const double*>(g),
+                                     static_cast<double*>(tape), static_cast<double*>(psi_next));
+}
+
+int mpdata_adjoint_replay(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, const void* tape,
+                          void* psi_bar, void* const* gc_bar) {
+  int rc = adjoint_checks(h, psi_n, gc, g);
+  if (rc != MPDATA_OK) return rc;
+  if (!psi_bar || !aligned(psi_bar, h->esize) || !aligned(tape, h->esize)) return MPDATA_EINVAL;
+  if (!tape && mpd::adjoint_tape_bytes(h, h->esize) > 0) return MPDATA_EINVAL;
+  if (gc_bar)
+    for (int d = 0; d < h->nd; ++d)
+      if (gc_bar[d] && !aligned(gc_bar[d], h->esize)) return MPDATA_EINVAL;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32)
+    return mpd::adjoint_replay<float>(h, static_cast<const float*>(psi_n), gc, static_cast<const float*>(g),
+                                      static_cast<const float*>(tape), static_cast<float*>(psi_bar), gc_bar);
+  return mpd::adjoint_replay<double>(h, static_cast<const double*>(psi_n), gc, static_cast<const double*>(g),
+                                     static_cast<const double*>(tape), static_cast<double*>(psi_bar), gc_bar);
+}
+
 int mpdata_reduce(mpdata_t h, const void* psi, const void* g, double* mass_out) {
   if (!h || !psi || !mass_out) return MPDATA_EINVAL;
   if (!aligned(psi, h->esize) || (g && !aligned(g, h->esize))) return MPDATA_EINVAL;

@@ -110,10 +110,11 @@ struct Tape {
 };
 
 // Forward step on the staged kernels keeping every pass's intermediates (no sources).
-// Writes psi^(1..K-1), the pseudo-advectors, the FCT bounds and factors into the tape.
+// Writes psi^(1..K-1), the pseudo-advectors, the FCT bounds and factors into the tape, and
+// the step's result psi^(K) into psi_next unless it is null.
 template <typename T>
 cudaError_t staged_forward_tape(const Grid& g, const Opts& o, const T* const* gc, const T* G,
-                                const Tape<T>& tp, T* const* psi_out_levels, cudaStream_t st);
+                                const Tape<T>& tp, T* const* psi_out_levels, T* psi_next, cudaStream_t st);
 
 // FP64 reductions (reduce.cu).  partial: device scratch of at least
 // kRedBlocks * n_fields doubles per output.

@@ -64,5 +64,14 @@ template <typename T>
 int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* psi_bar,
                  void* const* gc_bar);
 void adjoint_free(mpdata_s* h);
+// The reverse step split in two: the forward tape of one step recorded into a caller buffer of
+// adjoint_tape_bytes (plus the step's result when psi_next is not null), and the reverse sweep
+// that reads it.
+size_t adjoint_tape_bytes(mpdata_s* h, size_t esize);
+template <typename T>
+int adjoint_record(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* tape, T* psi_next);
+template <typename T>
+int adjoint_replay(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, const T* tape, T* psi_bar,
+                   void* const* gc_bar);
 
 }  // namespace mpd

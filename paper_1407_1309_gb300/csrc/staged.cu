@@ -970,10 +970,12 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
 
 template <typename T, int ND>
 cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G, const Tape<T>& tp,
-                    T* const* levels, cudaStream_t st) {
+                    T* const* levels, T* psi_next, cudaStream_t st) {
   const int bs = 256;
   const int K = o.n_iters;
   In3<T> v1{{gc[0], gc[1], gc[2]}};
+  if (K == 1 && psi_next)
+    k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, psi_next);
   if (K >= 2) {
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, levels[1]);
     if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
@@ -992,10 +994,11 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
       Out3<T> vl{{const_cast<T*>(tp.vh[k][0]), const_cast<T*>(tp.vh[k][1]), const_cast<T*>(tp.vh[k][2])}};
       k_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vu, o.iga, tp.bu[k], tp.bd[k], vl);
     }
-    if (k < K) {
+    T* const dst = k < K ? levels[k] : psi_next;  // the last pass only when the step's result is wanted
+    if (dst) {
       In3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
       k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vh, T(1), o.iga, G, o.kahan, nullptr, T(0), false,
-                                        levels[k]);
+                                        dst);
     }
   }
   return cudaGetLastError();
@@ -1034,19 +1037,19 @@ cudaError_t staged_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cons
 
 template <typename T>
 cudaError_t staged_forward_tape(const Grid& g, const Opts& o, const T* const* gc, const T* G, const Tape<T>& tp,
-                                T* const* levels, cudaStream_t st) {
+                                T* const* levels, T* psi_next, cudaStream_t st) {
   switch (g.nd) {
-    case 1: return tape_nd<T, 1>(g, o, gc, G, tp, levels, st);
-    case 2: return tape_nd<T, 2>(g, o, gc, G, tp, levels, st);
-    case 3: return tape_nd<T, 3>(g, o, gc, G, tp, levels, st);
+    case 1: return tape_nd<T, 1>(g, o, gc, G, tp, levels, psi_next, st);
+    case 2: return tape_nd<T, 2>(g, o, gc, G, tp, levels, psi_next, st);
+    case 3: return tape_nd<T, 3>(g, o, gc, G, tp, levels, psi_next, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template cudaError_t staged_forward_tape<float>(const Grid&, const Opts&, const float* const*, const float*,
-                                                const Tape<float>&, float* const*, cudaStream_t);
+                                                const Tape<float>&, float* const*, float*, cudaStream_t);
 template cudaError_t staged_forward_tape<double>(const Grid&, const Opts&, const double* const*, const double*,
-                                                 const Tape<double>&, double* const*, cudaStream_t);
+                                                 const Tape<double>&, double* const*, double*, cudaStream_t);
 template StagedScratch<float> carve_staged<float>(void*, long long);
 template StagedScratch<double> carve_staged<double>(void*, long long);
 template <typename T>

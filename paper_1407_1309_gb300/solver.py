@@ -61,6 +61,20 @@ class Mpdata:
         capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
         return psi_bar
 
+    def tape_numel(self):
+        """Elements of this handle's dtype in one step's adjoint tape."""
+        esize = 4 if self.dtype == torch.float32 else 8
+        return capi.mpdata_adjoint_tape_bytes(self.h) // esize
+
+    def adjoint_record(self, psi_n, gc, tape, psi_next=None, g=None):
+        """Forward step psi_n -> psi_next (if given) keeping its tape for adjoint_replay."""
+        capi.mpdata_adjoint_record(self.h, psi_n, gc, g, tape, psi_next)
+
+    def adjoint_replay(self, psi_n, gc, tape, psi_bar, g=None, gc_bar=None):
+        """adjoint_step from a recorded tape (psi_n and gc as at recording)."""
+        capi.mpdata_adjoint_replay(self.h, psi_n, gc, g, tape, psi_bar, gc_bar)
+        return psi_bar
+
     def set_stream(self, stream):
         """Send later work of the handle to `stream` (a torch.cuda.Stream)."""
         capi.mpdata_set_stream(self.h, stream)

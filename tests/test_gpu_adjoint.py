@@ -173,3 +173,87 @@ def test_graph_backward_equals_eager_backward():
         for a, b in zip(eager, graph):
             assert torch.allclose(a, b, rtol=1e-12, atol=1e-14)
     assert not torch.allclose(grads[False][0][1], grads[False][1][1])
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_record_replay_equals_adjoint_step(shape, name, dtype):
+    """The split reverse step (tape recorded with the step's result, then the reverse sweep
+    from the tape) gives the one-call reverse step (up to the order of the scatter kernels'
+    atomic additions), and the recorded step's result is the forward step (FP64: within
+    1e-12 of the oracle)."""
+    n_iters, opts = CASES[name]
+    rng = np.random.default_rng(len(shape) * 7 + n_iters)
+    psi = smooth_positive(shape, rng)
+    if opts & capi.IGA:
+        psi = psi - 2.0
+    gc = nondivergent(shape, rng, 0.3)
+    y = rng.normal(size=shape)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
+    with Mpdata(shape, dtype=dtype, n_iters=n_iters, opts=opts) as m:
+        p, g = t(psi), [t(v) for v in gc]
+        pb1, gb1 = t(y), [torch.full(shape, 0.25, dtype=dtype, device=dev) for _ in shape]
+        m.adjoint_step(p, g, pb1, gc_bar=gb1)
+        tape = torch.full((m.tape_numel(),), float("nan"), dtype=dtype, device=dev)
+        nxt = torch.empty_like(p)
+        m.adjoint_record(p, g, tape, psi_next=nxt)
+        pb2, gb2 = t(y), [torch.full(shape, 0.25, dtype=dtype, device=dev) for _ in shape]
+        m.adjoint_replay(p, g, tape, pb2, gc_bar=gb2)
+        torch.cuda.synchronize()
+        rel = 1e-6 if dtype == torch.float32 else 1e-14
+        scale = max(float(pb1.abs().max()), max(float(v.abs().max()) for v in gb1))
+        assert float((pb1 - pb2).abs().max()) <= rel * scale
+        for a, b in zip(gb1, gb2):
+            assert float((a - b).abs().max()) <= rel * scale
+    ref = oracle.step(psi if dtype == torch.float64 else p.double().cpu().numpy(),
+                      gc if dtype == torch.float64 else [v.double().cpu().numpy() for v in g],
+                      n_iters=n_iters, opts=opts)
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert np.abs(nxt.double().cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_tape_bytes_and_rejections():
+    dev = torch.device("cuda")
+    for shape, n_iters, opts, arrays in (((16, 12), 2, capi.FCT, 1 + 2 + 2 + 2 + 2), ((16, 12), 2, 0, 3),
+                                         ((9, 8, 7), 3, capi.FCT, 2 * 4 + 6 + 2 + 4), ((40,), 1, capi.FCT, 2)):
+        with Mpdata(shape, dtype=torch.float64, n_iters=n_iters, opts=opts) as m:
+            assert m.tape_numel() == arrays * int(np.prod(shape))
+    shape = (8, 8)
+    z = [torch.zeros(shape, device=dev) for _ in range(3)]
+    with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=capi.FCT) as m:
+        tape = torch.zeros(m.tape_numel(), device=dev)
+        assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, tape, z[0], raw=True) == capi.EINVAL
+        assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, None, z[1], raw=True) == capi.EINVAL
+        assert capi.mpdata_adjoint_replay(m.h, z[0], z[:2], None, None, z[1], raw=True) == capi.EINVAL
+    with Mpdata(shape, dtype=torch.float32, n_iters=3, opts=capi.TOT) as m:
+        assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, z[2], z[1], raw=True) == capi.EUNSUPPORTED
+
+
+def test_taped_rollout_gradient_matches_untaped():
+    """Backward through recorded tapes == backward that recomputes each tape, with graphs
+    and without (states recomputed on the staged kernels instead of the fused ones: equal to
+    FP64 rounding over the segment)."""
+    from paper_1407_1309_gb300 import autograd
+    psi0_np, gc_np, pert = workloads.adjoint_2d(80, seed=4)
+    dev = torch.device("cuda")
+    f64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    target = f64(psi0_np + 0.05 * pert)
+    grads = []
+    saved = autograd.tape_budget
+    try:
+        for budget, use_graphs in ((0, False), (None, False), (None, True)):
+            autograd.tape_budget = budget
+            with Mpdata((80, 80), dtype=torch.float64, n_iters=2, opts=capi.FCT) as m:
+                gg = [f64(v).requires_grad_(True) for v in gc_np]
+                p0 = f64(psi0_np).requires_grad_(True)
+                out = rollout(m, p0, gg, 17, 6, use_graphs=use_graphs)
+                (0.5 * (out - target) ** 2).sum().backward()
+                torch.cuda.synchronize()
+                grads.append([p0.grad.clone()] + [g.grad.clone() for g in gg])
+    finally:
+        autograd.tape_budget = saved
+    for other in grads[1:]:
+        for a, b in zip(grads[0], other):
+            assert torch.allclose(a, b, rtol=1e-10, atol=1e-12 * float(a.abs().max()))
