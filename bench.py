@@ -582,9 +582,12 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
         with Mpdata((n, n), dtype=dt, n_iters=2, opts=capi.FCT, device=dev) as m:
             a, b, g = t(psi0), torch.empty(n, n, dtype=dt, device=dev), [t(v) for v in gc_np]
             pb, gb = torch.ones_like(a), [torch.zeros_like(a), torch.zeros_like(a)]
+            tape = torch.empty(m.tape_numel(), dtype=dt, device=dev)
             for _ in range(3):
                 m.advance(a, b, g)
                 m.adjoint_step(a, g, pb, gc_bar=gb)
+                m.adjoint_record(a, g, tape, psi_next=b)
+                m.adjoint_replay(a, g, tape, pb, gc_bar=gb)
             e0, e1 = _events()
             e2 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -595,7 +598,6 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
                 m.adjoint_step(a, g, pb, gc_bar=gb)
             e2.record()
             # the split reverse step of the taped rollout backward: tape + result, then the sweep
-            tape = torch.empty(m.tape_numel(), dtype=dt, device=dev)
             e3, e4 = _events()
             for _ in range(50):
                 m.adjoint_record(a, g, tape, psi_next=b)

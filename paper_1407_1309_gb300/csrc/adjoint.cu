@@ -1,22 +1,28 @@
 // Adjoint (reverse mode) of one MPDATA step: given dL/dpsi^{n+1}, produce
 // dL/dpsi^n and add dL/dGC to the advector adjoints.  The forward step is first
 // recomputed on the staged kernels with every pass's intermediates kept
-// (staged_forward_tape); then each sub-step is reversed, last first:
+// (staged_forward_tape, or a tape the caller recorded); then the passes are
+// reversed, last first:
 //
-//   ka_donor_flux   donor-cell pass k and its fluxes (Eqs. 4-5)      gather
-//   ka_limit        FCT limited advector  V^ = V min(1, a, b)          scatter to beta
-//   ka_beta         FCT factors  G[psi_max - psi]+/in, ...            scatter to the fluxes
-//   ka_flux_u       unlimited fluxes of pass k                         gather
-//   ka_antidiff     antidiffusive advector (Eq. 6 + cross terms)       scatter (atomics)
-//   ka_bounds       FCT bounds over psi^n and psi^(1)                  scatter (atomics)
+//   ka_fct_a        (FCT) donor-cell pass k (Eqs. 4-5), the limiter V^ = V min(1, a, b)
+//                   and the factors G[psi_max - psi]+/in, ...: gather over the cell's
+//                   faces; scatters the flux adjoints (atomics)
+//   ka_fct_b        (FCT) the unlimited fluxes of pass k, the antidiffusive advector
+//                   (Eq. 6 + cross terms) and, after pass 2, the bounds over psi^n and
+//                   psi^(1): scatter (atomics)
+//   ka_donor_flux   (no FCT) donor-cell pass k: gather
+//   ka_antidiff     (no FCT) antidiffusive advector: scatter (atomics)
+//   ka_donor_flux   the first pass, which writes the step's outputs
 //
-// Every adjoint array starts at zero and is only accumulated into, so the order
-// of the kernels is the reverse of the forward sub-steps.  Conventions at the
-// kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0 there), a max/min
-// passes the derivative of the first extremal candidate in the forward
-// candidate order, the limiter's min(1, a, b) that of the first minimum.
+// Adjoint arrays that receive scatters start at zero; the others are set by their
+// first writer, so the order of the kernels is the reverse of the forward sub-steps.
+// Conventions at the kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0
+// there), a max/min passes the derivative of the first extremal candidate in the
+// forward candidate order, the limiter's min(1, a, b) that of the first minimum.
 // The third-order terms and the source terms have no adjoint here.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "kernels.h"
 #include "stencil2d.cuh"
@@ -136,59 +142,162 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
   CELL_END
 }
 
-// Reverse of the limiter V^ = V m, m = min(1, a, b) (a, b the factors the forward chose).
+// Reverse of the antidiffusive advector (Eq. 6 with the multi-D cross terms) on the face
+// (d, i) for the adjoint gout of its output:
+//   out = (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q,  A = (p1-p0)/(p0+p1),  B = (T-Bt)/(T+Bt)
+// (A = (p1-p0)/2 and B = (T-Bt)/4 under infinite gauge); scatters to pb and vhb.
 template <typename T, int ND>
-__global__ void ka_limit(Grid g, P3<T> vhb, P3<T> V, const T* __restrict__ psi, bool unit,
-                         const T* __restrict__ bu, const T* __restrict__ bd, W3<T> vb, T* bub, T* bdb) {
+__device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const long long i, const int d, const T gout,
+                                                  const T* __restrict__ psi, const P3<T>& Vin,
+                                                  const T* __restrict__ G, const bool iga, T* pb, const W3<T>& vhb) {
+  const long long ip = nb.at(d, +1);
+  const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
+  const T V = Vin.p[d][i];
+  const T p0 = psi[i], p1 = psi[ip];
+  T A, dA0, dA1;
+  if (iga) {
+    A = (p1 - p0) * T(0.5); dA0 = T(-0.5); dA1 = T(0.5);
+  } else {
+    const T s = p0 + p1;
+    if (s != T(0)) {
+      const T r = adiv(T(1), s);
+      A = (p1 - p0) * r; dA0 = T(-2) * p1 * (r * r); dA1 = T(2) * p0 * (r * r);
+    } else {
+      A = dA0 = dA1 = T(0);
+    }
+  }
+  const T rGb = G ? adiv(T(1), Gb) : T(1);
+  const T c = absv(V) - V * V * rGb;
+  T gV = gout * (sgn(V) - T(2) * V * rGb) * A;
+  atomicAdd(&pb[i], gout * c * dA0);
+  atomicAdd(&pb[ip], gout * c * dA1);
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    if (q == d) continue;
+    const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
+    const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
+    const T* Q = Vin.p[q];
+    const T Vq = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
+    const T Tp = psi[iqp] + psi[idqp], Bt = psi[iqm] + psi[idqm];
+    T B, dBT, dBB;
+    if (iga) {
+      B = (Tp - Bt) * T(0.25); dBT = T(0.25); dBB = T(-0.25);
+    } else {
+      const T S = Tp + Bt;
+      if (S != T(0)) {
+        const T r = adiv(T(1), S);
+        B = (Tp - Bt) * r; dBT = T(2) * Bt * (r * r); dBB = T(-2) * Tp * (r * r);
+      } else {
+        B = dBT = dBB = T(0);
+      }
+    }
+    gV += gout * (T(-0.5) * Vq * rGb * B);
+    const T gq = gout * (T(-0.5) * V * rGb * B) * T(0.25);
+    atomicAdd(&vhb.p[q][i], gq);
+    atomicAdd(&vhb.p[q][ip], gq);
+    atomicAdd(&vhb.p[q][iqm], gq);
+    atomicAdd(&vhb.p[q][idqm], gq);
+    const T gB = gout * (T(-0.5) * V * Vq * rGb);
+    atomicAdd(&pb[iqp], gB * dBT);
+    atomicAdd(&pb[idqp], gB * dBT);
+    atomicAdd(&pb[iqm], gB * dBB);
+    atomicAdd(&pb[idqm], gB * dBB);
+  }
+  atomicAdd(&vhb.p[d][i], gV);
+}
+
+// Reverse of the antidiffusive advector of a pass without the limiter: vb holds the adjoint
+// of its output on every face.
+template <typename T, int ND>
+__global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> Vin, const T* __restrict__ G,
+                            bool iga, T* pb, W3<T> vhb) {
   CELL_INDEX
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = nb.at(d, +1);
-    const T v = V.p[d][i];
-    const T F = flux(psi[i], psi[ip], v, unit);
-    const bool right = F > T(0) || (F == T(0) && v > T(0));
-    const T a = right ? bd[i] : bu[i];
-    const T b = right ? bu[ip] : bd[ip];
-    T m = T(1);
-    int sel = 0;
-    if (a < m) { m = a; sel = 1; }
-    if (b < m) { m = b; sel = 2; }
-    const T gq = vhb.p[d][i];
-    vb.p[d][i] += gq * m;
-    if (sel == 1) atomicAdd(right ? &bdb[i] : &bub[i], gq * v);
-    if (sel == 2) atomicAdd(right ? &bub[ip] : &bdb[ip], gq * v);
+    const T gout = vb.p[d][i];
+    if (gout != T(0)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
   }
   CELL_END
 }
 
-// Reverse of the FCT factors beta_up = G[mx - psi]+/in, beta_dn = G[psi - mn]+/out (1 when the
-// sum is 0), in/out the sums of the signed parts of the unlimited fluxes around the cell.
+// The limiter's choice on the face between cells l and r = l + e_d:
+// V^ = V min(1, a, b), a, b the factors of the upwind/downwind cells for the flux's direction;
+// sel = 0 (the 1), 1 (a, a factor of l) or 2 (b, a factor of r), the first minimum.
+template <typename T>
+__device__ __forceinline__ T limit_choice(const T F, const T v, const T* __restrict__ bu, const T* __restrict__ bd,
+                                          const long long l, const long long r, bool& right, int& sel) {
+  right = F > T(0) || (F == T(0) && v > T(0));
+  const T a = right ? bd[l] : bu[l];
+  const T b = right ? bu[r] : bd[r];
+  T m = T(1);
+  sel = 0;
+  if (a < m) { m = a; sel = 1; }
+  if (b < m) { m = b; sel = 2; }
+  return m;
+}
+
+// Reverse of corrective pass k under FCT, first half, per cell i: the donor-cell pass driven
+// by the limited advector V^ (Eqs. 4-5), the limiter V^ = V min(1, a, b) and the factors
+// beta_up = G[mx - psi]+/in, beta_dn = G[psi - mn]+/out (1 when the sum is 0; Sect. 3.1.4).
+// The adjoint of V^ is formed on the cell's own faces (d, i) and on the faces (d, i - e_d)
+// below it (donor part plus the scatter vhs of pass k + 1, nullable), so the factor adjoints
+// of the cell are gathered from its 2 ND faces without atomics.  Writes pb_prev[i] =
+// dL/dpsi^(k-1) of these sub-steps, vb[d][i] = dL/dV through the limiter, the bounds adjoints
+// (set on the first pass reversed, accumulated on later ones), and scatters the adjoints of
+// the unlimited fluxes into fb.  Branches follow the forward's choices.
 template <typename T, int ND>
-__global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__ bdb, const T* __restrict__ psi,
-                        P3<T> V, const T* __restrict__ G, bool unit, const T* __restrict__ mx,
-                        const T* __restrict__ mn, W3<T> fb, T* __restrict__ pb, T* __restrict__ mxb,
-                        T* __restrict__ mnb) {
+__global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> Vh, P3<T> Vu,
+                         P3<T> vhs, const T* __restrict__ G, bool unit, const T* __restrict__ bu,
+                         const T* __restrict__ bd, const T* __restrict__ mx, const T* __restrict__ mn, bool first,
+                         T* __restrict__ pb_prev, W3<T> vb, T* __restrict__ mxb, T* __restrict__ mnb, W3<T> fb) {
   CELL_INDEX
   const T p = psi[i];
+  const T gi = G ? adiv(pb[i], G[i]) : pb[i];
+  T acc = pb[i];
+  T gu = T(0), gd = T(0);  // adjoints of beta_up and beta_dn of this cell
   T Fp[3], Fm[3];
   long long im[3];
-  T in = T(0), ou = T(0);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
     im[d] = nb.at(d, -1);
-    Fp[d] = flux(p, psi[ip], V.p[d][i], unit);
-    Fm[d] = flux(psi[im[d]], p, V.p[d][im[d]], unit);
+    const T gp = G ? adiv(pb[ip], G[ip]) : pb[ip];
+    const T gm = G ? adiv(pb[im[d]], G[im[d]]) : pb[im[d]];
+    const T fp = gp - gi;  // dL/dF on the face (d, i)
+    const T fm = gi - gm;  // dL/dF on the face (d, i - e_d)
+    const T vh = Vh.p[d][i], vhm = Vh.p[d][im[d]];
+    const T pp = psi[ip], pm = psi[im[d]];
+    T dv = T(1), dvm = T(1);
+    if (!unit) {
+      acc += fp * posp(vh) + fm * negp(vhm);
+      dv = dpos(vh) * p + dneg(vh) * pp;
+      dvm = dpos(vhm) * pm + dneg(vhm) * p;
+    }
+    T gq = fp * dv, gqm = fm * dvm;  // dL/dV^ on the two faces
+    if (vhs.p[d]) { gq += vhs.p[d][i]; gqm += vhs.p[d][im[d]]; }
+    const T v = Vu.p[d][i], vm = Vu.p[d][im[d]];
+    Fp[d] = flux(p, pp, v, unit);
+    Fm[d] = flux(pm, p, vm, unit);
+    bool right;
+    int sel;
+    const T m = limit_choice(Fp[d], v, bu, bd, i, ip, right, sel);  // this cell is l
+    vb.p[d][i] = gq * m;
+    if (sel == 1) (right ? gd : gu) += gq * v;
+    limit_choice(Fm[d], vm, bu, bd, im[d], i, right, sel);          // this cell is r
+    if (sel == 2) (right ? gu : gd) += gqm * vm;
+  }
+  T in = T(0), ou = T(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
     in = in + (posp(Fm[d]) - negp(Fp[d]));
     ou = ou + (posp(Fp[d]) - negp(Fm[d]));
   }
   const T Gi = G ? G[i] : T(1);
-  T gin = T(0), gout = T(0), pacc = T(0);
-  const T gu = bub[i], gd = bdb[i];
+  T gin = T(0), gout = T(0), pacc = T(0), dmx = T(0), dmn = T(0);
   if (in > T(0) && gu != T(0)) {
     const T beta = adiv(Gi * posp(mx[i] - p), in);
     const T t = adiv(gu * Gi * dpos(mx[i] - p), in);
-    mxb[i] += t;
+    dmx = t;
     pacc -= t;
     gin = adiv(-gu * beta, in);
   }
@@ -196,7 +305,7 @@ __global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__
     const T beta = adiv(Gi * posp(p - mn[i]), ou);
     const T t = adiv(gd * Gi * dpos(p - mn[i]), ou);
     pacc += t;
-    mnb[i] -= t;
+    dmn = -t;
     gout = adiv(-gd * beta, ou);
   }
   if (gin != T(0) || gout != T(0)) {
@@ -206,107 +315,18 @@ __global__ void ka_beta(Grid g, const T* __restrict__ bub, const T* __restrict__
       atomicAdd(&fb.p[d][im[d]], gin * dpos(Fm[d]) - gout * dneg(Fm[d]));
     }
   }
-  pb[i] += pacc;
+  pb_prev[i] = acc + pacc;
+  mxb[i] = first ? dmx : mxb[i] + dmx;
+  mnb[i] = first ? dmn : mnb[i] + dmn;
   CELL_END
 }
 
-// Reverse of the unlimited fluxes F = flux(psi_{k-1}, V^k) that fed the FCT factors.
+// Reverse of the FCT bounds at cell i: the adjoint of each extremum goes to its first extremal
+// candidate (order: the cell, then per dimension its -e_d and +e_d neighbours; psi^n before
+// psi^(1)).
 template <typename T, int ND>
-__global__ void ka_flux_u(Grid g, P3<T> fb, const T* __restrict__ psi, P3<T> V, bool unit, T* __restrict__ pb,
-                          W3<T> vb) {
-  CELL_INDEX
-  T acc = T(0);
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
-    const T fp = fb.p[d][i], fm = fb.p[d][im];
-    const T v = V.p[d][i], vm = V.p[d][im];
-    T dv = T(1);
-    if (!unit) {
-      acc += fp * posp(v) + fm * negp(vm);
-      dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
-    }
-    vb.p[d][i] += fp * dv;
-  }
-  pb[i] += acc;
-  CELL_END
-}
-
-// Reverse of the antidiffusive advector (Eq. 6 with the multi-D cross terms):
-//   out = (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q,  A = (p1-p0)/(p0+p1),  B = (T-Bt)/(T+Bt)
-// (A = (p1-p0)/2 and B = (T-Bt)/4 under infinite gauge).
-template <typename T, int ND>
-__global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> Vin, const T* __restrict__ G,
-                            bool iga, T* pb, W3<T> vhb) {
-  CELL_INDEX
-#pragma unroll
-  for (int d = 0; d < ND; ++d) {
-    const T gout = vb.p[d][i];
-    if (gout == T(0)) continue;
-    const long long ip = nb.at(d, +1);
-    const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
-    const T V = Vin.p[d][i];
-    const T p0 = psi[i], p1 = psi[ip];
-    T A, dA0, dA1;
-    if (iga) {
-      A = (p1 - p0) * T(0.5); dA0 = T(-0.5); dA1 = T(0.5);
-    } else {
-      const T s = p0 + p1;
-      if (s != T(0)) {
-        const T r = adiv(T(1), s);
-        A = (p1 - p0) * r; dA0 = T(-2) * p1 * (r * r); dA1 = T(2) * p0 * (r * r);
-      } else {
-        A = dA0 = dA1 = T(0);
-      }
-    }
-    const T rGb = G ? adiv(T(1), Gb) : T(1);
-    const T c = absv(V) - V * V * rGb;
-    T gV = gout * (sgn(V) - T(2) * V * rGb) * A;
-    atomicAdd(&pb[i], gout * c * dA0);
-    atomicAdd(&pb[ip], gout * c * dA1);
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-      if (q == d) continue;
-      const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
-      const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
-      const T* Q = Vin.p[q];
-      const T Vq = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
-      const T Tp = psi[iqp] + psi[idqp], Bt = psi[iqm] + psi[idqm];
-      T B, dBT, dBB;
-      if (iga) {
-        B = (Tp - Bt) * T(0.25); dBT = T(0.25); dBB = T(-0.25);
-      } else {
-        const T S = Tp + Bt;
-        if (S != T(0)) {
-          const T r = adiv(T(1), S);
-          B = (Tp - Bt) * r; dBT = T(2) * Bt * (r * r); dBB = T(-2) * Tp * (r * r);
-        } else {
-          B = dBT = dBB = T(0);
-        }
-      }
-      gV += gout * (T(-0.5) * Vq * rGb * B);
-      const T gq = gout * (T(-0.5) * V * rGb * B) * T(0.25);
-      atomicAdd(&vhb.p[q][i], gq);
-      atomicAdd(&vhb.p[q][ip], gq);
-      atomicAdd(&vhb.p[q][iqm], gq);
-      atomicAdd(&vhb.p[q][idqm], gq);
-      const T gB = gout * (T(-0.5) * V * Vq * rGb);
-      atomicAdd(&pb[iqp], gB * dBT);
-      atomicAdd(&pb[idqp], gB * dBT);
-      atomicAdd(&pb[iqm], gB * dBB);
-      atomicAdd(&pb[idqm], gB * dBB);
-    }
-    atomicAdd(&vhb.p[d][i], gV);
-  }
-  CELL_END
-}
-
-// Reverse of the FCT bounds: the adjoint of each extremum goes to its first extremal candidate
-// (order: the cell, then per dimension its -e_d and +e_d neighbours; psi^n before psi^(1)).
-template <typename T, int ND>
-__global__ void ka_bounds(Grid g, const T* __restrict__ mxb, const T* __restrict__ mnb, const T* __restrict__ p0,
-                          const T* __restrict__ p1, T* pb0, T* pb1) {
-  CELL_INDEX
+__device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const long long i, const T gmx, const T gmn,
+                                           const T* __restrict__ p0, const T* __restrict__ p1, T* pb0, T* pb1) {
   long long loc[7];
   int nl = 0;
   loc[nl++] = i;
@@ -325,8 +345,36 @@ __global__ void ka_bounds(Grid g, const T* __restrict__ mxb, const T* __restrict
     if (a < lo) { lo = a; la = 0; lj = loc[j]; }
     if (b < lo) { lo = b; la = 1; lj = loc[j]; }
   }
-  if (mxb[i] != T(0)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], mxb[i]);
-  if (mnb[i] != T(0)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], mnb[i]);
+  if (gmx != T(0)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], gmx);
+  if (gmn != T(0)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], gmn);
+}
+
+// Reverse of corrective pass k under FCT, second half, per cell i: the unlimited fluxes
+// F = flux(psi^(k-1), V) that fed the factors (adjoints fb, complete after ka_fct_a), which
+// complete dL/dV on the face (d, i) with the limiter's part vbl, then the antidiffusive
+// advector that produced V (Eq. 6, scattered into pb and vhb).  On the last pass reversed
+// (mxb not null) also the bounds over psi^n = p0 and psi^(1) = psi.
+template <typename T, int ND>
+__global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi, P3<T> Vu, P3<T> Vin,
+                         const T* __restrict__ G, bool unit, T* pb, W3<T> vhb, const T* __restrict__ mxb,
+                         const T* __restrict__ mnb, const T* __restrict__ p0, T* pb0) {
+  CELL_INDEX
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
+    const T fp = fb.p[d][i], fm = fb.p[d][im];
+    const T v = Vu.p[d][i], vm = Vu.p[d][im];
+    T dv = T(1);
+    if (!unit) {
+      acc += fp * posp(v) + fm * negp(vm);
+      dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
+    }
+    const T gout = vbl.p[d][i] + fp * dv;
+    if (gout != T(0)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
+  }
+  if (acc != T(0)) atomicAdd(&pb[i], acc);
+  if (mxb) bounds_rev<T, ND>(nb, i, mxb[i], mnb[i], p0, psi, pb0, pb);
   CELL_END
 }
 
@@ -345,10 +393,10 @@ size_t tape_arrays(int K, int D, bool fct) {
 }
 
 // Arrays of the reverse sweep: psi adjoints 0..K-1, advector adjoints of passes 1..K and,
-// under FCT, the unlimited-advector, factor, flux and bounds adjoints.
+// under FCT, the unlimited-advector (limiter part), flux and bounds adjoints.
 size_t adj_arrays(int K, int D, bool fct) {
   size_t n = static_cast<size_t>(K) * (1 + D);
-  if (fct) n += static_cast<size_t>(D) * (K - 1) + 2 + D + 2;
+  if (fct) n += static_cast<size_t>(D) * (K - 1) + D + 2;
   return n;
 }
 
@@ -391,6 +439,14 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   Tape<T> tp{};
   T* levels[kTapeMax];
   if (mode == AdjMode::kRecord) {
+    if constexpr (ND == 2 && std::is_same<T, float>::value) {
+      // FP32 2D: one warp-march launch writes the tape and the step's result
+      if (!o.staged && psi_next) {
+        const StepArgs<float> a{psi_n, psi_next, {gc[0], gc[1], nullptr}, nullptr, nullptr, 0.f, 1.f};
+        const int rc = fused_tape(g, o, a, tape, st);
+        if (rc != MPDATA_EUNSUPPORTED) return rc;
+      }
+    }
     carve_tape<T>(tape, N, K, D, o.fct, psi_n, gc, tp, levels);
     if (staged_forward_tape<T>(g, o, gc, G, tp, levels, psi_next, st) != cudaSuccess) return MPDATA_ECUDA;
     return MPDATA_OK;
@@ -412,24 +468,30 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   carve_tape<T>(mode == AdjMode::kStep ? cur : tape, N, K, D, o.fct, psi_n, gc, tp, levels);
   cur += tape_n * static_cast<size_t>(N);
   auto take = [&]() { T* q = cur; cur += N; return q; };
+  // adjoint arrays: first those that only receive atomic scatters (zeroed), then those
+  // whose first writer sets them
   T* const adj_begin = cur;
   T* pbl[kTapeMax];
-  for (int k = 0; k < K; ++k) pbl[k] = take();
+  pbl[0] = take();
   T* vhb[kTapeMax + 1][3] = {};
   for (int k = 1; k <= K; ++k)
     for (int d = 0; d < D; ++d) vhb[k][d] = take();
+  T* fb[3] = {nullptr, nullptr, nullptr};
+  if (o.fct)
+    for (int d = 0; d < D; ++d) fb[d] = take();
+  T* const zero_end = cur;
+  for (int k = 1; k < K; ++k) pbl[k] = take();
   T* vbk[kTapeMax + 1][3] = {};
-  T *bub = nullptr, *bdb = nullptr, *fb[3] = {nullptr, nullptr, nullptr}, *mxb = nullptr, *mnb = nullptr;
+  T *mxb = nullptr, *mnb = nullptr;
   if (o.fct) {
     for (int k = 2; k <= K; ++k)
       for (int d = 0; d < D; ++d) vbk[k][d] = take();
-    bub = take();
-    bdb = take();
-    for (int d = 0; d < D; ++d) fb[d] = take();
     mxb = take();
     mnb = take();
   }
-  if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(cur - adj_begin) * sizeof(T), st) != cudaSuccess)
+  // without the limiter the donor-cell reverse accumulates into every psi adjoint
+  T* const zero_to = o.fct ? zero_end : cur;
+  if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(zero_to - adj_begin) * sizeof(T), st) != cudaSuccess)
     return MPDATA_ECUDA;
   if (mode == AdjMode::kStep && staged_forward_tape<T>(g, o, gc, G, tp, levels, nullptr, st) != cudaSuccess)
     return MPDATA_ECUDA;
@@ -439,30 +501,33 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   for (int k = K; k >= 2; --k) {
     const T* pbk = (k == K) ? psi_bar : pbl[k];
     P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
-    W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
-    ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1],
-                                                                 vhbk, nullptr, W3<T>{});
     P3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
-    P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
-    if (o.fct) {
-      // factor and flux adjoints of this pass: bub, bdb, fb[0..D-1] are contiguous and were
-      // zeroed with the rest of the adjoint scratch; later passes clear them again
-      if (k < K) cudaMemsetAsync(bub, 0, static_cast<size_t>(N) * (2 + D) * sizeof(T), st);
-      P3<T> vhbr{{vhb[k][0], vhb[k][1], vhb[k][2]}};
-      W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
-      ka_limit<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, vhbr, vu, tp.psi[k - 1], o.iga, tp.bu[k], tp.bd[k], vbw, bub, bdb);
-      W3<T> fbw{{fb[0], fb[1], fb[2]}};
-      ka_beta<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, bub, bdb, tp.psi[k - 1], vu, G, o.iga, tp.mx, tp.mn, fbw, pbl[k - 1],
-                                        mxb, mnb);
-      P3<T> fbr{{fb[0], fb[1], fb[2]}};
-      ka_flux_u<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, fbr, tp.psi[k - 1], vu, o.iga, pbl[k - 1], vbw);
-      gv = P3<T>{{vbk[k][0], vbk[k][1], vbk[k][2]}};
-    }
     P3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     W3<T> vhbp{{vhb[k - 1][0], vhb[k - 1][1], vhb[k - 1][2]}};
-    ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
+    if (o.fct) {
+      // two kernels per pass: donor pass + limiter + factors (gather), then the unlimited
+      // fluxes + antidiffusive advector (+ the bounds on the last pass reversed)
+      if (k < K && cudaMemsetAsync(fb[0], 0, static_cast<size_t>(N) * D * sizeof(T), st) != cudaSuccess)
+        return MPDATA_ECUDA;
+      P3<T> vhs{{k < K ? vhb[k][0] : nullptr, k < K ? vhb[k][1] : nullptr, k < K ? vhb[k][2] : nullptr}};
+      W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
+      W3<T> fbw{{fb[0], fb[1], fb[2]}};
+      ka_fct_a<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, vu, vhs, G, o.iga, tp.bu[k], tp.bd[k],
+                                                       tp.mx, tp.mn, k == K, pbl[k - 1], vbw, mxb, mnb, fbw);
+      P3<T> fbr{{fb[0], fb[1], fb[2]}};
+      P3<T> vbr{{vbk[k][0], vbk[k][1], vbk[k][2]}};
+      const bool last = k == 2;
+      ka_fct_b<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, fbr, vbr, tp.psi[k - 1], vu, vprev, G, o.iga, pbl[k - 1],
+                                                       vhbp, last ? mxb : nullptr, last ? mnb : nullptr, tp.psi[0],
+                                                       pbl[0]);
+    } else {
+      W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
+      ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1],
+                                                                   vhbk, nullptr, W3<T>{});
+      P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
+      ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
+    }
   }
-  if (o.fct && K >= 2) ka_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, mxb, mnb, tp.psi[0], tp.psi[1], pbl[0], pbl[1]);
   P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
   W3<T> vhb1{{vhb[1][0], vhb[1][1], vhb[1][2]}};
   if (K >= 2) {

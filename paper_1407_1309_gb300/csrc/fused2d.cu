@@ -54,6 +54,8 @@ struct F2Params {
   int rhs_a, rhs_b, vec;
   const T* lo;   // compensated state: low parts in / out (COMP only)
   T* lo_out;
+  T* tape;       // adjoint tape (TAPE only): arrays of tape_n elements
+  long long tape_n;
 };
 
 // One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
@@ -63,7 +65,10 @@ struct F2Params {
 // (donor_comp), the first pass also moves the low parts with their own donor-cell fluxes
 // (the corrective pass's low-part fluxes are of the order of FP32 rounding and omitted),
 // and both parts are stored.
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP>
+// TAPE: the step also writes, for the tile's own rows, what the reverse step reads: psi^(1),
+// the pseudo-advectors of both dimensions, and under FCT the limited ones, the bounds and the
+// factors (arrays 0..8 of p.tape in that order).
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP, bool TAPE = false>
 __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip, const int R0, T* ring_warp,
                                            const int lane) {
   constexpr int kArr = arrs<COMP>();
@@ -76,6 +81,15 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   for (int c = 0; c < NC; ++c) col[c] = wrapi(cs + lc0 + c, p.n1);
   T* ring = ring_warp + lc0;
   const int nt = p.ty + 6;
+  // one row of tape array j, own rows and columns only
+  auto tape_store = [&](const int j, const int row, const T (&v)[NC]) {
+    if (!TAPE || row < R0 || row >= R0 + p.ty || row >= p.n0) return;
+    const int gcol = strip * kStride + lc0 - kLead;
+    T* q = p.tape + j * p.tape_n + static_cast<long long>(row) * p.n1 + gcol;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (lc0 + c >= kLead && lc0 + c < kLead + kStride && gcol + c < p.n1) q[c] = v[c];
+  };
   const T* src[6] = {p.psi, p.gc0, p.gc1, NUG ? p.G : nullptr, p.rhs_b ? p.R : nullptr, COMP ? p.lo : nullptr};
   // prefetch cursor: next row to copy, its element offset and ring slot
   int pf_t = 0, pf_row = wrapi(R0 - 3, p.n0), pf_slot = 0;
@@ -204,6 +218,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
           np1[c] = donor<T, NUG, KAHAN>(ps[2][c], fnew[c], f0c[c], F1[c], left_of(F1, c, F1L), rG);
         }
       }
+      tape_store(0, R0 - 4 + t, np1);
       copy_row(p1[0], p1[1]); copy_row(p1[1], p1[2]); copy_row(p1[2], p1[3]); copy_row(p1[3], np1);
       if (COMP) { copy_row(l1[0], l1[1]); copy_row(l1[1], l1[2]); copy_row(l1[2], nl1); }
       if (FCT) {
@@ -241,6 +256,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
         nu0[c] = IGA ? out : flux(p1[2][c], p1[3][c], out);
         npv[c] = v0[0][c] + right_of(v0[0], c, v0R);
       }
+      tape_store(1, R0 - 5 + t, na0);
       copy_row(pv0[0], pv0[1]); copy_row(pv0[1], npv);
       copy_row(a0[0], a0[1]); copy_row(a0[1], na0);
       copy_row(u0[0], u0[1]); copy_row(u0[1], nu0);
@@ -269,6 +285,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
         na1[c] = out;
         nu1[c] = IGA ? out : flux(q0, q1, out);
       }
+      tape_store(2, R0 - 5 + t, na1);
       copy_row(a1[0], a1[1]); copy_row(a1[1], na1);
       copy_row(u1[0], u1[1]); copy_row(u1[1], nu1);
       if (FCT) {
@@ -276,7 +293,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
         const T hL = from_left(hi[1]), hR = from_right(hi[1]);
         const T lL = from_left(lo[1]), lR = from_right(lo[1]);
         const T u1L = from_left(u1[1]);
-        T nbu[NC], nbd[NC];
+        T nbu[NC], nbd[NC], tmx[NC], tmn[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T mx = maxv(maxv(maxv(hi[1][c], hi[0][c]), maxv(hi[2][c], left_of(hi[1], c, hL))),
@@ -295,7 +312,13 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
           // min(1, x / |s|) is 1 for s = 0 (x/0 is inf or NaN, and min ignores NaN)
           nbu[c] = min1(fdiv(Gi * posp(mx - q), absv(in)));
           nbd[c] = min1(fdiv(Gi * posp(q - mn), absv(ou)));
+          tmx[c] = mx;
+          tmn[c] = mn;
         }
+        tape_store(5, R0 - 5 + t, tmx);
+        tape_store(6, R0 - 5 + t, tmn);
+        tape_store(7, R0 - 5 + t, nbu);
+        tape_store(8, R0 - 5 + t, nbd);
         copy_row(bu[0], bu[1]); copy_row(bu[1], nbu);
         copy_row(bd[0], bd[1]); copy_row(bd[1], nbd);
       }
@@ -322,6 +345,26 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
             const T b = right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR);
             h1[c] = F * minv(a, b);
           }
+        }
+        if (TAPE) {
+          // the limited pseudo-advectors; where the flux is 0 the factors follow the
+          // advector's sign (the flux itself is 0 either way)
+          T lv0[NC], lv1[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            {
+              const T F = u0[0][c], V = a0[0][c];
+              const bool right = F > T(0) || (F == T(0) && V > T(0));
+              lv0[c] = V * minv(right ? bd[0][c] : bu[0][c], right ? bu[1][c] : bd[1][c]);
+            }
+            {
+              const T F = u1[0][c], V = a1[0][c];
+              const bool right = F > T(0) || (F == T(0) && V > T(0));
+              lv1[c] = V * minv(right ? bd[0][c] : bu[0][c], right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR));
+            }
+          }
+          tape_store(3, R0 - 6 + t, lv0);
+          tape_store(4, R0 - 6 + t, lv1);
         }
       } else {
 #pragma unroll
@@ -392,7 +435,7 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
   cp_wait<0>();
 }
 
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP, bool TAPE = false>
 __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
   constexpr int kArr = arrs<COMP>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -402,7 +445,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_fused2d(const F2Params<T> p) {
   const int strip = static_cast<int>(wid % p.strips);
   const int R0 = static_cast<int>(wid / p.strips) * p.ty;
   T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(wib) * kSlots * kArr * cols<NC>();
-  march_tile<T, NC, FCT, NUG, IGA, KAHAN, COMP>(p, strip, R0, ring, lane);
+  march_tile<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE>(p, strip, R0, ring, lane);
 }
 
 // Ensemble of fields: a persistent grid walks a table of (field, strip, row tile) items.
@@ -450,22 +493,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_fused2d_batched(const BatchPara
     p.vec = fd.vec && b.vec_ok;
     p.lo = nullptr;
     p.lo_out = nullptr;
+    p.tape = nullptr;
+    p.tape_n = 0;
     march_tile<T, NC, FCT, NUG, IGA, KAHAN, false>(p, local % fd.strips, (local / fd.strips) * b.ty, ring, lane);
   }
 }
 
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP = false>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP = false, bool TAPE = false>
 void launch(const F2Params<T>& p, cudaStream_t st) {
   const long long warps = static_cast<long long>(p.strips) * p.rowtiles;
   const unsigned blocks = static_cast<unsigned>((warps + kWarps - 1) / kWarps);
   const size_t smem = static_cast<size_t>(kWarps) * kSlots * arrs<COMP>() * cols<NC>() * sizeof(T);
   static bool attr_set = false;  // large rings exceed the default 48 KB of dynamic shared memory
   if (!attr_set) {
-    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
+    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     attr_set = true;
   }
-  k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP><<<blocks, kWarps * 32, smem, st>>>(p);
+  k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE><<<blocks, kWarps * 32, smem, st>>>(p);
 }
 
 template <typename T, int NC, bool FCT, bool NUG>
@@ -604,6 +649,8 @@ F2Params<T> warp_params(const Grid& g, const Opts& o, const StepArgs<T>& a, bool
           al(p.G, va) && al(p.R, va);
   p.lo = nullptr;
   p.lo_out = nullptr;
+  p.tape = nullptr;
+  p.tape_n = 0;
   return p;
 }
 
@@ -641,6 +688,19 @@ int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, cons
   } else {
     if (o.nug) launch_comp<false, true>(p, o.iga, st); else launch_comp<false, false>(p, o.iga, st);
   }
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st) {
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
+    return MPDATA_EUNSUPPORTED;
+  if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+  bool band_auto = false;
+  F2Params<float> p = warp_params(g, o, a, &band_auto);  // the warp march writes the tape
+  p.tape = tape;
+  p.tape_n = g.N;
+  if (o.fct) launch<float, 4, true, false, false, false, false, true>(p, st);
+  else launch<float, 4, false, false, false, false, false, true>(p, st);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 

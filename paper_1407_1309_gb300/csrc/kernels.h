@@ -25,6 +25,12 @@ uint32_t handle_opts(const mpdata_s* h);
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 
+// One FP32 2D step (n_iters = 2, no third-order terms, Kahan summation, G, infinite gauge
+// or sources) by the warp march that also writes the adjoint tape (psi^(1), pseudo-advectors
+// and, under FCT, limited advectors, bounds and factors; the layout of mpdata_adjoint_record)
+// into `tape`; MPDATA_EUNSUPPORTED for other cases.
+int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st);
+
 // The fused 2D step on a compensated FP32 state psi = hi + lo (fused2d.cu, warp march):
 // hi in a.psi_in / a.psi_out, lo in lo_in / lo_out.  MPDATA_EUNSUPPORTED outside 2D,
 // n_iters = 2, no tot, out of place.

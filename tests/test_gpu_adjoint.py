@@ -257,3 +257,39 @@ def test_taped_rollout_gradient_matches_untaped():
     for other in grads[1:]:
         for a, b in zip(grads[0], other):
             assert torch.allclose(a, b, rtol=1e-10, atol=1e-12 * float(a.abs().max()))
+
+
+@pytest.mark.parametrize("shape", [(37, 150), (64, 64), (9, 1000)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("opts", [0, capi.FCT], ids=["basic", "fct"])
+def test_fused_tape_matches_staged_tape(shape, opts):
+    """FP32 2D: the warp march that records the tape (one launch) writes the arrays the staged
+    recording writes (psi^(1), pseudo-advectors, limited advectors, bounds, factors capped at
+    1), to FP32 rounding; its step result is the fused forward step's."""
+    rng = np.random.default_rng(sum(shape) + opts)
+    psi = smooth_positive(shape, rng)
+    gc = nondivergent(shape, rng, 0.4)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    tapes, nxts = {}, {}
+    for staged in (False, True):
+        with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=opts | (capi.STAGED if staged else 0)) as m:
+            p, g = t(psi), [t(v) for v in gc]
+            tape = torch.full((m.tape_numel(),), float("nan"), device=dev)
+            nxt = torch.empty_like(p)
+            m.adjoint_record(p, g, tape, psi_next=nxt)
+            if not staged:  # the warp march's forward step (small fields default to the band march)
+                m.tune(capi.TUNE_KERNEL, 1)
+                fwd = torch.empty_like(p)
+                m.advance(p, fwd, g)
+            torch.cuda.synchronize()
+            tapes[staged], nxts[staged] = tape.view(-1, *shape).cpu().numpy(), nxt.cpu().numpy()
+    assert np.array_equal(nxts[False], fwd.cpu().numpy())
+    assert np.abs(nxts[False] - nxts[True]).max() <= 1e-5 * np.abs(psi).max()
+    fused, ref = tapes[False], tapes[True]
+    assert fused.shape[0] == (9 if opts else 3) and np.isfinite(fused).all()
+    if opts:
+        ref[7:9] = np.minimum(ref[7:9], 1.0)
+    for j in range(fused.shape[0]):
+        scale = max(np.abs(ref[j]).max(), 1e-30)
+        tol = 1e-3 if j >= 7 else 1e-5  # factors divide by flux sums that may be small
+        assert np.abs(fused[j] - ref[j]).max() <= tol * max(scale, 1.0), j
