@@ -239,17 +239,18 @@ __device__ __forceinline__ T limit_choice(const T F, const T v, const T* __restr
 // Reverse of corrective pass k under FCT, first half, per cell i: the donor-cell pass driven
 // by the limited advector V^ (Eqs. 4-5), the limiter V^ = V min(1, a, b) and the factors
 // beta_up = G[mx - psi]+/in, beta_dn = G[psi - mn]+/out (1 when the sum is 0; Sect. 3.1.4).
-// The adjoint of V^ is formed on the cell's own faces (d, i) and on the faces (d, i - e_d)
-// below it (donor part plus the scatter vhs of pass k + 1, nullable), so the factor adjoints
-// of the cell are gathered from its 2 ND faces without atomics.  Writes pb_prev[i] =
-// dL/dpsi^(k-1) of these sub-steps, vb[d][i] = dL/dV through the limiter, the bounds adjoints
-// (set on the first pass reversed, accumulated on later ones), and scatters the adjoints of
-// the unlimited fluxes into fb.  Branches follow the forward's choices.
+// V^ is re-derived from the unlimited advector and the limiter's choice (the product the
+// forward formed).  The adjoint of V^ is formed on the cell's own faces (d, i) and on the
+// faces (d, i - e_d) below it (donor part plus the scatter vhs of pass k + 1, nullable), so
+// the factor adjoints of the cell are gathered from its 2 ND faces without atomics.  Writes
+// pb_prev[i] = dL/dpsi^(k-1) of these sub-steps, vb[d][i] = dL/dV through the limiter, the
+// bounds adjoints (set on the first pass reversed, accumulated on later ones), and scatters
+// the adjoints of the unlimited fluxes into fb.  Branches follow the forward's choices.
 template <typename T, int ND>
-__global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> Vh, P3<T> Vu,
-                         P3<T> vhs, const T* __restrict__ G, bool unit, const T* __restrict__ bu,
-                         const T* __restrict__ bd, const T* __restrict__ mx, const T* __restrict__ mn, bool first,
-                         T* __restrict__ pb_prev, W3<T> vb, T* __restrict__ mxb, T* __restrict__ mnb, W3<T> fb) {
+__global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> Vu, P3<T> vhs,
+                         const T* __restrict__ G, bool unit, const T* __restrict__ bu, const T* __restrict__ bd,
+                         const T* __restrict__ mx, const T* __restrict__ mn, bool first, T* __restrict__ pb_prev,
+                         W3<T> vb, T* __restrict__ mxb, T* __restrict__ mnb, W3<T> fb) {
   CELL_INDEX
   const T p = psi[i];
   const T gi = G ? adiv(pb[i], G[i]) : pb[i];
@@ -261,12 +262,19 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
     im[d] = nb.at(d, -1);
+    const T pp = psi[ip], pm = psi[im[d]];
+    const T v = Vu.p[d][i], vm = Vu.p[d][im[d]];
+    Fp[d] = flux(p, pp, v, unit);
+    Fm[d] = flux(pm, p, vm, unit);
+    bool right, right_m;
+    int sel, sel_m;
+    const T m = limit_choice(Fp[d], v, bu, bd, i, ip, right, sel);               // this cell is l
+    const T m_m = limit_choice(Fm[d], vm, bu, bd, im[d], i, right_m, sel_m);     // this cell is r
+    const T vh = v * m, vhm = vm * m_m;
     const T gp = G ? adiv(pb[ip], G[ip]) : pb[ip];
     const T gm = G ? adiv(pb[im[d]], G[im[d]]) : pb[im[d]];
     const T fp = gp - gi;  // dL/dF on the face (d, i)
     const T fm = gi - gm;  // dL/dF on the face (d, i - e_d)
-    const T vh = Vh.p[d][i], vhm = Vh.p[d][im[d]];
-    const T pp = psi[ip], pm = psi[im[d]];
     T dv = T(1), dvm = T(1);
     if (!unit) {
       acc += fp * posp(vh) + fm * negp(vhm);
@@ -275,16 +283,9 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
     }
     T gq = fp * dv, gqm = fm * dvm;  // dL/dV^ on the two faces
     if (vhs.p[d]) { gq += vhs.p[d][i]; gqm += vhs.p[d][im[d]]; }
-    const T v = Vu.p[d][i], vm = Vu.p[d][im[d]];
-    Fp[d] = flux(p, pp, v, unit);
-    Fm[d] = flux(pm, p, vm, unit);
-    bool right;
-    int sel;
-    const T m = limit_choice(Fp[d], v, bu, bd, i, ip, right, sel);  // this cell is l
     vb.p[d][i] = gq * m;
     if (sel == 1) (right ? gd : gu) += gq * v;
-    limit_choice(Fm[d], vm, bu, bd, im[d], i, right, sel);          // this cell is r
-    if (sel == 2) (right ? gu : gd) += gqm * vm;
+    if (sel_m == 2) (right_m ? gu : gd) += gqm * vm;
   }
   T in = T(0), ou = T(0);
 #pragma unroll
@@ -512,7 +513,7 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       P3<T> vhs{{k < K ? vhb[k][0] : nullptr, k < K ? vhb[k][1] : nullptr, k < K ? vhb[k][2] : nullptr}};
       W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
       W3<T> fbw{{fb[0], fb[1], fb[2]}};
-      ka_fct_a<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, vu, vhs, G, o.iga, tp.bu[k], tp.bd[k],
+      ka_fct_a<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vu, vhs, G, o.iga, tp.bu[k], tp.bd[k],
                                                        tp.mx, tp.mn, k == K, pbl[k - 1], vbw, mxb, mnb, fbw);
       P3<T> fbr{{fb[0], fb[1], fb[2]}};
       P3<T> vbr{{vbk[k][0], vbk[k][1], vbk[k][2]}};
@@ -555,6 +556,7 @@ template <typename T>
 int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const T* g, T* psi_bar,
                      void* const* gc_bar, AdjMode mode, T* tape, T* psi_next) {
   Opts o = make_opts(handle_opts(h), handle_n_iters(h));
+  handle_tuning(h, &o.kernel, &o.tile_rows);  // the fused recording follows the forward's kernel
   if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
   const Grid& gr = handle_grids(h)[0];
   const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,

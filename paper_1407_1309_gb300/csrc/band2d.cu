@@ -45,6 +45,9 @@ struct BandParams {
   int n0, n1, strips, H;
   T dt, scale;
   int rhs_a, rhs_b, vec;
+  T* tape;  // adjoint tape (TAPE only): arrays of tape_n elements
+  long long tape_n;
+  int tape_vec;  // tape rows may be written as 16-byte vectors
 };
 
 // NC values of one lane from / to a shared-memory row (16-byte vectors where they fit)
@@ -73,7 +76,11 @@ __device__ __forceinline__ void sts(T* q, const T (&s)[NC]) {
   }
 }
 
-template <typename T, int NC, int W, bool FCT, bool NUG, bool IGA, bool KAHAN>
+// TAPE: the step also writes, for the band's own rows, what the reverse step reads: psi^(1)
+// (tape array 0), the pseudo-advectors of both dimensions (1, 2) and under FCT the bounds
+// (5, 6) and the factors (7, 8); the limited advectors (3, 4) are left to the reverse step,
+// which re-derives them from these.
+template <typename T, int NC, int W, bool FCT, bool NUG, bool IGA, bool KAHAN, bool TAPE = false>
 __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
   constexpr int kCols = 32 * NC;
   constexpr int kStride = kCols - 2 * kLeadB;
@@ -115,6 +122,19 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
     ok[c] = lc0 + c >= kLeadB && lc0 + c < kLeadB + kStride && gcol + c < p.n1;
     all_ok = all_ok && ok[c];
   }
+
+  // one row (local row L) of tape array j, own rows and columns only
+  auto tape_row = [&](const int j, const int L, const T (&v)[NC]) {
+    if (!TAPE || L < 3 || L > Hb + 2) return;
+    T* q = p.tape + j * p.tape_n + static_cast<long long>(Rs + L) * p.n1 + gcol;
+    if (p.tape_vec && all_ok) {
+      sts(q, v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (ok[c]) q[c] = v[c];
+    }
+  };
 
   auto copy_in = [&](T* dst, const T* src_row) {
     if (p.vec) {
@@ -274,6 +294,7 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         p1_c[c] = donor<T, NUG, KAHAN>(pn_c[c], Fp0, Fm0, F1[c], left_of(F1, c, F1L), rG);
       }
       sts(mid_row(s_p1, a), p1_c);
+      tape_row(0, a, p1_c);
     }
     __syncthreads();
     load_row((j + kDepth) * W + w);  // after the barrier: the slots it refills are no longer read
@@ -298,6 +319,7 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) { S0[c] = q_c[c] + p1_c[c]; PV1[c] = w1_c[c] + v1_c[c]; }
       const T S0L = from_left(S0), S0R = from_right(S0), PV1L = from_left(PV1);
+      T na0[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const T V = v0_m[c];
@@ -310,9 +332,11 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         const T rGb = NUG ? fdiv(T(1), Gb) : T(1);
         const T out = (absv(V) - V * V * rGb) * A - T(0.5) * V * Vq * rGb * B;
         u0n[c] = IGA ? out : flux(q_c[c], p1_c[c], out);
+        na0[c] = out;
         pvp[c] = v0_m[c] + right_of(v0_m, c, v0R);
       }
       sts(mid_row(s_u0, b), u0n);
+      tape_row(1, b, na0);
       if (do_x) {
         // dimension-1 faces (b, c+1/2)
         T w0_m[NC];
@@ -321,6 +345,7 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         const T w0R = from_right(w0_m);
         const T rm = from_right(q_m), rc = from_right(q_c), rp = from_right(p1_c);
         const T gR = NUG ? from_right(g_b) : T(1);
+        T na1[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const T V = w1_c[c];
@@ -336,8 +361,10 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
           const T rGb = NUG ? fdiv(T(1), Gb) : T(1);
           const T out = (absv(V) - V * V * rGb) * A - T(0.5) * V * Vq * rGb * B;
           u1n[c] = IGA ? out : flux(q0, q1, out);
+          na1[c] = out;
         }
         sts(mid_row(s_u1, b), u1n);
+        tape_row(2, b, na1);
         if (FCT) {
           // extrema of psi^n and psi^(1) over the cell and its face neighbours
           T pn_mm[NC], hi_m[NC], hi_c[NC], hi_p[NC], lo_m[NC], lo_c[NC], lo_p[NC];
@@ -357,6 +384,8 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
             mn[c] = minv(minv(minv(lo_c[c], lo_m[c]), minv(lo_p[c], left_of(lo_c, c, lL))),
                          right_of(lo_c, c, lR));
           }
+          tape_row(5, b, mx);
+          tape_row(6, b, mn);
         }
       }
     }
@@ -384,6 +413,8 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
         }
         sts(mid_row(s_bu, b), bun);
         sts(mid_row(s_bd, b), bdn);
+        tape_row(7, b, bun);
+        tape_row(8, b, bdn);
       }
     }
     // next chunk's input rows
@@ -400,10 +431,10 @@ constexpr size_t band_smem(int n_in, bool fct) {
          sizeof(T);
 }
 
-template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
+template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool TAPE = false>
 void launch_band(BandParams<T> p, int tile_rows, cudaStream_t st) {
   constexpr int W = kBandWarps;
-  auto kern = k_band2d<T, NC, W, FCT, NUG, IGA, KAHAN>;
+  auto kern = k_band2d<T, NC, W, FCT, NUG, IGA, KAHAN, TAPE>;
   static int slots = 0;  // blocks resident on the whole GPU at the largest ring layout
   if (slots == 0) {
     const size_t most = band_smem<T>(5, FCT);
@@ -464,6 +495,9 @@ int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t s
   const size_t va = NC * sizeof(T) <= 16 ? NC * sizeof(T) : 16;
   p.vec = (p.n1 % NC == 0) && aligned_to(p.psi, va) && aligned_to(p.out, va) && aligned_to(p.gc0, va) &&
           aligned_to(p.gc1, va) && aligned_to(p.G, va) && aligned_to(p.R, va);
+  p.tape = nullptr;
+  p.tape_n = 0;
+  p.tape_vec = 0;
   if (o.fct) {
     if (o.nug) band_mode<T, NC, true, true>(p, o.tile_rows, o.iga, o.kahan, st);
     else band_mode<T, NC, true, false>(p, o.tile_rows, o.iga, o.kahan, st);
@@ -471,6 +505,35 @@ int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t s
     if (o.nug) band_mode<T, NC, false, true>(p, o.tile_rows, o.iga, o.kahan, st);
     else band_mode<T, NC, false, false>(p, o.tile_rows, o.iga, o.kahan, st);
   }
+  return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+}
+
+int band_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st) {
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
+    return MPDATA_EUNSUPPORTED;
+  if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+  BandParams<float> p;
+  p.psi = a.psi_in;
+  p.out = a.psi_out;
+  p.gc0 = a.gc[0];
+  p.gc1 = a.gc[1];
+  p.G = nullptr;
+  p.R = nullptr;
+  p.n0 = g.n[1];
+  p.n1 = g.n[2];
+  p.strips = (p.n1 + 128 - 2 * kLeadB - 1) / (128 - 2 * kLeadB);
+  p.H = 0;
+  p.dt = 0.f;
+  p.scale = a.gc_scale;
+  p.rhs_a = 0;
+  p.rhs_b = 0;
+  p.vec = (p.n1 % 4 == 0) && aligned_to(p.psi, 16) && aligned_to(p.out, 16) && aligned_to(p.gc0, 16) &&
+          aligned_to(p.gc1, 16);
+  p.tape = tape;
+  p.tape_n = g.N;
+  p.tape_vec = p.vec && aligned_to(tape, 16);
+  if (o.fct) launch_band<float, 4, true, false, false, false, true>(p, o.tile_rows, st);
+  else launch_band<float, 4, false, false, false, false, true>(p, o.tile_rows, st);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 

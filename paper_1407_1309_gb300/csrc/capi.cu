@@ -163,6 +163,10 @@ void** handle_batch(mpdata_s* h) { return &h->batch; }
 void** handle_adj(mpdata_s* h) { return &h->adj; }
 int handle_n_iters(const mpdata_s* h) { return h->n_iters; }
 uint32_t handle_opts(const mpdata_s* h) { return h->opts; }
+void handle_tuning(const mpdata_s* h, int* kernel, int* tile_rows) {
+  *kernel = h->kernel;
+  *tile_rows = h->tile_rows;  // as mpdata_advance passes them
+}
 }  // namespace mpd
 
 extern "C" {

@@ -65,9 +65,10 @@ struct F2Params {
 // (donor_comp), the first pass also moves the low parts with their own donor-cell fluxes
 // (the corrective pass's low-part fluxes are of the order of FP32 rounding and omitted),
 // and both parts are stored.
-// TAPE: the step also writes, for the tile's own rows, what the reverse step reads: psi^(1),
-// the pseudo-advectors of both dimensions, and under FCT the limited ones, the bounds and the
-// factors (arrays 0..8 of p.tape in that order).
+// TAPE: the step also writes, for the tile's own rows, what the reverse step reads: psi^(1)
+// (tape array 0), the pseudo-advectors of both dimensions (1, 2) and under FCT the bounds
+// (5, 6) and the factors (7, 8); the limited advectors (3, 4) are left to the reverse step,
+// which re-derives them from these.
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool COMP, bool TAPE = false>
 __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip, const int R0, T* ring_warp,
                                            const int lane) {
@@ -345,26 +346,6 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
             const T b = right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR);
             h1[c] = F * minv(a, b);
           }
-        }
-        if (TAPE) {
-          // the limited pseudo-advectors; where the flux is 0 the factors follow the
-          // advector's sign (the flux itself is 0 either way)
-          T lv0[NC], lv1[NC];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            {
-              const T F = u0[0][c], V = a0[0][c];
-              const bool right = F > T(0) || (F == T(0) && V > T(0));
-              lv0[c] = V * minv(right ? bd[0][c] : bu[0][c], right ? bu[1][c] : bd[1][c]);
-            }
-            {
-              const T F = u1[0][c], V = a1[0][c];
-              const bool right = F > T(0) || (F == T(0) && V > T(0));
-              lv1[c] = V * minv(right ? bd[0][c] : bu[0][c], right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR));
-            }
-          }
-          tape_store(3, R0 - 6 + t, lv0);
-          tape_store(4, R0 - 6 + t, lv1);
         }
       } else {
 #pragma unroll
@@ -696,7 +677,8 @@ int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* ta
     return MPDATA_EUNSUPPORTED;
   if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   bool band_auto = false;
-  F2Params<float> p = warp_params(g, o, a, &band_auto);  // the warp march writes the tape
+  F2Params<float> p = warp_params(g, o, a, &band_auto);
+  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_tape(g, o, a, tape, st);
   p.tape = tape;
   p.tape_n = g.N;
   if (o.fct) launch<float, 4, true, false, false, false, false, true>(p, st);

@@ -17,6 +17,8 @@ void** handle_batch(mpdata_s* h);
 void** handle_adj(mpdata_s* h);
 int handle_n_iters(const mpdata_s* h);
 uint32_t handle_opts(const mpdata_s* h);
+// the handle's MPDATA_TUNE_KERNEL and MPDATA_TUNE_TILE_ROWS settings
+void handle_tuning(const mpdata_s* h, int* kernel, int* tile_rows);
 
 // Fused tile kernel for one field and one step (fused2d.cu).  Returns
 // MPDATA_EUNSUPPORTED when the field / options are not covered, so the caller
@@ -27,9 +29,12 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaS
 
 // One FP32 2D step (n_iters = 2, no third-order terms, Kahan summation, G, infinite gauge
 // or sources) by the warp march that also writes the adjoint tape (psi^(1), pseudo-advectors
-// and, under FCT, limited advectors, bounds and factors; the layout of mpdata_adjoint_record)
-// into `tape`; MPDATA_EUNSUPPORTED for other cases.
+// and, under FCT, bounds and factors, in the layout of mpdata_adjoint_record; the limited
+// advectors are left unwritten, the reverse step re-derives them) into `tape`;
+// MPDATA_EUNSUPPORTED for other cases.
 int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st);
+// The same by the band march (band2d.cu); fused_tape picks the family as fused_step does.
+int band_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st);
 
 // The fused 2D step on a compensated FP32 state psi = hi + lo (fused2d.cu, warp march):
 // hi in a.psi_in / a.psi_out, lo in lo_in / lo_out.  MPDATA_EUNSUPPORTED outside 2D,

@@ -261,10 +261,12 @@ def test_taped_rollout_gradient_matches_untaped():
 
 @pytest.mark.parametrize("shape", [(37, 150), (64, 64), (9, 1000)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("opts", [0, capi.FCT], ids=["basic", "fct"])
-def test_fused_tape_matches_staged_tape(shape, opts):
-    """FP32 2D: the warp march that records the tape (one launch) writes the arrays the staged
-    recording writes (psi^(1), pseudo-advectors, limited advectors, bounds, factors capped at
-    1), to FP32 rounding; its step result is the fused forward step's."""
+@pytest.mark.parametrize("family", [1, 2], ids=["warp", "band"])
+def test_fused_tape_matches_staged_tape(shape, opts, family):
+    """FP32 2D: the fused step that records the tape in one launch (warp or band march) writes
+    the arrays the staged recording writes (psi^(1), pseudo-advectors, bounds, factors capped
+    at 1; the limited advectors are re-derived by the reverse step and left unwritten), to
+    FP32 rounding; its step result is that family's forward step."""
     rng = np.random.default_rng(sum(shape) + opts)
     psi = smooth_positive(shape, rng)
     gc = nondivergent(shape, rng, 0.4)
@@ -274,11 +276,12 @@ def test_fused_tape_matches_staged_tape(shape, opts):
     for staged in (False, True):
         with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=opts | (capi.STAGED if staged else 0)) as m:
             p, g = t(psi), [t(v) for v in gc]
+            if not staged:
+                m.tune(capi.TUNE_KERNEL, family)
             tape = torch.full((m.tape_numel(),), float("nan"), device=dev)
             nxt = torch.empty_like(p)
             m.adjoint_record(p, g, tape, psi_next=nxt)
-            if not staged:  # the warp march's forward step (small fields default to the band march)
-                m.tune(capi.TUNE_KERNEL, 1)
+            if not staged:
                 fwd = torch.empty_like(p)
                 m.advance(p, fwd, g)
             torch.cuda.synchronize()
@@ -286,10 +289,13 @@ def test_fused_tape_matches_staged_tape(shape, opts):
     assert np.array_equal(nxts[False], fwd.cpu().numpy())
     assert np.abs(nxts[False] - nxts[True]).max() <= 1e-5 * np.abs(psi).max()
     fused, ref = tapes[False], tapes[True]
-    assert fused.shape[0] == (9 if opts else 3) and np.isfinite(fused).all()
+    written = [0, 1, 2, 5, 6, 7, 8] if opts else [0, 1, 2]
+    assert fused.shape[0] == (9 if opts else 3)
     if opts:
         ref[7:9] = np.minimum(ref[7:9], 1.0)
-    for j in range(fused.shape[0]):
+        assert np.isnan(fused[3:5]).all()
+    for j in written:
+        assert np.isfinite(fused[j]).all(), j
         scale = max(np.abs(ref[j]).max(), 1e-30)
         tol = 1e-3 if j >= 7 else 1e-5  # factors divide by flux sums that may be small
         assert np.abs(fused[j] - ref[j]).max() <= tol * max(scale, 1.0), j
