@@ -22,8 +22,6 @@
 // The third-order terms and the source terms have no adjoint here.
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include "kernels.h"
 #include "stencil2d.cuh"
 
@@ -440,11 +438,11 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   Tape<T> tp{};
   T* levels[kTapeMax];
   if (mode == AdjMode::kRecord) {
-    if constexpr (ND == 2 && std::is_same<T, float>::value) {
-      // FP32 2D: one warp-march launch writes the tape and the step's result
+    if constexpr (ND == 2) {
+      // 2D: one launch of the fused step writes the tape and the step's result
       if (!o.staged && psi_next) {
-        const StepArgs<float> a{psi_n, psi_next, {gc[0], gc[1], nullptr}, nullptr, nullptr, 0.f, 1.f};
-        const int rc = fused_tape(g, o, a, tape, st);
+        const StepArgs<T> a{psi_n, psi_next, {gc[0], gc[1], nullptr}, nullptr, nullptr, T(0), T(1)};
+        const int rc = fused_tape<T>(g, o, a, tape, st);
         if (rc != MPDATA_EUNSUPPORTED) return rc;
       }
     }

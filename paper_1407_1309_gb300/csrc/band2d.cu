@@ -508,11 +508,13 @@ int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t s
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
-int band_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st) {
+template <typename T>
+int band_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st) {
   if (g.nd != 2 || o.n_iters != 2 || o.tot || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
     return MPDATA_EUNSUPPORTED;
   if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
-  BandParams<float> p;
+  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
+  BandParams<T> p;
   p.psi = a.psi_in;
   p.out = a.psi_out;
   p.gc0 = a.gc[0];
@@ -521,22 +523,24 @@ int band_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tap
   p.R = nullptr;
   p.n0 = g.n[1];
   p.n1 = g.n[2];
-  p.strips = (p.n1 + 128 - 2 * kLeadB - 1) / (128 - 2 * kLeadB);
+  p.strips = (p.n1 + 32 * NC - 2 * kLeadB - 1) / (32 * NC - 2 * kLeadB);
   p.H = 0;
-  p.dt = 0.f;
+  p.dt = T(0);
   p.scale = a.gc_scale;
   p.rhs_a = 0;
   p.rhs_b = 0;
-  p.vec = (p.n1 % 4 == 0) && aligned_to(p.psi, 16) && aligned_to(p.out, 16) && aligned_to(p.gc0, 16) &&
+  p.vec = (p.n1 % NC == 0) && aligned_to(p.psi, 16) && aligned_to(p.out, 16) && aligned_to(p.gc0, 16) &&
           aligned_to(p.gc1, 16);
   p.tape = tape;
   p.tape_n = g.N;
   p.tape_vec = p.vec && aligned_to(tape, 16);
-  if (o.fct) launch_band<float, 4, true, false, false, false, true>(p, o.tile_rows, st);
-  else launch_band<float, 4, false, false, false, false, true>(p, o.tile_rows, st);
+  if (o.fct) launch_band<T, NC, true, false, false, false, true>(p, o.tile_rows, st);
+  else launch_band<T, NC, false, false, false, false, true>(p, o.tile_rows, st);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
+template int band_tape<float>(const Grid&, const Opts&, const StepArgs<float>&, float*, cudaStream_t);
+template int band_tape<double>(const Grid&, const Opts&, const StepArgs<double>&, double*, cudaStream_t);
 template int band_step<float>(const Grid&, const Opts&, const StepArgs<float>&, cudaStream_t);
 template int band_step<double>(const Grid&, const Opts&, const StepArgs<double>&, cudaStream_t);
 

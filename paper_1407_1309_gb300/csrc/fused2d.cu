@@ -672,19 +672,24 @@ int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, cons
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
-int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st) {
+template <typename T>
+int fused_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st) {
   if (g.nd != 2 || o.n_iters != 2 || o.tot || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
     return MPDATA_EUNSUPPORTED;
   if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
+  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   bool band_auto = false;
-  F2Params<float> p = warp_params(g, o, a, &band_auto);
-  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_tape(g, o, a, tape, st);
+  F2Params<T> p = warp_params(g, o, a, &band_auto);
+  if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_tape<T>(g, o, a, tape, st);
   p.tape = tape;
   p.tape_n = g.N;
-  if (o.fct) launch<float, 4, true, false, false, false, false, true>(p, st);
-  else launch<float, 4, false, false, false, false, false, true>(p, st);
+  if (o.fct) launch<T, NC, true, false, false, false, false, true>(p, st);
+  else launch<T, NC, false, false, false, false, false, true>(p, st);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
+
+template int fused_tape<float>(const Grid&, const Opts&, const StepArgs<float>&, float*, cudaStream_t);
+template int fused_tape<double>(const Grid&, const Opts&, const StepArgs<double>&, double*, cudaStream_t);
 
 template int fused_step<float>(const Grid&, const Opts&, const StepArgs<float>&, float*, cudaStream_t);
 template int fused_step<double>(const Grid&, const Opts&, const StepArgs<double>&, double*, cudaStream_t);

@@ -27,14 +27,17 @@ void handle_tuning(const mpdata_s* h, int* kernel, int* tile_rows);
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 
-// One FP32 2D step (n_iters = 2, no third-order terms, Kahan summation, G, infinite gauge
-// or sources) by the warp march that also writes the adjoint tape (psi^(1), pseudo-advectors
+// One 2D step (n_iters = 2, no third-order terms, Kahan summation, G, infinite gauge or
+// sources) by the warp march that also writes the adjoint tape (psi^(1), pseudo-advectors
 // and, under FCT, bounds and factors, in the layout of mpdata_adjoint_record; the limited
 // advectors are left unwritten, the reverse step re-derives them) into `tape`;
-// MPDATA_EUNSUPPORTED for other cases.
-int fused_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st);
-// The same by the band march (band2d.cu); fused_tape picks the family as fused_step does.
-int band_tape(const Grid& g, const Opts& o, const StepArgs<float>& a, float* tape, cudaStream_t st);
+// MPDATA_EUNSUPPORTED for other cases.  It hands over to band_tape where fused_step would
+// run the band march.
+template <typename T>
+int fused_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st);
+// The same by the band march (band2d.cu).
+template <typename T>
+int band_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st);
 
 // The fused 2D step on a compensated FP32 state psi = hi + lo (fused2d.cu, warp march):
 // hi in a.psi_in / a.psi_out, lo in lo_in / lo_out.  MPDATA_EUNSUPPORTED outside 2D,

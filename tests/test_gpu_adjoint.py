@@ -202,7 +202,7 @@ def test_record_replay_equals_adjoint_step(shape, name, dtype):
         pb2, gb2 = t(y), [torch.full(shape, 0.25, dtype=dtype, device=dev) for _ in shape]
         m.adjoint_replay(p, g, tape, pb2, gc_bar=gb2)
         torch.cuda.synchronize()
-        rel = 1e-6 if dtype == torch.float32 else 1e-14
+        rel = 1e-6 if dtype == torch.float32 else 1e-12  # 2D records on the fused kernels
         scale = max(float(pb1.abs().max()), max(float(v.abs().max()) for v in gb1))
         assert float((pb1 - pb2).abs().max()) <= rel * scale
         for a, b in zip(gb1, gb2):
@@ -262,23 +262,24 @@ def test_taped_rollout_gradient_matches_untaped():
 @pytest.mark.parametrize("shape", [(37, 150), (64, 64), (9, 1000)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("opts", [0, capi.FCT], ids=["basic", "fct"])
 @pytest.mark.parametrize("family", [1, 2], ids=["warp", "band"])
-def test_fused_tape_matches_staged_tape(shape, opts, family):
-    """FP32 2D: the fused step that records the tape in one launch (warp or band march) writes
-    the arrays the staged recording writes (psi^(1), pseudo-advectors, bounds, factors capped
-    at 1; the limited advectors are re-derived by the reverse step and left unwritten), to
-    FP32 rounding; its step result is that family's forward step."""
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_fused_tape_matches_staged_tape(shape, opts, family, dtype):
+    """2D: the fused step that records the tape in one launch (warp or band march) writes the
+    arrays the staged recording writes (psi^(1), pseudo-advectors, bounds, factors capped at 1;
+    the limited advectors are re-derived by the reverse step and left unwritten), to rounding;
+    its step result is that family's forward step."""
     rng = np.random.default_rng(sum(shape) + opts)
     psi = smooth_positive(shape, rng)
     gc = nondivergent(shape, rng, 0.4)
     dev = torch.device("cuda")
-    t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
     tapes, nxts = {}, {}
     for staged in (False, True):
-        with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=opts | (capi.STAGED if staged else 0)) as m:
+        with Mpdata(shape, dtype=dtype, n_iters=2, opts=opts | (capi.STAGED if staged else 0)) as m:
             p, g = t(psi), [t(v) for v in gc]
             if not staged:
                 m.tune(capi.TUNE_KERNEL, family)
-            tape = torch.full((m.tape_numel(),), float("nan"), device=dev)
+            tape = torch.full((m.tape_numel(),), float("nan"), dtype=dtype, device=dev)
             nxt = torch.empty_like(p)
             m.adjoint_record(p, g, tape, psi_next=nxt)
             if not staged:
@@ -286,8 +287,9 @@ def test_fused_tape_matches_staged_tape(shape, opts, family):
                 m.advance(p, fwd, g)
             torch.cuda.synchronize()
             tapes[staged], nxts[staged] = tape.view(-1, *shape).cpu().numpy(), nxt.cpu().numpy()
+    f32 = dtype == torch.float32
     assert np.array_equal(nxts[False], fwd.cpu().numpy())
-    assert np.abs(nxts[False] - nxts[True]).max() <= 1e-5 * np.abs(psi).max()
+    assert np.abs(nxts[False] - nxts[True]).max() <= (1e-5 if f32 else 1e-13) * np.abs(psi).max()
     fused, ref = tapes[False], tapes[True]
     written = [0, 1, 2, 5, 6, 7, 8] if opts else [0, 1, 2]
     assert fused.shape[0] == (9 if opts else 3)
@@ -297,5 +299,5 @@ def test_fused_tape_matches_staged_tape(shape, opts, family):
     for j in written:
         assert np.isfinite(fused[j]).all(), j
         scale = max(np.abs(ref[j]).max(), 1e-30)
-        tol = 1e-3 if j >= 7 else 1e-5  # factors divide by flux sums that may be small
+        tol = (1e-3 if j >= 7 else 1e-5) if f32 else (1e-9 if j >= 7 else 1e-13)  # factors: small flux sums
         assert np.abs(fused[j] - ref[j]).max() <= tol * max(scale, 1.0), j
