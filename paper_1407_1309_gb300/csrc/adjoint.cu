@@ -92,6 +92,28 @@ template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit
   return unit ? V : posp(V) * L + negp(V) * R;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_after() may start while its
+// predecessor on the stream finishes; it calls grid_wait() before it reads anything the
+// predecessor wrote (no-ops for kernels launched the ordinary way).  grid_release() lets the
+// successor's launch begin as soon as every block of this grid has started.
+__device__ __forceinline__ void grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_after(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // loop over the cells on a (fast, middle, slow) launch grid; closed by CELL_END
 #define CELL_INDEX                                                                    \
   for (int c0_ = blockIdx.z; c0_ < g.n[0]; c0_ += gridDim.z)                            \
@@ -105,11 +127,14 @@ template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit
 // Reverse of the donor-cell pass k, psi_k = psi_{k-1} + sum_d (F_{i-e_d} - F_i)/G_i with
 // F = flux(psi_{k-1}, V^k): pb_prev += dL/dpsi_{k-1}, vhb[d] += dL/dV^k.  FINAL (the first
 // pass, reversed last): the step's outputs are written here instead, psi_out = pb_prev +
-// this pass's part, and gc_out[d] += vhb[d] + this pass's part (gc_out[d] may be null).
+// this pass's part, and gc_out[d] += vhb[d] + this pass's part (gc_out[d] may be null);
+// then the cell's element of each of the nz arrays at zb (stride zn; they include pb_prev
+// and vhb) is cleared for the next reverse step.
 template <typename T, int ND, bool FINAL>
 __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restrict__ psi, P3<T> V,
-                              const T* __restrict__ G, bool unit, T* __restrict__ pb_prev, W3<T> vhb,
-                              T* __restrict__ psi_out, W3<T> gc_out) {
+                              const T* __restrict__ G, bool unit, T* pb_prev, W3<T> vhb, T* __restrict__ psi_out,
+                              W3<T> gc_out, T* zb, int nz, long long zn) {
+  grid_wait();
   CELL_INDEX
   const T gi = G ? adiv(pb[i], G[i]) : pb[i];
   T acc = pb[i];
@@ -134,6 +159,7 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
   }
   if (FINAL) {
     psi_out[i] = pb_prev[i] + acc;
+    for (int a = 0; a < nz; ++a) zb[a * zn + i] = T(0);
   } else {
     pb_prev[i] += acc;
   }
@@ -249,6 +275,8 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
                          const T* __restrict__ G, bool unit, const T* __restrict__ bu, const T* __restrict__ bd,
                          const T* __restrict__ mx, const T* __restrict__ mn, bool first, T* __restrict__ pb_prev,
                          W3<T> vb, T* __restrict__ mxb, T* __restrict__ mnb, W3<T> fb) {
+  grid_wait();
+  grid_release();
   CELL_INDEX
   const T p = psi[i];
   const T gi = G ? adiv(pb[i], G[i]) : pb[i];
@@ -357,6 +385,8 @@ template <typename T, int ND>
 __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi, P3<T> Vu, P3<T> Vin,
                          const T* __restrict__ G, bool unit, T* pb, W3<T> vhb, const T* __restrict__ mxb,
                          const T* __restrict__ mnb, const T* __restrict__ p0, T* pb0) {
+  grid_wait();
+  grid_release();
   CELL_INDEX
   T acc = T(0);
 #pragma unroll
@@ -424,6 +454,14 @@ void carve_tape(T* base, long long N, int K, int D, bool fct, const T* psi_n, co
   }
 }
 
+// The handle's adjoint scratch: size, device pointer, and where its zero-initialised arrays
+// started when the last call left them cleared (null when not known to be clear).
+struct AdjScratch {
+  size_t bytes;
+  void* ptr;
+  void* clean;
+};
+
 // What one call does: the whole reverse step (tape recomputed into the handle's scratch),
 // only the tape (into the caller's buffer, plus the step's result), or only the reverse
 // sweep from a tape the caller recorded.
@@ -453,19 +491,19 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) : 0;
   const size_t need = (tape_n + adj_arrays(K, D, o.fct)) * static_cast<size_t>(N) * sizeof(T);
   void** slot = handle_adj(h);
-  // the adjoint scratch is allocated on first use and kept with the handle; its size is
-  // stored in front of it
-  struct Hdr { size_t bytes; void* ptr; };
-  Hdr* hdr = static_cast<Hdr*>(*slot);
+  // the adjoint scratch is allocated on first use and kept with the handle
+  AdjScratch* hdr = static_cast<AdjScratch*>(*slot);
   if (hdr == nullptr || hdr->bytes < need) {
     if (hdr) { cudaFree(hdr->ptr); delete hdr; *slot = nullptr; }
-    hdr = new Hdr{need, nullptr};
+    hdr = new AdjScratch{need, nullptr, nullptr};
     if (cudaMalloc(&hdr->ptr, need) != cudaSuccess) { delete hdr; return MPDATA_ENOMEM; }
     *slot = hdr;
   }
+  // the adjoint arrays first, so that they sit at the same place whether or not the tape is
+  // kept in the scratch too (behind them)
   T* cur = static_cast<T*>(hdr->ptr);
-  carve_tape<T>(mode == AdjMode::kStep ? cur : tape, N, K, D, o.fct, psi_n, gc, tp, levels);
-  cur += tape_n * static_cast<size_t>(N);
+  carve_tape<T>(mode == AdjMode::kStep ? cur + adj_arrays(K, D, o.fct) * static_cast<size_t>(N) : tape, N, K, D,
+                o.fct, psi_n, gc, tp, levels);
   auto take = [&]() { T* q = cur; cur += N; return q; };
   // adjoint arrays: first those that only receive atomic scatters (zeroed), then those
   // whose first writer sets them
@@ -488,10 +526,17 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     mxb = take();
     mnb = take();
   }
-  // without the limiter the donor-cell reverse accumulates into every psi adjoint
+  // Without the limiter the donor-cell reverse accumulates into every psi adjoint, which are
+  // cleared on every call.  With it only the arrays before zero_end must start at zero, and
+  // the last kernel of every call clears them again, so only the first call on a scratch
+  // buffer clears them (a CUDA graph captured after that first call holds no memset).
+  const bool chain = o.fct && K >= 2;
   T* const zero_to = o.fct ? zero_end : cur;
-  if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(zero_to - adj_begin) * sizeof(T), st) != cudaSuccess)
-    return MPDATA_ECUDA;
+  if (!chain || hdr->clean != adj_begin) {
+    if (cudaMemsetAsync(adj_begin, 0, static_cast<size_t>(zero_to - adj_begin) * sizeof(T), st) != cudaSuccess)
+      return MPDATA_ECUDA;
+  }
+  hdr->clean = nullptr;
   if (mode == AdjMode::kStep && staged_forward_tape<T>(g, o, gc, G, tp, levels, nullptr, st) != cudaSuccess)
     return MPDATA_ECUDA;
 
@@ -511,18 +556,21 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       P3<T> vhs{{k < K ? vhb[k][0] : nullptr, k < K ? vhb[k][1] : nullptr, k < K ? vhb[k][2] : nullptr}};
       W3<T> vbw{{vbk[k][0], vbk[k][1], vbk[k][2]}};
       W3<T> fbw{{fb[0], fb[1], fb[2]}};
-      ka_fct_a<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vu, vhs, G, o.iga, tp.bu[k], tp.bd[k],
-                                                       tp.mx, tp.mn, k == K, pbl[k - 1], vbw, mxb, mnb, fbw);
+      if (launch_after(ka_fct_a<T, ND>, cell_grid(g, bs), dim3(bs), st, g, pbk, tp.psi[k - 1], vu, vhs, G,
+                       static_cast<bool>(o.iga), tp.bu[k], tp.bd[k], tp.mx, tp.mn, k == K, pbl[k - 1], vbw, mxb,
+                       mnb, fbw) != cudaSuccess)
+        return MPDATA_ECUDA;
       P3<T> fbr{{fb[0], fb[1], fb[2]}};
       P3<T> vbr{{vbk[k][0], vbk[k][1], vbk[k][2]}};
       const bool last = k == 2;
-      ka_fct_b<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, fbr, vbr, tp.psi[k - 1], vu, vprev, G, o.iga, pbl[k - 1],
-                                                       vhbp, last ? mxb : nullptr, last ? mnb : nullptr, tp.psi[0],
-                                                       pbl[0]);
+      if (launch_after(ka_fct_b<T, ND>, cell_grid(g, bs), dim3(bs), st, g, fbr, vbr, tp.psi[k - 1], vu, vprev, G,
+                       static_cast<bool>(o.iga), pbl[k - 1], vhbp, last ? mxb : nullptr, last ? mnb : nullptr,
+                       tp.psi[0], pbl[0]) != cudaSuccess)
+        return MPDATA_ECUDA;
     } else {
       W3<T> vhbk{{vhb[k][0], vhb[k][1], vhb[k][2]}};
       ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1],
-                                                                   vhbk, nullptr, W3<T>{});
+                                                                   vhbk, nullptr, W3<T>{}, nullptr, 0, 0);
       P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
       ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
     }
@@ -534,12 +582,15 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     // already) and gc_bar
     W3<T> out{{nullptr, nullptr, nullptr}};
     for (int d = 0; d < D; ++d) out.p[d] = gc_bar ? static_cast<T*>(gc_bar[d]) : nullptr;
-    ka_donor_flux<T, ND, true><<<cell_grid(g, bs), bs, 0, st>>>(g, pbl[1], tp.psi[0], v1, G, false, pbl[0], vhb1,
-                                                                psi_bar, out);
+    if (launch_after(ka_donor_flux<T, ND, true>, cell_grid(g, bs), dim3(bs), st, g, pbl[1], tp.psi[0], v1, G, false,
+                     pbl[0], vhb1, psi_bar, out, adj_begin, static_cast<int>((zero_end - adj_begin) / N), N) !=
+        cudaSuccess)
+      return MPDATA_ECUDA;
+    if (chain) hdr->clean = adj_begin;
   } else {
     // one pass: psi_bar is this kernel's input, so the result goes through scratch
     ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, psi_bar, tp.psi[0], v1, G, false, pbl[0], vhb1,
-                                                                 nullptr, W3<T>{});
+                                                                 nullptr, W3<T>{}, nullptr, 0, 0);
     if (cudaMemcpyAsync(psi_bar, pbl[0], static_cast<size_t>(N) * sizeof(T), cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)
       return MPDATA_ECUDA;
@@ -572,9 +623,8 @@ int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const 
 }  // namespace
 
 void adjoint_free(mpdata_s* h) {
-  struct Hdr { size_t bytes; void* ptr; };
   void** slot = handle_adj(h);
-  Hdr* hdr = static_cast<Hdr*>(*slot);
+  AdjScratch* hdr = static_cast<AdjScratch*>(*slot);
   if (hdr) {
     cudaFree(hdr->ptr);
     delete hdr;
