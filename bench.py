@@ -52,10 +52,11 @@ def parse_args():
     ap.add_argument("--kernel", choices=["warp", "band"], default=None,
                     help="time this fused kernel family (skips the autotuner)")
     ap.add_argument("--tile-rows", type=int, default=0, help="tile / band rows with --kernel (0 = automatic)")
-    ap.add_argument("--workload", choices=["rotation", "ensemble", "deform3d"], default="rotation",
+    ap.add_argument("--workload", choices=["rotation", "ensemble", "deform3d", "adjoint"], default="rotation",
                     help="rotation: 1024^2 rotating cone (default); ensemble: 512 fields of 64^2..512^2, "
                          "split over the ranks by cell count; deform3d: 256^3 deformational flow, "
-                         "n_iters = 3 + tot + fct, G != 1 (replicas under torchrun)")
+                         "n_iters = 3 + tot + fct, G != 1 (replicas under torchrun); adjoint: the 512^2 "
+                         "adjoint workload alone (one GPU; --no-extras skips its finite-difference check)")
     return ap.parse_args()
 
 
@@ -636,7 +637,7 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
                         "rollout_forward_ms": round((tf1 - tf0) * 1e3, 2),
                         "rollout_backward_ms": round((tb1 - tf1) * 1e3, 2),
                         "backward_over_forward": round((tb1 - tf1) / (tf1 - tf0), 2)}
-            if dt == torch.float64:
+            if dt == torch.float64 and n_dirs > 0:
                 rng = np.random.default_rng(1)
                 errs = []
                 for _ in range(n_dirs):
@@ -906,6 +907,12 @@ def main():
         run_ensemble(args)
     elif args.workload == "deform3d":
         run_deform3d(args, args.n3d)
+    elif args.workload == "adjoint":
+        import torch
+        res = bench_config5(torch.device("cuda", 0), n_dirs=0 if args.no_extras else 8)
+        print(json.dumps({"metric": "adjoint rollout backward / forward (512^2, fct, n_iters 2, 200 steps)",
+                          "value": res["f64"]["backward_over_forward"], "unit": "x (FP64)",
+                          "higher_is_better": False, "data": "synthetic", **res}), flush=True)
     else:
         run_ours(args)
 
