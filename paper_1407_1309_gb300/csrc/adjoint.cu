@@ -511,11 +511,13 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   T* pbl[kTapeMax];
   pbl[0] = take();
   T* vhb[kTapeMax + 1][3] = {};
-  for (int k = 1; k <= K; ++k)
+  for (int k = 1; k < K; ++k)
     for (int d = 0; d < D; ++d) vhb[k][d] = take();
   T* fb[3] = {nullptr, nullptr, nullptr};
   if (o.fct)
     for (int d = 0; d < D; ++d) fb[d] = take();
+  T* const dirty_end = cur;  // under FCT the reverse sweep never writes vhb[K]: it stays zero
+  for (int d = 0; d < D; ++d) vhb[K][d] = take();
   T* const zero_end = cur;
   for (int k = 1; k < K; ++k) pbl[k] = take();
   T* vbk[kTapeMax + 1][3] = {};
@@ -583,7 +585,7 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     W3<T> out{{nullptr, nullptr, nullptr}};
     for (int d = 0; d < D; ++d) out.p[d] = gc_bar ? static_cast<T*>(gc_bar[d]) : nullptr;
     if (launch_after(ka_donor_flux<T, ND, true>, cell_grid(g, bs), dim3(bs), st, g, pbl[1], tp.psi[0], v1, G, false,
-                     pbl[0], vhb1, psi_bar, out, adj_begin, static_cast<int>((zero_end - adj_begin) / N), N) !=
+                     pbl[0], vhb1, psi_bar, out, adj_begin, static_cast<int>((dirty_end - adj_begin) / N), N) !=
         cudaSuccess)
       return MPDATA_ECUDA;
     if (chain) hdr->clean = adj_begin;
