@@ -621,14 +621,23 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
             for x in gg:
                 x.grad = None
             torch.cuda.synchronize(dev)
-            tf0 = time.perf_counter()
-            outT = rollout(m, p0, gg, steps, every)
-            torch.cuda.synchronize(dev)
-            tf1 = time.perf_counter()
-            loss = 0.5 * ((outT.double() - target.double()) ** 2).sum()
-            loss.backward()
-            torch.cuda.synchronize(dev)
-            tb1 = time.perf_counter()
+            fw, bw = [], []
+            for rep in range(3):  # wall-clock medians of three rollouts (forward, then backward)
+                if rep:
+                    p0.grad = None
+                    for x in gg:
+                        x.grad = None
+                tf0 = time.perf_counter()
+                outT = rollout(m, p0, gg, steps, every)
+                torch.cuda.synchronize(dev)
+                tf1 = time.perf_counter()
+                loss = 0.5 * ((outT.double() - target.double()) ** 2).sum()
+                loss.backward()
+                torch.cuda.synchronize(dev)
+                tb1 = time.perf_counter()
+                fw.append(tf1 - tf0)
+                bw.append(tb1 - tf1)
+            tf0, tf1, tb1 = 0.0, statistics.median(fw), statistics.median(fw) + statistics.median(bw)
             key = "f32" if dt == torch.float32 else "f64"
             res[key] = {"forward_step_ms": round(fwd, 4), "adjoint_step_ms": round(adj, 4),
                         "adjoint_over_forward_step": round(adj / fwd, 2),

@@ -143,9 +143,10 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
  * dL/dgc_d is ADDED to gc_bar[d].  Branches (signs, FCT min/max) follow the
  * forward step's choices; [x]+ and [x]- have derivative 1/2 at 0; a min/max
  * passes the derivative of its first extremal candidate.  The step is
- * recomputed internally; the adjoint scratch is allocated on first use and kept
- * with the handle.  Errors: EINVAL; EUNSUPPORTED for batched handles, for the
- * third-order option, for source terms and for n_iters > 4; ENOMEM; ECUDA.
+ * recomputed internally, as mpdata_adjoint_record records it; the adjoint scratch
+ * is allocated on first use and kept with the handle.  Errors: EINVAL;
+ * EUNSUPPORTED for batched handles, for the third-order option, for source terms
+ * and for n_iters > 4; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
                         void* psi_bar, void* const* gc_bar);

@@ -488,7 +488,8 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     if (staged_forward_tape<T>(g, o, gc, G, tp, levels, psi_next, st) != cudaSuccess) return MPDATA_ECUDA;
     return MPDATA_OK;
   }
-  const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) : 0;
+  // the one-call reverse step keeps its tape (and the recorded step's unused result) in the scratch
+  const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) + 1 : 0;
   const size_t need = (tape_n + adj_arrays(K, D, o.fct)) * static_cast<size_t>(N) * sizeof(T);
   void** slot = handle_adj(h);
   // the adjoint scratch is allocated on first use and kept with the handle
@@ -502,8 +503,8 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   // the adjoint arrays first, so that they sit at the same place whether or not the tape is
   // kept in the scratch too (behind them)
   T* cur = static_cast<T*>(hdr->ptr);
-  carve_tape<T>(mode == AdjMode::kStep ? cur + adj_arrays(K, D, o.fct) * static_cast<size_t>(N) : tape, N, K, D,
-                o.fct, psi_n, gc, tp, levels);
+  T* const tape_base = mode == AdjMode::kStep ? cur + adj_arrays(K, D, o.fct) * static_cast<size_t>(N) : tape;
+  carve_tape<T>(tape_base, N, K, D, o.fct, psi_n, gc, tp, levels);
   auto take = [&]() { T* q = cur; cur += N; return q; };
   // adjoint arrays: first those that only receive atomic scatters (zeroed), then those
   // whose first writer sets them
@@ -539,8 +540,19 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       return MPDATA_ECUDA;
   }
   hdr->clean = nullptr;
-  if (mode == AdjMode::kStep && staged_forward_tape<T>(g, o, gc, G, tp, levels, nullptr, st) != cudaSuccess)
-    return MPDATA_ECUDA;
+  if (mode == AdjMode::kStep) {
+    int rc = MPDATA_EUNSUPPORTED;
+    if constexpr (ND == 2) {
+      if (!o.staged) {
+        T* const unused = tape_base + tape_arrays(K, D, o.fct) * static_cast<size_t>(N);
+        const StepArgs<T> a{psi_n, unused, {gc[0], gc[1], nullptr}, nullptr, nullptr, T(0), T(1)};
+        rc = fused_tape<T>(g, o, a, tape_base, st);
+      }
+    }
+    if (rc == MPDATA_EUNSUPPORTED)
+      rc = staged_forward_tape<T>(g, o, gc, G, tp, levels, nullptr, st) == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+    if (rc != MPDATA_OK) return rc;
+  }
 
   const int bs = 256;
   const unsigned nb = static_cast<unsigned>((N + bs - 1) / bs);
