@@ -622,8 +622,8 @@ def bench_config5(dev, n=512, steps=200, every=20, n_dirs=8):
                 x.grad = None
             torch.cuda.synchronize(dev)
             fw, bw = [], []
-            for rep in range(3):  # wall-clock medians of three rollouts (forward, then backward)
-                if rep:
+            for trial in range(3):  # wall-clock medians of three rollouts (forward, then backward)
+                if trial:
                     p0.grad = None
                     for x in gg:
                         x.grad = None
