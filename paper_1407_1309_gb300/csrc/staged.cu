@@ -451,6 +451,164 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
   }
 }
 
+// Pass 1 and the FCT bounds of a 3D field as one z-march (the work of k_donor and k_bounds,
+// same expressions, same order): at step z the donor-cell pass (Eqs. 4-5) forms psi^(1) of
+// plane z on the tile and a one-cell halo into a ring of three planes; then the bounds of
+// plane z-1 (Sect. 3.1.4: extrema of psi^n and psi^(1) over the cell and its face neighbours)
+// are formed and plane z-1 of psi^(1), mx and mn is written.  Shared tiles: psi^n with a
+// two-cell halo on planes z-2 .. z+1; the x and y advector components with halo [-2, +1] and
+// G with halo 1 on plane z; the z component with halo 1 on planes z-1, z.  Each ring has one
+// slot more, into which the next step's plane is copied (cp.async) while this step computes.
+constexpr int kBw = kAx + 4, kBh = kAy + 4;  // psi^n
+constexpr int kXw = kAx + 3, kXh = kAy + 3;  // x and y advector components
+constexpr int kHw = kAx + 2, kHh = kAy + 2;  // z component, G, psi^(1)
+constexpr int kP1N = 5, kP1X = 2, kP1Z = 3, kP1Q = 3;  // ring slots: psi^n, x/y/G, z, psi^(1)
+template <typename T>
+constexpr size_t p1b3_smem() {
+  return sizeof(T) * (kP1N * kBw * kBh + 2 * kP1X * kXw * kXh + (kP1Z + kP1X + kP1Q) * kHw * kHh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kAx * kAy) k_p1b3(Grid g, const T* __restrict__ psi, In3<T> V, T vscale,
+                                                    const T* __restrict__ G, bool kahan, T* __restrict__ p1,
+                                                    T* __restrict__ mx, T* __restrict__ mn) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int nB = kBw * kBh, nX = kXw * kXh, nH = kHw * kHh;
+  T* const sN = reinterpret_cast<T*>(smem_raw);  // [kP1N][nB] psi^n
+  T* const sX = sN + kP1N * nB;                   // [kP1X][nX] x component
+  T* const sY = sX + kP1X * nX;                   // [kP1X][nX] y component
+  T* const sZ = sY + kP1X * nX;                   // [kP1Z][nH] z component
+  T* const sG = sZ + kP1Z * nH;                   // [kP1X][nH] G
+  T* const s1 = sG + kP1X * nH;                   // [kP1Q][nH] psi^(1)
+  const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAx + tx;
+  constexpr int kT = kAx * kAy;
+  const int x0 = blockIdx.x * kAx, y0 = blockIdx.y * kAy;
+  const int zb = blockIdx.z * kAz;
+  const int ze = zb + kAz < nz ? zb + kAz : nz;
+  const long long plane = static_cast<long long>(ny) * nx;
+  // Every plane region is copied with the same element assignment: this thread copies region
+  // elements tid and tid + kT (when they exist), whose in-plane source offsets are fixed.
+  static_assert(nB <= 2 * kT && nX <= 2 * kT && nH <= 2 * kT, "two elements per thread cover a plane");
+  int offB[2], offX[2], offH[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = tid + r * kT;
+    int yy = k / kBw;
+    offB[r] = wrapc(y0 - 2 + yy, ny) * nx + wrapc(x0 - 2 + (k - yy * kBw), nx);
+    yy = k / kXw;
+    offX[r] = wrapc(y0 - 2 + yy, ny) * nx + wrapc(x0 - 2 + (k - yy * kXw), nx);
+    yy = k / kHw;
+    offH[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + (k - yy * kHw), nx);
+  }
+  const bool hasB1 = tid + kT < nB, hasX1 = tid + kT < nX, hasH1 = tid + kT < nH;
+  auto zsrc = [&](const T* base, int z) { return base + static_cast<long long>(wrapc(z, nz)) * plane; };
+  auto copy = [&](T* dst, const T* src, const int (&off)[2], bool has1) {
+    dev::cp_async<sizeof(T)>(dst + tid, src + off[0]);
+    if (has1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + off[1]);
+  };
+  auto slotN = [&](int z) { return (z - zb + 10) % kP1N; };
+  auto slotX = [&](int z) { return (z - zb + 4) % kP1X; };
+  auto slotZ = [&](int z) { return (z - zb + 6) % kP1Z; };
+  auto slot1 = [&](int z) { return (z - zb + 6) % kP1Q; };
+  // the planes step z reads that step z-1 did not: psi^n z+1; the x, y, z components and G of z
+  auto copy_step = [&](int z) {
+    copy(sN + slotN(z + 1) * nB, zsrc(psi, z + 1), offB, hasB1);
+    copy(sX + slotX(z) * nX, zsrc(V.p[2], z), offX, hasX1);
+    copy(sY + slotX(z) * nX, zsrc(V.p[1], z), offX, hasX1);
+    copy(sZ + slotZ(z) * nH, zsrc(V.p[0], z), offH, hasH1);
+    if (G) copy(sG + slotX(z) * nH, zsrc(G, z), offH, hasH1);
+  };
+
+  copy(sN + slotN(zb - 2) * nB, zsrc(psi, zb - 2), offB, hasB1);
+  copy(sN + slotN(zb - 1) * nB, zsrc(psi, zb - 1), offB, hasB1);
+  copy(sZ + slotZ(zb - 2) * nH, zsrc(V.p[0], zb - 2), offH, hasH1);
+  copy_step(zb - 1);
+  dev::cp_commit();
+  dev::cp_wait<0>();
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < nx && y < ny;
+  for (int z = zb - 1; z <= ze; ++z) {
+    __syncthreads();  // step z's planes are in (each thread waited for its own copies)
+    if (z < ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    dev::cp_commit();
+    {  // pass 1 on plane z, tile and one-cell halo
+      const T* Nm = sN + slotN(z - 1) * nB;
+      const T* Nc = sN + slotN(z) * nB;
+      const T* Np = sN + slotN(z + 1) * nB;
+      const T* Zm = sZ + slotZ(z - 1) * nH;
+      const T* Zc = sZ + slotZ(z) * nH;
+      const T* Xc = sX + slotX(z) * nX;
+      const T* Yc = sY + slotX(z) * nX;
+      const T* Gc = sG + slotX(z) * nH;
+      T* const P1 = s1 + slot1(z) * nH;
+      for (int k = tid; k < nH; k += kT) {
+        const int hy = k / kHw, hx = k - hy * kHw;
+        const int b = (hy + 1) * kBw + (hx + 1);  // the cell in the psi^n planes
+        const int q = (hy + 1) * kXw + (hx + 1);  // its x and y faces in the advector planes
+        const T p = Nc[b];
+        T sum = p, comp = T(0);
+        const T Gi = G ? Gc[k] : T(1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const T pp = d == 0 ? Np[b] : (d == 1 ? Nc[b + kBw] : Nc[b + 1]);
+          const T pm = d == 0 ? Nm[b] : (d == 1 ? Nc[b - kBw] : Nc[b - 1]);
+          const T vp = (d == 0 ? Zc[k] : (d == 1 ? Yc[q] : Xc[q])) * vscale;
+          const T vm = (d == 0 ? Zm[k] : (d == 1 ? Yc[q - kXw] : Xc[q - 1])) * vscale;
+          const T Fp = flux(p, pp, vp, false);
+          const T Fm = flux(pm, p, vm, false);
+          const T t0 = G ? -qdiv(Fp, Gi) : -Fp;
+          const T t1 = G ? qdiv(Fm, Gi) : Fm;
+          if (kahan) {
+            T yk = t0 - comp;
+            T u = sum + yk;
+            comp = (u - sum) - yk;
+            sum = u;
+            yk = t1 - comp;
+            u = sum + yk;
+            comp = (u - sum) - yk;
+            sum = u;
+          } else {
+            sum = sum + t0;
+            sum = sum + t1;
+          }
+        }
+        P1[k] = sum;
+      }
+    }
+    __syncthreads();
+    if (z - 1 >= zb && inside) {  // bounds of plane z-1
+      const int zc = z - 1;
+      const int b = (ty + 2) * kBw + (tx + 2), h = (ty + 1) * kHw + (tx + 1);
+      const T* N0 = sN + slotN(zc) * nB;
+      const T* Q0 = s1 + slot1(zc) * nH;
+      const T a0 = N0[b], b0 = Q0[h];
+      T hi = a0 > b0 ? a0 : b0;
+      T lo = a0 < b0 ? a0 : b0;
+      // neighbours in k_bounds's order: z-1, z+1, y-1, y+1, x-1, x+1
+      const T cand[6][2] = {{sN[slotN(zc - 1) * nB + b], s1[slot1(zc - 1) * nH + h]},
+                            {sN[slotN(zc + 1) * nB + b], s1[slot1(zc + 1) * nH + h]},
+                            {N0[b - kBw], Q0[h - kHw]},
+                            {N0[b + kBw], Q0[h + kHw]},
+                            {N0[b - 1], Q0[h - 1]},
+                            {N0[b + 1], Q0[h + 1]}};
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const T a = cand[j][0], c = cand[j][1];
+        hi = a > hi ? a : hi;
+        hi = c > hi ? c : hi;
+        lo = a < lo ? a : lo;
+        lo = c < lo ? c : lo;
+      }
+      const long long i = static_cast<long long>(zc) * plane + static_cast<long long>(y) * nx + x;
+      p1[i] = b0;
+      mx[i] = hi;
+      mn[i] = lo;
+    }
+    dev::cp_wait<0>();
+  }
+}
+
 // One FCT corrective pass of a 3D field as a z-march (the work of k_beta, k_limit and
 // k_donor, same expressions, same order): at plane z the limiting factors of plane z are
 // formed on the tile and a one-cell halo into a ring of three planes; then plane z-1 is
@@ -892,6 +1050,17 @@ void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* 
 }
 
 template <typename T>
+void launch_p1b3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool kahan, T* p1, T* mx, T* mn,
+                 cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_p1b3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p1b3_smem<T>()));
+    attr = true;
+  }
+  k_p1b3<T><<<march3_grid(g), dim3(kAx, kAy), p1b3_smem<T>(), st>>>(g, psi, v, vscale, G, kahan, p1, mx, mn);
+}
+
+template <typename T>
 void launch_corr3(const Grid& g, const T* psi, In3<T> vu, const T* G, bool unit, bool kahan, const T* mx,
                   const T* mn, const T* R, T dt, bool post, Out3<T> lim, T* out, cudaStream_t st) {
   static bool attr = false;  // the FP64 rings exceed the default 48 KB of dynamic shared memory
@@ -919,14 +1088,18 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   // pass 1
   const bool inplace1 = (a.psi_out == a.psi_in) && !o.rhs_b;
   T* dst1 = (K == 1 && !inplace1) ? a.psi_out : s.pa;
-  k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
-                                    K == 1 && o.rhs_a, dst1);
-  if (K == 1) {
-    if (dst1 != a.psi_out)
-      return cudaMemcpyAsync(a.psi_out, dst1, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st);
-    return cudaGetLastError();
+  if (ND == 3 && K >= 2 && o.fct) {  // pass 1 and the bounds in one z-march
+    launch_p1b3<T>(g, p0, gc, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
+  } else {
+    k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
+                                      K == 1 && o.rhs_a, dst1);
+    if (K == 1) {
+      if (dst1 != a.psi_out)
+        return cudaMemcpyAsync(a.psi_out, dst1, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, st);
+      return cudaGetLastError();
+    }
+    if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, s.pa, s.mx, s.mn);
   }
-  if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, s.pa, s.mx, s.mn);
   const T* prev = s.pa;
   In3<T> vprev = gc;
   T vscale = a.gc_scale;
@@ -977,8 +1150,13 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
   if (K == 1 && psi_next)
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, psi_next);
   if (K >= 2) {
-    k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, levels[1]);
-    if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
+    if (ND == 3 && o.fct) {
+      launch_p1b3<T>(g, tp.psi[0], v1, T(1), G, o.kahan, levels[1], tp.mx, tp.mn, st);
+    } else {
+      k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false,
+                                                      levels[1]);
+      if (o.fct) k_bounds<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], tp.psi[1], tp.mx, tp.mn);
+    }
   }
   for (int k = 2; k <= K; ++k) {
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
