@@ -805,8 +805,22 @@ def cpu_baseline(psi_np, gc_np, budget_s=12.0):
     oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=k)
     secs = time.perf_counter() - t0
     cells = psi_np.size
+    # the same oracle on one thread (the plain sweep), on a smaller bounded sample
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=1)
+        one1 = time.perf_counter() - t0
+        k1 = max(1, min(10, int(budget_s / 3 / max(one1, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=k1)
+        secs1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(0)
     return {"value": round(cells * k / secs / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{k} steps of the full {psi_np.shape[0]}x{psi_np.shape[1]} workload, FP64, OpenMP over rows"}
+            "sample": f"{k} steps of the full {psi_np.shape[0]}x{psi_np.shape[1]} workload, FP64, OpenMP over rows",
+            "single_thread": {"value": round(cells * k1 / secs1 / 1e9, 6), "unit": UNIT, "cores": 1,
+                              "sample": f"{k1} steps of the same workload, one thread"}}
 
 
 # ----------------------------------------------------------------------------------- reference arm
