@@ -57,7 +57,10 @@ class MPDATAFunction(torch.autograd.Function):
         solver, n, every = ctx.solver, ctx.n_steps, ctx.every
         pb = grad_out.detach().contiguous().clone()
         gcb = [torch.zeros_like(g) for g in gc]
-        taped = _tapes_fit(solver, min(every, n), pb)
+        taped = _tapes_fit(solver, 2 * min(every, n), pb)  # two buffer sets when pipelined
+        if ctx.use_graphs and taped:
+            return (None, None, None, None, *_pipelined_backward(solver, ckpts, gc, pb, n, every))
+        taped = taped or _tapes_fit(solver, min(every, n), pb)
         if ctx.use_graphs:
             used = []
             for seg in range(n_ck - 1, -1, -1):
@@ -105,6 +108,66 @@ def _tapes_fit(solver: Mpdata, length: int, like) -> bool:
     return need <= free // 4
 
 
+def _pipelined_backward(solver: Mpdata, ckpts, gc, pb, n: int, every: int):
+    """The taped backward with graphs, two segments in flight: while one segment's reverse
+    sweeps run on one stream, the next segment (earlier in time; it needs only its checkpoint)
+    records its states and tapes on another.  Two buffer sets alternate between segments."""
+    dev = pb.device
+    cur = torch.cuda.current_stream(dev)
+    gcb = [torch.zeros_like(g) for g in gc]
+    s_rec, s_rev = _pipeline_streams(solver, dev)
+    s_rec.wait_stream(cur)
+    s_rev.wait_stream(cur)
+    segs = []  # (segment, its buffer set), last segment first
+    for idx, seg in enumerate(range(len(ckpts) - 1, -1, -1)):
+        start, end = seg * every, min(seg * every + every, n)
+        segs.append((seg, _segment_graph(solver, end - start, pb, gc, True, idx % 2)))
+    used = []
+    for _, sg in segs:
+        if sg not in used:
+            used.append(sg)
+    with torch.cuda.stream(s_rev):
+        for sg in used:
+            sg.load(gc)
+    s_rec.wait_stream(s_rev)
+    last_rev = {}  # buffer set -> event after its last reverse sweep
+    for seg, sg in segs:
+        if sg in last_rev:
+            s_rec.wait_event(last_rev[sg])
+        with torch.cuda.stream(s_rec):
+            sg.states[0].copy_(ckpts[seg])
+            sg.rec_graph.replay()
+            recorded = torch.cuda.Event()
+            recorded.record(s_rec)
+        s_rev.wait_event(recorded)
+        with torch.cuda.stream(s_rev):
+            sg.pb.copy_(pb)
+            sg.rev_graph.replay()
+            pb.copy_(sg.pb)
+            done = torch.cuda.Event()
+            done.record(s_rev)
+        last_rev[sg] = done
+    with torch.cuda.stream(s_rev):
+        for sg in used:
+            for acc, b in zip(gcb, sg.gcb):
+                acc += b
+    cur.wait_stream(s_rev)
+    cur.wait_stream(s_rec)
+    for t in [pb, *gcb, *ckpts]:
+        t.record_stream(s_rev)
+    for t in ckpts:
+        t.record_stream(s_rec)
+    return (pb, *gcb)
+
+
+def _pipeline_streams(solver: Mpdata, dev):
+    streams = solver.__dict__.get("_pipeline_streams")
+    if streams is None:
+        streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+        solver.__dict__["_pipeline_streams"] = streams
+    return streams
+
+
 class _SegmentGraph:
     """The backward work of one checkpoint segment (recompute its states, then the adjoint
     steps last to first) captured as a CUDA graph on static buffers: the states, psi_bar,
@@ -134,15 +197,21 @@ class _SegmentGraph:
                     solver.adjoint_record(self.states[0], gc, tapes[0], psi_next=tmp)
                     solver.adjoint_replay(self.states[0], gc, tapes[0], tmp, gc_bar=scratch)
             side.synchronize()
-            self.graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(self.graph, stream=side):
-                if taped:
+            if taped:  # the recording and the reverse sweeps as separate graphs, so that they
+                # can run on two streams (_pipelined_backward), or back to back (run)
+                self.rec_graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.rec_graph, stream=side):
                     for s in range(length):
                         nxt = self.states[s + 1] if s + 1 < length else None
                         solver.adjoint_record(self.states[s], gc, tapes[s], psi_next=nxt)
+                self.rev_graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.rev_graph, stream=side):
                     for s in range(length - 1, -1, -1):
                         solver.adjoint_replay(self.states[s], gc, tapes[s], self.pb, gc_bar=gcb)
-                else:
+                self.graph = None
+            else:
+                self.graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self.graph, stream=side):
                     for s in range(length - 1):
                         solver.advance(self.states[s], self.states[s + 1], gc)
                     for s in range(length - 1, -1, -1):
@@ -160,15 +229,20 @@ class _SegmentGraph:
     def run(self, checkpoint, pb):
         self.states[0].copy_(checkpoint)
         self.pb.copy_(pb)
-        self.graph.replay()
+        if self.graph is None:
+            self.rec_graph.replay()
+            self.rev_graph.replay()
+        else:
+            self.graph.replay()
         pb.copy_(self.pb)
 
 
-def _segment_graph(solver: Mpdata, length: int, like, gc, taped: bool) -> _SegmentGraph:
+def _segment_graph(solver: Mpdata, length: int, like, gc, taped: bool, slot: int = 0) -> _SegmentGraph:
     """The captured segment of this length, kept on the handle (a rollout has at most two
-    segment lengths: checkpoint_every and the remainder)."""
+    segment lengths: checkpoint_every and the remainder; the pipelined backward uses two
+    buffer sets, `slot` 0 and 1, of each)."""
     cache = solver.__dict__.setdefault("_segment_graphs", {})
-    key = (length, like.dtype, tuple(like.shape), taped)
+    key = (length, like.dtype, tuple(like.shape), taped, slot)
     if key not in cache:
         cache[key] = _SegmentGraph(solver, length, like, gc, taped)
     return cache[key]
