@@ -15,7 +15,9 @@ the gradient is that of the staged trajectory from each checkpoint.  Memory is
 one field per checkpoint plus one segment of states (and tapes).  With
 use_graphs (default) the work of one segment is captured once as a CUDA graph
 on static buffers and replayed per segment, so the host issues one replay per
-segment instead of tens of launches per step.
+segment instead of tens of launches per step; with tapes, the recording of the
+next segment (earlier in time) runs on a second stream while the current
+segment's reverse sweeps run, on two alternating buffer sets.
 """
 from __future__ import annotations
 
