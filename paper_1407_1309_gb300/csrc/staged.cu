@@ -1088,7 +1088,9 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   // pass 1
   const bool inplace1 = (a.psi_out == a.psi_in) && !o.rhs_b;
   T* dst1 = (K == 1 && !inplace1) ? a.psi_out : s.pa;
-  if (ND == 3 && K >= 2 && o.fct) {  // pass 1 and the bounds in one z-march
+  // FP32: pass 1 and the bounds in one z-march (FP64 is arithmetic-bound and the z-march
+  // recomputes pass 1 on a one-cell halo)
+  if (ND == 3 && K >= 2 && o.fct && sizeof(T) == 4) {
     launch_p1b3<T>(g, p0, gc, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
   } else {
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
@@ -1150,7 +1152,7 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
   if (K == 1 && psi_next)
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false, psi_next);
   if (K >= 2) {
-    if (ND == 3 && o.fct) {
+    if (ND == 3 && o.fct && sizeof(T) == 4) {
       launch_p1b3<T>(g, tp.psi[0], v1, T(1), G, o.kahan, levels[1], tp.mx, tp.mn, st);
     } else {
       k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[0], v1, T(1), false, G, o.kahan, nullptr, T(0), false,
