@@ -34,8 +34,10 @@
  * Sect. 2.4).  All device work is enqueued on the handle's stream and is
  * asynchronous; a device-side failure is reported by the next call on the
  * handle that synchronises (mpdata_reduce, mpdata_sync).  No kernel of this
- * library waits on another block (block barriers only), so no call can hang on
- * a device-side wait.
+ * library waits on another block of its grid (block barriers only); the reverse
+ * step's kernels, launched as programmatic dependents, wait only for the
+ * completion of the kernel before them on the stream.  No call can hang on a
+ * device-side wait.
  */
 #ifndef MPDATA_GB300_H
 #define MPDATA_GB300_H
