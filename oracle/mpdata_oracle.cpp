@@ -51,7 +51,7 @@ namespace {
 
 /* Option bits of the oracle (the same values the library interface defines). */
 constexpr unsigned O_FCT = 1u, O_TOT = 2u, O_IGA = 4u, O_NUG = 8u, O_KAHAN = 16u,
-                   O_RHS_A = 32u, O_RHS_B = 64u;
+                   O_RHS_A = 32u, O_RHS_B = 64u, O_ABS = 256u;
 
 /* ------------------------------------------------------------------ grid */
 
@@ -138,6 +138,7 @@ struct Ctx {
   Ids id;
   int K = 1;
   bool fct = false, tot = false, iga = false, kahan = false, rhs_a = false, rhs_b = false;
+  bool abs = false;  /* |psi| in every psi-fraction of the pseudo-velocity (Sect. 3.1.5) */
   const double* G = nullptr;  /* NULL => G = 1 */
   const double* R = nullptr;
   double dt = 0.0;
@@ -238,9 +239,11 @@ template <class T, class Get> T f_bound(const Ctx& c, long i, bool upper, Get ge
  *   D_q1q2 = frac(pairs at (+q1+q2) - (+q1-q2) - (-q1+q2) + (-q1-q2), their sum),
  *            a pair being psi_j + psi_{j+e_d}. */
 template <class T, class Get>
-T f_tot(const Ctx& c, int k, int d, long i, const T& V, const T* Vq, double Gb, Get get) {
+T f_tot(const Ctx& c, int k, int d, long i, const T& V, const T* Vq, double Gb, Get get_psi) {
   const Grid& g = c.g;
   const int P = c.id.psi(k - 1);
+  /* variable-sign option: the psi values of the fractions enter as |psi| */
+  auto get = [&](int a, long j) { return c.abs ? absv(get_psi(a, j)) : get_psi(a, j); };
   const Cell x = cell_of(g, i);
   T pm = get(P, nbr(g, i, d, -1));
   T p0 = get(P, i);
@@ -292,7 +295,9 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
   const long ip = lin(g, sh(g, x, d, +1));
   const double Gb = 0.5 * (c.Gc(i) + c.Gc(ip));
   T V = get(c.adv(k - 1, d), i);
-  T p0 = get(P, i), p1 = get(P, ip);
+  /* variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi| */
+  auto psi = [&](long j) { return c.abs ? absv(get(P, j)) : get(P, j); };
+  T p0 = psi(i), p1 = psi(ip);
   T A = c.iga ? (p1 - p0) * 0.5 : frac(p1 - p0, p0 + p1);
   T out = (absv(V) - V * V / Gb) * A;
   T Vq[3];
@@ -303,8 +308,8 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
     const long iqp = lin(g, xp), idqp = lin(g, sh(g, xp, d, +1));
     const long iqm = lin(g, xm), idqm = lin(g, sh(g, xm, d, +1));
     Vq[q] = 0.25 * ((get(Q, i) + get(Q, ip)) + (get(Q, iqm) + get(Q, idqm)));
-    T Tp = get(P, iqp) + get(P, idqp);
-    T Bt = get(P, iqm) + get(P, idqm);
+    T Tp = psi(iqp) + psi(idqp);
+    T Bt = psi(iqm) + psi(idqm);
     T B = c.iga ? (Tp - Bt) * 0.25 : frac(Tp - Bt, Tp + Bt);
     out = out - 0.5 * V * Vq[q] / Gb * B;
   }
@@ -425,6 +430,7 @@ int setup(Ctx& c, int nd, const int64_t* shape, const double* const* gc, const d
           const double* r, double dt, int n_iters, unsigned opts) {
   if (nd < 1 || nd > 3 || !shape || n_iters < 1) return 1;
   if ((opts & O_IGA) && n_iters != 2) return 1;
+  if ((opts & O_IGA) && (opts & O_ABS)) return 1;  /* two alternative variable-sign options */
   if ((opts & O_RHS_A) && (opts & O_RHS_B)) return 1;
   if (((opts & (O_RHS_A | O_RHS_B)) != 0) != (r != nullptr)) return 1;
   if (((opts & O_NUG) != 0) != (g != nullptr)) return 1;
@@ -442,6 +448,7 @@ int setup(Ctx& c, int nd, const int64_t* shape, const double* const* gc, const d
   c.fct = opts & O_FCT;
   c.tot = opts & O_TOT;
   c.iga = opts & O_IGA;
+  c.abs = opts & O_ABS;
   c.kahan = opts & O_KAHAN;
   c.rhs_a = opts & O_RHS_A;
   c.rhs_b = opts & O_RHS_B;

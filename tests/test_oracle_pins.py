@@ -33,6 +33,8 @@ OPTION_SETS = {
     "iga_fct": (2, oracle.IGA | oracle.FCT),
     "iga_tot_fct": (2, oracle.IGA | oracle.TOT | oracle.FCT),
     "kahan_fct": (2, oracle.KAHAN | oracle.FCT),
+    "abs_fct": (2, oracle.ABS | oracle.FCT),
+    "abs_tot3": (3, oracle.ABS | oracle.TOT),
 }
 
 
@@ -362,3 +364,76 @@ def test_adjoint_dot_product(shape, name):
     lhs = float(np.sum(tl * y))
     rhs = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+# ----------------------------------------------------------------------------- variable-sign option (abs)
+
+ABS_SETS = {"basic": (2, 0), "fct": (2, oracle.FCT), "it3_fct": (3, oracle.FCT), "tot3_fct": (3, oracle.TOT | oracle.FCT)}
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("name", sorted(ABS_SETS))
+def test_abs_equals_the_basic_scheme_on_one_signed_fields(shape, name):
+    """Sect. 3.1.5: the abs option replaces psi by |psi| in the psi-fractions only, so on a
+    positive field it is the basic scheme, bit for bit, and on a negative field the basic
+    scheme's odd reflection."""
+    n_iters, opts = ABS_SETS[name]
+    rng = np.random.default_rng(len(shape) + n_iters)
+    gc = nondivergent(shape, rng, 0.4)
+    psi = 1.0 + rng.uniform(size=shape)
+    st = lambda p, o: oracle.step(p, gc, n_iters=n_iters, opts=o, n_steps=3)
+    assert np.array_equal(st(psi, opts | oracle.ABS), st(psi, opts))
+    assert np.array_equal(st(-psi, opts | oracle.ABS), -st(psi, opts))
+
+
+def test_abs_keeps_the_psi_fraction_bounded():
+    """Sect. 3.1.5: with a variable-sign field the psi-fraction of Eq. 6 is unbounded where two
+    neighbouring values nearly cancel (here psi^(1) = 1 and -1 + 1e-6 after the donor pass at
+    C = 1/2, so the basic scheme's pseudo-velocity is about -5e5); with |psi| it stays within
+    [-1, 1] and the step stays within the initial range.  Both conserve the sum."""
+    eps = 1e-6
+    psi = np.array([0.5, 1.0, 1.0, -3.0 + 2 * eps, -2.0, -1.0, 0.0, 0.2])
+    gc = [np.full(psi.shape, 0.5)]
+    basic = oracle.step(psi, gc, n_iters=2)
+    absv = oracle.step(psi, gc, n_iters=2, opts=oracle.ABS)
+    assert np.abs(basic).max() > 1e5
+    assert np.abs(absv).max() <= np.abs(psi).max()
+    for out in (basic, absv):
+        assert abs(out.sum() - psi.sum()) <= 1e-9 * np.abs(psi).sum()
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("name", ["fct", "tot3_fct"])
+def test_abs_on_variable_sign_fields(shape, name):
+    """abs on a variable-sign field: conservation (the fluxes telescope, Eq. 4), odd symmetry
+    and scaling by powers of two (|psi| fractions are invariant under both; exact in floating
+    point), the FCT bounds (Sect. 3.1.4), and a constant field of either sign is kept."""
+    n_iters, opts = ABS_SETS[name]
+    opts |= oracle.ABS
+    rng = np.random.default_rng(11 * len(shape))
+    gc = nondivergent(shape, rng, 0.4)
+    psi = rng.normal(size=shape)
+    st = lambda p: oracle.step(p, gc, n_iters=n_iters, opts=opts, n_steps=5)
+    out = st(psi)
+    assert abs(out.sum() - psi.sum()) <= 1e-13 * np.abs(psi).sum() * 5
+    assert np.array_equal(st(-psi), -out)
+    assert np.array_equal(st(4.0 * psi), 4.0 * out)
+    one = oracle.step(psi, gc, n_iters=n_iters, opts=opts)
+    assert one.max() <= psi.max() + 1e-12 and one.min() >= psi.min() - 1e-12
+    for c in (2.5, -2.5):
+        const = st(np.full(shape, c))
+        assert np.abs(const - c).max() <= 1e-13 * abs(c)
+
+
+def test_abs_depends_on_the_background_and_excludes_iga():
+    """Sect. 3.4.1 (the abs results' ripples depend on the constant background, unlike the
+    infinite gauge, the linear limit): abs(psi + c) != abs(psi) + c; and abs and the infinite
+    gauge are alternatives (the combination is rejected)."""
+    rng = np.random.default_rng(5)
+    shape = (14, 13)
+    gc = nondivergent(shape, rng, 0.35)
+    a = rng.normal(size=shape)
+    st = lambda p: oracle.step(p, gc, n_iters=2, opts=oracle.ABS, n_steps=3)
+    assert np.abs(st(a + 3.0) - (st(a) + 3.0)).max() > 1e-6
+    with pytest.raises(ValueError):
+        oracle.step(a, gc, n_iters=2, opts=oracle.ABS | oracle.IGA)
