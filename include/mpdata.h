@@ -63,8 +63,11 @@ enum {
   MPDATA_KAHAN = 16u,       /* compensated summation in the donor-cell passes (Sect. 3.1.1) */
   MPDATA_RHS_EULER_A = 32u, /* psi^{n+1} = ADV(psi^n) + dt R (Sect. 4.1) */
   MPDATA_RHS_EULER_B = 64u, /* psi^{n+1} = ADV(psi^n + dt R) (Sect. 4.1) */
-  MPDATA_STAGED = 128u      /* run the one-kernel-per-sub-step path even where a fused
+  MPDATA_STAGED = 128u,     /* run the one-kernel-per-sub-step path even where a fused
                                kernel covers the case (comparison and testing) */
+  MPDATA_ABS = 256u         /* variable-sign fields: |psi| in every psi-fraction of the
+                               pseudo-velocity (Sect. 3.1.5); excludes MPDATA_IGA.  Runs on
+                               the one-kernel-per-sub-step path; no reverse step */
 };
 
 /* status codes */
@@ -86,7 +89,7 @@ enum {
  * opts: OR of MPDATA_* option bits.  cuda_stream: a cudaStream_t (NULL = legacy
  * default stream) on the current device; all work of the handle goes there.
  * Errors: EINVAL for ndims not in 1..3, n_fields < 1, a non-positive extent,
- * n_iters < 1, IGA with n_iters != 2, both RHS bits; ENOMEM; ECUDA.
+ * n_iters < 1, IGA with n_iters != 2, IGA with ABS, both RHS bits; ENOMEM; ECUDA.
  */
 int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype,
                   int n_iters, uint32_t opts, void* cuda_stream);
@@ -147,7 +150,7 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
  * passes the derivative of its first extremal candidate.  The step is
  * recomputed internally, as mpdata_adjoint_record records it; the adjoint scratch
  * is allocated on first use and kept with the handle.  Errors: EINVAL;
- * EUNSUPPORTED for batched handles, for the third-order option, for source terms
+ * EUNSUPPORTED for batched handles, for the third-order and abs options, for source terms
  * and for n_iters > 4; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,

@@ -183,18 +183,20 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
 // values it uses (over their count under infinite gauge).
 template <typename T, int ND>
 __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vscale,
-                           const T* __restrict__ G, bool iga, bool tot, Out3<T> Vout) {
+                           const T* __restrict__ G, bool iga, bool tot, bool abs_psi, Out3<T> Vout) {
+  // variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
+  auto ps = [&](long long j) { const T v = psi[j]; return abs_psi ? absv(v) : v; };
   FOR_CELLS(g) {
   const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});
   const long long i = nb.i;
-  const T p0 = psi[i];
+  const T p0 = ps(i);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
     // every 1/Gb of the face is one reciprocal, multiplied in
     const T rGb = G ? qdiv(T(1), T(0.5) * (G[i] + G[ip])) : T(1);
     const T V = Vin.p[d][i] * vscale;
-    const T p1 = psi[ip];
+    const T p1 = ps(ip);
     const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
     T out = (absv(V) - V * V * rGb) * A;
     T Vq[3] = {T(0), T(0), T(0)};
@@ -205,14 +207,14 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
       const T* Q = Vin.p[q];
       Vq[q] = T(0.25) * ((Q[i] * vscale + Q[ip] * vscale) + (Q[iqm] * vscale + Q[idqm] * vscale));
-      const T Tp = psi[iqp] + psi[idqp];
-      const T Bt = psi[iqm] + psi[idqm];
+      const T Tp = ps(iqp) + ps(idqp);
+      const T Bt = ps(iqm) + ps(idqm);
       const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
       out = out - T(0.5) * V * Vq[q] * rGb * B;
     }
     if (tot) {
-      const T pm = psi[nb.at(d, -1)];
-      const T p2 = psi[nb.at(d, +2)];
+      const T pm = ps(nb.at(d, -1));
+      const T p2 = ps(nb.at(d, +2));
       const T num = ((p2 - p1) - p0) + pm;
       const T D = iga ? num * T(0.25) : fracg(num, ((p2 + p1) + p0) + pm);
       out = out + ((T(3) * V * absv(V)) * rGb - (T(2) * V * V * V) * (rGb * rGb) - V) * T(1.0 / 3.0) * D;
@@ -221,8 +223,8 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       for (int q = 0; q < ND; ++q) {
         if (q == d) continue;
         qs[nq++] = q;
-        const T a = psi[nb.at(q, +1)], b = psi[nb.at2(q, +1, d, +1)];
-        const T e = psi[nb.at(q, -1)], f = psi[nb.at2(q, -1, d, +1)];
+        const T a = ps(nb.at(q, +1)), b = ps(nb.at2(q, +1, d, +1));
+        const T e = ps(nb.at(q, -1)), f = ps(nb.at2(q, -1, d, +1));
         const T n2 = (b - a) - (f - e);
         const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
         out = out + absv(V) * Vq[q] * rGb * (T(1) - T(2) * absv(V) * rGb) * D2;
@@ -235,7 +237,7 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
 #pragma unroll
           for (int s2 = 1; s2 >= -1; s2 -= 2) {
             const long long y = nb.i + nb.off[qs[0]][s1 + 2] + nb.off[qs[1]][s2 + 2];
-            pr[m++] = psi[y] + psi[y + nb.off[d][3]];
+            pr[m++] = ps(y) + ps(y + nb.off[d][3]);
           }
         }
         // pr = {(+,+), (+,-), (-,+), (-,-)}
@@ -282,7 +284,7 @@ constexpr size_t antidiff3_smem() {
 template <typename T>
 __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __restrict__ psi, In3<T> Vin,
                                                          T vscale, const T* __restrict__ G, bool iga, bool tot,
-                                                         Out3<T> Vout) {
+                                                         bool abs_psi, Out3<T> Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int nP = kPw * kPh, nV = kVw * kVh;
   T* const sP = reinterpret_cast<T*>(smem_raw);  // [kA3P][nP]
@@ -381,7 +383,11 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
       const T* vy[2] = {Vp(1, z) + cV, Vp(1, z + 1) + cV};      // y component, planes z, z+1
       const T* vx[2] = {Vp(2, z) + cV, Vp(2, z + 1) + cV};      // x component, planes z, z+1
       const T* gz[2] = {Gp(z) + cV, Gp(z + 1) + cV};
-      auto P = [&](int dz, int dy, int dx) { return pz[dz + 1][dy * kPw + dx]; };
+      // variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
+      auto P = [&](int dz, int dy, int dx) {
+        const T v = pz[dz + 1][dy * kPw + dx];
+        return abs_psi ? absv(v) : v;
+      };
       auto Q = [&](int q, int dz, int dy, int dx) {
         return q == 0 ? vz[dz + 1][dy * kVw + dx] : (q == 1 ? vy[dz][dy * kVw + dx] : vx[dz][dy * kVw + dx]);
       };
@@ -1038,7 +1044,8 @@ template <typename T>
 size_t steps1d_smem(long long n) { return static_cast<size_t>(kSteps1dArrays) * static_cast<size_t>(n) * sizeof(T); }
 
 template <typename T>
-void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, Out3<T> out,
+void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, bool abs_psi,
+                      Out3<T> out,
                       cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -1046,7 +1053,8 @@ void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* 
                          static_cast<int>(antidiff3_smem<T>()));
     attr = true;
   }
-  k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, out);
+  k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, abs_psi,
+                                                                                     out);
 }
 
 template <typename T>
@@ -1109,9 +1117,9 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
     if (ND == 3) {
-      launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, vk, st);
+      launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk, st);
     } else {
-      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, vk);
+      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk);
     }
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
     // FP32: factors, limiter and donor pass in one z-march (it limits each face from both sides
@@ -1164,9 +1172,10 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (ND == 3) {
-      launch_antidiff3<T>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk, st);
+      launch_antidiff3<T>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs, vk, st);
     } else {
-      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, vk);
+      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs,
+                                                         vk);
     }
     In3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (o.fct) {
@@ -1235,7 +1244,7 @@ template StagedScratch<double> carve_staged<double>(void*, long long);
 template <typename T>
 int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc, const T* G, const T* R, T dt,
             int n_steps, cudaStream_t st) {
-  if (g.nd != 1 || o.n_iters > 64) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 1 || o.n_iters > 64 || o.abs) return MPDATA_EUNSUPPORTED;
   const size_t smem = steps1d_smem<T>(g.N);
   static int max_smem = -1;
   if (max_smem < 0) {
