@@ -380,21 +380,6 @@ def run_ours(args):
                     "rel_l2": float(np.linalg.norm(ec) / np.linalg.norm(ref64)),
                     "max_abs": float(np.abs(ec).max()),
                     "rel_mass_drift": float(abs(got.sum() - psi_np.sum()) / abs(psi_np.sum()))}}
-        try:
-            import oracle
-            oracle.set_threads(0)
-            p32 = psi0.double().cpu().numpy()
-            g32 = [v.double().cpu().numpy() for v in gc]
-            ref = oracle.step(p32, g32, n_iters=2, opts=oracle.FCT, n_steps=10)
-            with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev) as mm:
-                x = psi0.clone()
-                y = torch.empty_like(x)
-                mm.advance(x, y, gc, n_steps=10)
-                got = y.double().cpu().numpy()
-            extras["err_vs_oracle_10_steps"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                                                "max_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
-        except Exception as ex:  # the oracle leg must not sink the bench line
-            extras["err_vs_oracle_10_steps"] = {"error": str(ex)[:200]}
         # staged path (one kernel per sub-step) for comparison
         with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT | capi.STAGED, device=dev) as ms:
             x, y = psi0.clone(), torch.empty_like(psi0)
@@ -412,8 +397,16 @@ def run_ours(args):
             st = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
             extras["staged_path"] = {"value": round(cells * ks / st / 1e9, 3), "unit": UNIT, "steps": ks,
                                      "kernels_per_step": 6}
+        extras["abs_variable_sign"] = bench_abs(psi_np, gc_np, dtype, dev, stream, flush, min(args.steps, 300))
         out["e2e"] = run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
-        out["cpu_baseline"] = cpu_baseline(psi_np, gc_np)
+        def gpu_steps(k):  # this build's step from the same FP32 input, for the oracle leg's comparison
+            with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev) as mm:
+                x, y = psi0.clone(), torch.empty_like(psi0)
+                mm.advance(x, y, gc, n_steps=k)
+                return y.double().cpu().numpy()
+
+        out["cpu_baseline"] = cpu_baseline(psi0.double().cpu().numpy(), [v.double().cpu().numpy() for v in gc],
+                                           gpu_steps=gpu_steps)
         out["extras"] = extras
         configs = {}
         for name, fn in (("1d", bench_config1), ("3d", bench_config3), ("ensemble", bench_config4),
@@ -438,12 +431,56 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def bench_abs(psi_np, gc_np, dtype, dev, stream, flush, steps):
+    """The variable-sign option (abs, Sect. 3.1.5) on the rotation workload shifted to cross zero
+    (cone top +1.5 over a background of -1.5), FCT, on the staged kernels (the fused ones
+    decline it): each step timed between CUDA events after an L2 flush, and 10 steps against
+    the same option in FP64 on the GPU (whose parity with the oracle the tests check)."""
+    import numpy as np
+    import torch
+
+    from paper_1407_1309_gb300 import capi
+    from paper_1407_1309_gb300.solver import Mpdata
+    n = psi_np.shape[0]
+    psi_v = psi_np - 2.5
+    opts = capi.ABS | capi.FCT
+    with Mpdata((n, n), dtype=dtype, n_iters=2, opts=opts, device=dev) as m:
+        x = torch.tensor(psi_v, dtype=dtype, device=dev)
+        y = torch.empty_like(x)
+        gc = [torch.tensor(v, dtype=dtype, device=dev) for v in gc_np]
+        m.advance(x, y, gc, n_steps=3)
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.advance(x, y, gc)
+            e1.record(stream)
+            evs.append((e0, e1))
+            x, y = y, x
+        torch.cuda.synchronize(dev)
+        secs = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
+        res = {"value": round(n * n * steps / secs / 1e9, 3), "unit": UNIT, "steps": steps,
+               "workload": f"2d_rotation_{n}x{n}_variable_sign_abs_fct", "path": "staged kernels"}
+        p0 = torch.tensor(psi_v, dtype=dtype, device=dev)
+        q = torch.empty_like(p0)
+        m.advance(p0, q, gc, n_steps=10)
+        got = q.double().cpu().numpy()
+    with Mpdata((n, n), dtype=torch.float64, n_iters=2, opts=opts, device=dev) as m64:
+        p64 = p0.double()
+        q64 = torch.empty_like(p64)
+        m64.advance(p64, q64, [v.double() for v in gc], n_steps=10)
+        ref = q64.cpu().numpy()
+    res["err_vs_fp64_gpu_10_steps"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                                       "max_abs": float(np.abs(got - ref).max())}
+    return res
+
+
 def bench_config1(dev):
     """1D: N = 500, C = 0.5, box + Gaussian, two passes, FP64, 1000 steps = one transit."""
     import numpy as np
     import torch
 
-    import oracle
     from paper_1407_1309_gb300 import workloads
     from paper_1407_1309_gb300.solver import Mpdata
     psi, gc = workloads.hello_1d()
@@ -459,10 +496,8 @@ def bench_config1(dev):
         torch.cuda.synchronize(dev)
         secs = e0.elapsed_time(e1) / 1e3
         out = b.cpu().numpy()
-    ref = oracle.step(psi, gc, n_iters=2, n_steps=1000)
     return {"workload": "1d_box_gaussian_n500_c0.5_n_iters2_f64", "steps": 1000, "time_ms": round(secs * 1e3, 3),
             "value": round(500 * 1000 / secs / 1e9, 4), "unit": UNIT,
-            "err_vs_oracle_max_rel": float(np.abs(out - ref).max() / np.abs(ref).max()),
             "one_transit_rms_err_vs_initial": float(np.sqrt(np.mean((out - psi) ** 2))),
             "path": "one launch of one block for all steps (field and intermediates in shared memory; FP64 rate of one SM)"}
 
@@ -793,8 +828,12 @@ def run_e2e(m, psi_np, gc_np, dtype, dev, stream, K, ws):
             "overlap": "copies of neighbouring steps overlap the step (3 streams, 2 buffer sets)"}
 
 
-def cpu_baseline(psi_np, gc_np, budget_s=12.0):
-    """The oracle as it stands on this host's cores, on a bounded sample of the workload."""
+def cpu_baseline(psi_np, gc_np, budget_s=12.0, gpu_steps=None):
+    """The oracle as it stands on this host's cores, on a bounded sample of the workload.
+    With gpu_steps (k -> this build's result after k steps from the same input), the oracle's
+    timed result is also the reference of the GPU run's error."""
+    import numpy as np
+
     import oracle
     cores = oracle.set_threads(0)
     t0 = time.perf_counter()
@@ -802,8 +841,13 @@ def cpu_baseline(psi_np, gc_np, budget_s=12.0):
     one = time.perf_counter() - t0
     k = max(1, min(40, int(budget_s / max(one, 1e-3))))
     t0 = time.perf_counter()
-    oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=k)
+    ref = oracle.step(psi_np, gc_np, n_iters=2, opts=oracle.FCT, n_steps=k)
     secs = time.perf_counter() - t0
+    err = None
+    if gpu_steps is not None:
+        got = gpu_steps(k)
+        err = {"steps": k, "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+               "max_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
     cells = psi_np.size
     # the same oracle on one thread (the plain sweep), on a smaller bounded sample
     oracle.set_threads(1)
@@ -820,7 +864,8 @@ def cpu_baseline(psi_np, gc_np, budget_s=12.0):
     return {"value": round(cells * k / secs / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} steps of the full {psi_np.shape[0]}x{psi_np.shape[1]} workload, FP64, OpenMP over rows",
             "single_thread": {"value": round(cells * k1 / secs1 / 1e9, 6), "unit": UNIT, "cores": 1,
-                              "sample": f"{k1} steps of the same workload, one thread"}}
+                              "sample": f"{k1} steps of the same workload, one thread"},
+            "gpu_fp32_err_vs_this_run": err}
 
 
 # ----------------------------------------------------------------------------------- reference arm
