@@ -28,6 +28,7 @@ LIB = os.path.join(BUILD_DIR, "libmpdata_oracle.so")
 # option bits, same values as the library interface (the oracle defines its own)
 FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B = 1, 2, 4, 8, 16, 32, 64
 ABS = 256  # |psi| in the psi-fractions of the pseudo-velocity (variable-sign fields)
+DFL = 512  # divergent-flow term of the pseudo-velocity
 
 _lock = threading.Lock()
 _lib = None

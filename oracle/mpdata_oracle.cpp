@@ -51,7 +51,7 @@ namespace {
 
 /* Option bits of the oracle (the same values the library interface defines). */
 constexpr unsigned O_FCT = 1u, O_TOT = 2u, O_IGA = 4u, O_NUG = 8u, O_KAHAN = 16u,
-                   O_RHS_A = 32u, O_RHS_B = 64u, O_ABS = 256u;
+                   O_RHS_A = 32u, O_RHS_B = 64u, O_ABS = 256u, O_DFL = 512u;
 
 /* ------------------------------------------------------------------ grid */
 
@@ -139,6 +139,7 @@ struct Ctx {
   int K = 1;
   bool fct = false, tot = false, iga = false, kahan = false, rhs_a = false, rhs_b = false;
   bool abs = false;  /* |psi| in every psi-fraction of the pseudo-velocity (Sect. 3.1.5) */
+  bool dfl = false;  /* divergent-flow term of the pseudo-velocity (Sect. 3.1.3) */
   const double* G = nullptr;  /* NULL => G = 1 */
   const double* R = nullptr;
   double dt = 0.0;
@@ -314,6 +315,23 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
     out = out - 0.5 * V * Vq[q] / Gb * B;
   }
   if (c.tot) out = out + f_tot<T>(c, k, d, i, V, Vq, Gb, get);
+  if (c.dfl) {
+    /* Divergent-flow term (Sect. 3.1.3, cited there to Smolarkiewicz & Margolin 1998; the
+     * formula is not reproduced in the paper).  Reading, from the donor-cell scheme's
+     * first-order error -dt/2 G psi_tt, whose flux part -dt/2 (V/G) psi div(V) is not
+     * cancelled by the terms above when the advector is divergent:
+     *   - 1/4 V (div_i + div_{i+e_d}) / Gb,  div_j = sum_q (V_q at face j+1/2 - at face j-1/2),
+     * with the advector of the previous pass (1D: -1/4 V_{i+1/2} (V_{i+3/2} - V_{i-1/2})). */
+    auto div = [&](const Cell& y) {
+      T s = 0.0;
+      for (int q = 0; q < g.nd; ++q) {
+        const int Q = c.adv(k - 1, q);
+        s = s + (get(Q, lin(g, y)) - get(Q, lin(g, sh(g, y, q, -1))));
+      }
+      return s;
+    };
+    out = out - 0.25 * V * (div(x) + div(sh(g, x, d, +1))) / Gb;
+  }
   return out;
 }
 
@@ -431,6 +449,7 @@ int setup(Ctx& c, int nd, const int64_t* shape, const double* const* gc, const d
   if (nd < 1 || nd > 3 || !shape || n_iters < 1) return 1;
   if ((opts & O_IGA) && n_iters != 2) return 1;
   if ((opts & O_IGA) && (opts & O_ABS)) return 1;  /* two alternative variable-sign options */
+  if ((opts & O_IGA) && (opts & O_DFL)) return 1;  /* the divergent-flow flux scales with psi */
   if ((opts & O_RHS_A) && (opts & O_RHS_B)) return 1;
   if (((opts & (O_RHS_A | O_RHS_B)) != 0) != (r != nullptr)) return 1;
   if (((opts & O_NUG) != 0) != (g != nullptr)) return 1;
@@ -449,6 +468,7 @@ int setup(Ctx& c, int nd, const int64_t* shape, const double* const* gc, const d
   c.tot = opts & O_TOT;
   c.iga = opts & O_IGA;
   c.abs = opts & O_ABS;
+  c.dfl = opts & O_DFL;
   c.kahan = opts & O_KAHAN;
   c.rhs_a = opts & O_RHS_A;
   c.rhs_b = opts & O_RHS_B;

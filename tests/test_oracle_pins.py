@@ -35,6 +35,8 @@ OPTION_SETS = {
     "kahan_fct": (2, oracle.KAHAN | oracle.FCT),
     "abs_fct": (2, oracle.ABS | oracle.FCT),
     "abs_tot3": (3, oracle.ABS | oracle.TOT),
+    "dfl": (2, oracle.DFL),
+    "dfl_it3_fct": (3, oracle.DFL | oracle.FCT),
 }
 
 
@@ -437,3 +439,99 @@ def test_abs_depends_on_the_background_and_excludes_iga():
     assert np.abs(st(a + 3.0) - (st(a) + 3.0)).max() > 1e-6
     with pytest.raises(ValueError):
         oracle.step(a, gc, n_iters=2, opts=oracle.ABS | oracle.IGA)
+
+
+# ----------------------------------------------------------------------------- divergent-flow option (dfl)
+
+def _gl_means(f, n, pts=5):
+    """Cell means on [0, 1) with n cells by Gauss-Legendre quadrature."""
+    gx, gw = np.polynomial.legendre.leggauss(pts)
+    dx = 1.0 / n
+    q = ((np.arange(n) + 0.5) * dx)[:, None] + 0.5 * dx * gx[None, :]
+    return q, gw, (f(q) * gw[None, :]).sum(1) / 2.0
+
+
+def _foot(vel, x, t):
+    """Foot at time 0 of the characteristic dx/dt = vel(x) through x at time t (steady flow)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    sol = integrate.solve_ivp(lambda s, X: -vel(X), (0.0, t), x.ravel(), rtol=1e-12, atol=1e-13, method="DOP853")
+    return sol.y[:, -1].reshape(x.shape)
+
+
+def _divergent_1d_error(n, opts, T=0.3, a=0.5):
+    """psi_t + (u psi)_x = 0 with the steady divergent u = 1 + a sin(2 pi x): u psi is constant
+    along characteristics, so the exact cell means follow from the characteristics' feet."""
+    u = lambda x: 1.0 + a * np.sin(2 * np.pi * x)
+    p0 = lambda x: 2.0 + np.sin(2 * np.pi * x)
+    dx = 1.0 / n
+    steps = int(np.ceil(T / (0.5 * dx / (1.0 + a))))
+    dt = T / steps
+    q, gw, psi = _gl_means(p0, n)
+    X0 = _foot(u, q, T)
+    ref = ((u(X0) * p0(X0) / u(q)) * gw[None, :]).sum(1) / 2.0
+    gc = [u((np.arange(n) + 1) * dx) * dt / dx]
+    out = oracle.step(psi, gc, n_iters=2, opts=opts, n_steps=steps)
+    return np.sqrt(np.mean((out - ref) ** 2))
+
+
+def test_dfl_restores_second_order_in_divergent_1d_flow():
+    """Sect. 3.1.3: in a divergent flow the basic pseudo-velocity leaves the donor-cell scheme's
+    -dt/2 (V/G) psi div(V) error uncancelled (first order); the divergent-flow term removes it
+    (second order).  A dropped term, a wrong sign or factor leaves first order."""
+    ns = (64, 128, 256, 512)
+    for opts, lo, hi in ((0, 0.9, 1.2), (oracle.DFL, 1.9, 2.1)):
+        errs = [_divergent_1d_error(n, opts) for n in ns]
+        order = math.log2(errs[-2] / errs[-1])
+        assert lo <= order <= hi, (opts, errs)
+
+
+def test_dfl_restores_second_order_in_divergent_2d_flow():
+    """The multi-D form: the divergence at a face is the mean of its two cells' divergences over
+    every dimension.  Separable steady flow u(x), v(y) (both divergent): u v psi is carried
+    unchanged along characteristics, so the exact cell means follow from the feet."""
+    a, b, T = 0.5, 0.4, 0.3
+    u = lambda x: 1.0 + a * np.sin(2 * np.pi * x)
+    v = lambda y: 0.7 * (1.0 + b * np.cos(2 * np.pi * y))
+    p0 = lambda x, y: 2.0 + np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    gx, gw = np.polynomial.legendre.leggauss(4)
+
+    def err(n, opts):
+        dx = 1.0 / n
+        steps = int(np.ceil(T / (0.25 * dx / 1.5)))
+        dt = T / steps
+        q = ((np.arange(n) + 0.5) * dx)[:, None] + 0.5 * dx * gx[None, :]
+        Y, X = q[:, None, :, None], q[None, :, None, :]  # arrays [y, x]
+        W = gw[:, None] * gw[None, :] / 4.0
+        psi = (p0(X, Y) * W).sum((2, 3))
+        X0, Y0 = _foot(u, q, T), _foot(v, q, T)
+        ex = p0(X0[None, :, None, :], Y0[:, None, :, None]) * u(X0)[None, :, None, :] * v(Y0)[:, None, :, None] \
+            / (u(X) * v(Y))
+        ref = (ex * W).sum((2, 3))
+        f = (np.arange(n) + 1) * dx
+        g0 = np.broadcast_to((v(f) * dt / dx)[:, None], (n, n)).copy()
+        g1 = np.broadcast_to((u(f) * dt / dx)[None, :], (n, n)).copy()
+        out = oracle.step(psi, [g0, g1], n_iters=2, opts=opts, n_steps=steps)
+        return np.sqrt(np.mean((out - ref) ** 2))
+
+    errs = [err(n, oracle.DFL) for n in (32, 64, 128)]
+    assert math.log2(errs[-2] / errs[-1]) >= 1.85, errs
+    base = [err(n, 0) for n in (64, 128)]
+    assert math.log2(base[0] / base[1]) <= 1.4, base
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+def test_dfl_term_vanishes_for_nondivergent_flow_and_conserves(shape):
+    """For a (discretely) nondivergent advector the divergent-flow term is zero in the first
+    corrective pass (two passes: the basic result to rounding); on a divergent advector the
+    step stays in flux form and conserves the sum; it excludes the infinite gauge."""
+    rng = np.random.default_rng(31 + len(shape))
+    gc = nondivergent(shape, rng, 0.4)
+    psi = 1.0 + rng.uniform(size=shape)
+    a = oracle.step(psi, gc, n_iters=2, opts=oracle.DFL, n_steps=3)
+    b = oracle.step(psi, gc, n_iters=2, opts=0, n_steps=3)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+    div = [0.3 * rng.uniform(size=shape) for _ in shape]
+    out = oracle.step(psi, div, n_iters=3, opts=oracle.DFL | oracle.FCT, n_steps=4)
+    assert abs(out.sum() - psi.sum()) <= 1e-13 * psi.sum() * 4
+    with pytest.raises(ValueError):
+        oracle.step(psi, gc, n_iters=2, opts=oracle.DFL | oracle.IGA)
