@@ -65,9 +65,13 @@ enum {
   MPDATA_RHS_EULER_B = 64u, /* psi^{n+1} = ADV(psi^n + dt R) (Sect. 4.1) */
   MPDATA_STAGED = 128u,     /* run the one-kernel-per-sub-step path even where a fused
                                kernel covers the case (comparison and testing) */
-  MPDATA_ABS = 256u         /* variable-sign fields: |psi| in every psi-fraction of the
+  MPDATA_ABS = 256u,        /* variable-sign fields: |psi| in every psi-fraction of the
                                pseudo-velocity (Sect. 3.1.5); excludes MPDATA_IGA.  Runs on
                                the one-kernel-per-sub-step path; no reverse step */
+  MPDATA_DFL = 512u         /* divergent flow (Sect. 3.1.3): the pseudo-velocity gains
+                               -1/4 V (div_i + div_{i+e_d}) / Gb, div_j the advector's
+                               difference summed over the dimensions across cell j; excludes
+                               MPDATA_IGA.  One-kernel-per-sub-step path; no reverse step */
 };
 
 /* status codes */
@@ -89,7 +93,7 @@ enum {
  * opts: OR of MPDATA_* option bits.  cuda_stream: a cudaStream_t (NULL = legacy
  * default stream) on the current device; all work of the handle goes there.
  * Errors: EINVAL for ndims not in 1..3, n_fields < 1, a non-positive extent,
- * n_iters < 1, IGA with n_iters != 2, IGA with ABS, both RHS bits; ENOMEM; ECUDA.
+ * n_iters < 1, IGA with n_iters != 2, IGA with ABS or DFL, both RHS bits; ENOMEM; ECUDA.
  */
 int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype,
                   int n_iters, uint32_t opts, void* cuda_stream);
@@ -130,8 +134,8 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
  * conserved up to the rounding of the lo additions, and the state carries about twice
  * the FP32 precision across steps.  Start from lo = 0 for an FP32 initial field (or
  * lo = x - (float)x for an FP64 one).
- * Requirements: an FP32 handle with one 2D field, n_iters = 2, without MPDATA_TOT or
- * MPDATA_STAGED (MPDATA_EUNSUPPORTED otherwise); lo_in / lo_out aliased exactly when
+ * Requirements: an FP32 handle with one 2D field, n_iters = 2, without MPDATA_TOT,
+ * MPDATA_ABS, MPDATA_DFL or MPDATA_STAGED (MPDATA_EUNSUPPORTED otherwise); lo_in / lo_out aliased exactly when
  * psi_in / psi_out are (EINVAL otherwise).  The warp-march kernel runs it (the handle's
  * MPDATA_TUNE_TILE_ROWS applies unless MPDATA_TUNE_KERNEL selects the band march).  The
  * first call allocates a second ping-pong buffer (ENOMEM).  Other errors as mpdata_advance.
@@ -150,7 +154,7 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
  * passes the derivative of its first extremal candidate.  The step is
  * recomputed internally, as mpdata_adjoint_record records it; the adjoint scratch
  * is allocated on first use and kept with the handle.  Errors: EINVAL;
- * EUNSUPPORTED for batched handles, for the third-order and abs options, for source terms
+ * EUNSUPPORTED for batched handles, for the third-order, abs and dfl options, for source terms
  * and for n_iters > 4; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,

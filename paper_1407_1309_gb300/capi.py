@@ -16,7 +16,7 @@ from . import build as _build
 
 # element types, option bits and status codes (include/mpdata.h)
 F32, F64 = 0, 1
-FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B, STAGED, ABS = 1, 2, 4, 8, 16, 32, 64, 128, 256
+FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B, STAGED, ABS, DFL = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
 OK, EINVAL, EUNSUPPORTED, ECUDA, ECOURANT, ETIMEOUT, ESTOPPED, ENOMEM = range(8)
 
 EXPORTED = (

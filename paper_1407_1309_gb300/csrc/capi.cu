@@ -177,9 +177,9 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
   *out = nullptr;
   if (ndims < 1 || ndims > 3 || n_fields < 1 || n_iters < 1) return MPDATA_EINVAL;
   if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return MPDATA_EINVAL;
-  if (opts & ~511u) return MPDATA_EINVAL;
+  if (opts & ~1023u) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && n_iters != 2) return MPDATA_EINVAL;
-  if ((opts & MPDATA_IGA) && (opts & MPDATA_ABS)) return MPDATA_EINVAL;
+  if ((opts & MPDATA_IGA) && (opts & (MPDATA_ABS | MPDATA_DFL))) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
   for (long long i = 0; i < static_cast<long long>(n_fields) * ndims; ++i)
     if (shapes[i] < 1 || shapes[i] > (int64_t(1) << 30)) return MPDATA_EINVAL;
@@ -304,7 +304,8 @@ int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, con
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
                         void* const* gc_bar) {
   if (!h || !psi_bar) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS)) return MPDATA_EUNSUPPORTED;
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+    return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
   if (!aligned(psi_bar, h->esize)) return MPDATA_EINVAL;
@@ -323,7 +324,8 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
 // Checks shared by the reverse-step entry points: options, fields, a single-field handle.
 static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
   if (!h) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS)) return MPDATA_EUNSUPPORTED;
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+    return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
   if (h->n_fields != 1) return MPDATA_EUNSUPPORTED;
@@ -333,7 +335,8 @@ static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, 
 
 int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes) {
   if (!h || !bytes) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS)) return MPDATA_EUNSUPPORTED;
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+    return MPDATA_EUNSUPPORTED;
   if (h->n_fields != 1 || h->n_iters > 4) return MPDATA_EUNSUPPORTED;
   *bytes = mpd::adjoint_tape_bytes(h, h->esize);
   return MPDATA_OK;

@@ -34,6 +34,7 @@ inline Grid make_grid(int nd, const int64_t* shape) {
 struct Opts {
   bool fct, tot, iga, nug, kahan, rhs_a, rhs_b, staged;
   bool abs;  // |psi| in the psi-fractions of the pseudo-velocity (variable-sign fields)
+  bool dfl;  // divergent-flow term of the pseudo-velocity
   int n_iters;
   int tile_rows;  // fused 2D kernels: rows per warp tile / per block band (0 = automatic)
   int kernel;     // fused 2D kernel family: 0 automatic, 1 warp march, 2 band march
@@ -50,6 +51,7 @@ inline Opts make_opts(uint32_t o, int n_iters) {
   p.rhs_b = o & MPDATA_RHS_EULER_B;
   p.staged = o & MPDATA_STAGED;
   p.abs = o & MPDATA_ABS;
+  p.dfl = o & MPDATA_DFL;
   p.n_iters = n_iters;
   p.tile_rows = 0;
   p.kernel = 0;

@@ -77,9 +77,9 @@ extern "C" int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, i
   if (!shape || !psi_in || !psi_out || !gc) return MPDATA_EINVAL;
   if (ndims < 1 || ndims > 3 || n_iters < 1) return MPDATA_EINVAL;
   if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return MPDATA_EINVAL;
-  if (opts & ~511u) return MPDATA_EINVAL;
+  if (opts & ~1023u) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && n_iters != 2) return MPDATA_EINVAL;
-  if ((opts & MPDATA_IGA) && (opts & MPDATA_ABS)) return MPDATA_EINVAL;
+  if ((opts & MPDATA_IGA) && (opts & (MPDATA_ABS | MPDATA_DFL))) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
   const bool nug = opts & MPDATA_NUG;
   const bool rhs = opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B);

@@ -183,7 +183,7 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
 // values it uses (over their count under infinite gauge).
 template <typename T, int ND>
 __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vscale,
-                           const T* __restrict__ G, bool iga, bool tot, bool abs_psi, Out3<T> Vout) {
+                           const T* __restrict__ G, bool iga, bool tot, bool abs_psi, bool dfl, Out3<T> Vout) {
   // variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
   auto ps = [&](long long j) { const T v = psi[j]; return abs_psi ? absv(v) : v; };
   FOR_CELLS(g) {
@@ -245,6 +245,19 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
         const T D3 = iga ? n3 * T(0.125) : fracg(n3, (pr[0] + pr[1]) + (pr[2] + pr[3]));
         out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] * (rGb * rGb) * D3;
       }
+    }
+    if (dfl) {
+      // divergent-flow term (Sect. 3.1.3): -1/4 V (div_i + div_{i+e_d}) / Gb, div_j the sum over
+      // the dimensions of the advector's difference across cell j
+      T div = T(0);
+#pragma unroll
+      for (int q = 0; q < ND; ++q) {
+        const T* Q = Vin.p[q];
+        const long long jm = nb.at(q, -1);                                 // i - e_q
+        const long long pm = q == d ? i : nb.at2(d, +1, q, -1);            // i + e_d - e_q
+        div = div + ((Q[i] * vscale - Q[jm] * vscale) + (Q[ip] * vscale - Q[pm] * vscale));
+      }
+      out = out - T(0.25) * V * div * rGb;
     }
     Vout.p[d][i] = out;
   }
@@ -1116,10 +1129,11 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   for (int k = 2; k <= K; ++k) {
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
-    if (ND == 3) {
+    if (ND == 3 && !o.dfl) {
       launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk, st);
     } else {
-      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk);
+      k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, o.dfl,
+                                                         vk);
     }
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
     // FP32: factors, limiter and donor pass in one z-march (it limits each face from both sides
@@ -1175,7 +1189,7 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
       launch_antidiff3<T>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs,
-                                                         vk);
+                                                         o.dfl, vk);
     }
     In3<T> vu{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
     if (o.fct) {
@@ -1244,7 +1258,7 @@ template StagedScratch<double> carve_staged<double>(void*, long long);
 template <typename T>
 int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc, const T* G, const T* R, T dt,
             int n_steps, cudaStream_t st) {
-  if (g.nd != 1 || o.n_iters > 64 || o.abs) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 1 || o.n_iters > 64 || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
   const size_t smem = steps1d_smem<T>(g.N);
   static int max_smem = -1;
   if (max_smem < 0) {

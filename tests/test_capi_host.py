@@ -42,7 +42,8 @@ def test_status_strings_and_version():
     dict(ndims=2, shapes=[(4, -3)], dtype=0, n_iters=2, opts=0),
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=3, opts=capi.IGA),
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.RHS_EULER_A | capi.RHS_EULER_B),
-    dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=1 << 9),
+    dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=1 << 10),
+    dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.DFL | capi.IGA),
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.ABS | capi.IGA),
 ])
 def test_create_rejects_invalid_arguments(args):

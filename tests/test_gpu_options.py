@@ -1,7 +1,8 @@
 """The variable-sign option abs (Sect. 3.1.5: |psi| in every psi-fraction of the
-pseudo-velocity) on the GPU against the oracle: 1D, 2D and 3D, with the limiter and the
-third-order terms, FP64 and FP32, single and batched handles; on a positive field it is the
-basic scheme bit for bit; it has no reverse step."""
+pseudo-velocity) and the divergent-flow option dfl (Sect. 3.1.3) on the GPU against the
+oracle: 1D, 2D and 3D, with the limiter and the third-order terms, FP64 and FP32, single and
+batched handles; on a positive field abs is the basic scheme bit for bit; neither has a
+reverse step."""
 import numpy as np
 import pytest
 import torch
@@ -103,4 +104,53 @@ def test_abs_has_no_reverse_step_and_excludes_iga():
     with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.ABS | capi.FCT) as m:
         assert capi.mpdata_adjoint_step(m.h, z[0], z[:2], None, z[2], raw=True) == capi.EUNSUPPORTED
     rc, h = capi.mpdata_create(2, [shape], capi.F64, 2, capi.ABS | capi.IGA, raw=True)
+    assert rc == capi.EINVAL and not h
+
+
+# ----------------------------------------------------------------------------- divergent-flow option
+
+DFL_CASES = {"dfl": (2, capi.DFL), "dfl_fct": (2, capi.DFL | capi.FCT), "dfl_it3_fct": (3, capi.DFL | capi.FCT),
+             "dfl_tot3": (3, capi.DFL | capi.TOT), "dfl_abs_fct": (2, capi.DFL | capi.ABS | capi.FCT)}
+
+
+def divergent(shape, seed):
+    rng = np.random.default_rng(seed)
+    psi = smooth_positive(shape, rng) - (0.0 if seed % 2 else 1.2)
+    gc = [0.3 * rng.uniform(-1, 1, size=shape) / len(shape) for _ in shape]  # divergent everywhere
+    return psi, gc
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("name", sorted(DFL_CASES))
+def test_dfl_fp64_matches_oracle(shape, name):
+    n_iters, opts = DFL_CASES[name]
+    psi, gc = divergent(shape, 2 * len(shape) + n_iters)
+    if not opts & capi.ABS:
+        psi = np.abs(psi) + 0.5
+    ref = oracle.step(psi, gc, n_iters=n_iters, opts=int(opts), n_steps=4)
+    out = run(psi, gc, n_iters, opts, torch.float64, 4)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+def test_dfl_fp32_and_nonunit_g_close_to_oracle(shape):
+    psi, gc = divergent(shape, 9)
+    r = lambda a: a.astype(np.float32).astype(np.float64)
+    G = r(1.0 + 0.2 * np.random.default_rng(5).uniform(size=shape))
+    psi, gc = r(psi), [r(v) for v in gc]
+    opts = capi.DFL | capi.FCT
+    ref = oracle.step(psi, gc, g=G, n_iters=2, opts=int(opts), n_steps=4)
+    out = run(psi, gc, 2, opts, torch.float32, 4, G=G)
+    assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
+    ref64 = oracle.step(psi, gc, g=G, n_iters=3, opts=int(opts), n_steps=4)
+    out64 = run(psi, gc, 3, opts, torch.float64, 4, G=G)
+    assert np.abs(out64 - ref64).max() <= 1e-12 * np.abs(ref64).max()
+
+
+def test_dfl_has_no_reverse_step_and_excludes_iga():
+    shape = (16, 16)
+    z = [torch.zeros(shape, dtype=torch.float64, device=DEV) for _ in range(3)]
+    with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.DFL | capi.FCT) as m:
+        assert capi.mpdata_adjoint_step(m.h, z[0], z[:2], None, z[2], raw=True) == capi.EUNSUPPORTED
+    rc, h = capi.mpdata_create(2, [shape], capi.F64, 2, capi.DFL | capi.IGA, raw=True)
     assert rc == capi.EINVAL and not h
