@@ -398,6 +398,7 @@ def run_ours(args):
             extras["staged_path"] = {"value": round(cells * ks / st / 1e9, 3), "unit": UNIT, "steps": ks,
                                      "kernels_per_step": 6}
         extras["abs_variable_sign"] = bench_abs(psi_np, gc_np, dtype, dev, stream, flush, min(args.steps, 300))
+        extras["dfl_divergent_flow"] = bench_dfl(n, dtype, dev, stream, flush, min(args.steps, 300))
         out["e2e"] = run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
         def gpu_steps(k):  # this build's step from the same FP32 input, for the oracle leg's comparison
             with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev) as mm:
@@ -473,6 +474,51 @@ def bench_abs(psi_np, gc_np, dtype, dev, stream, flush, steps):
         ref = q64.cpu().numpy()
     res["err_vs_fp64_gpu_10_steps"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                                        "max_abs": float(np.abs(got - ref).max())}
+    return res
+
+
+def bench_dfl(n, dtype, dev, stream, flush, steps):
+    """The divergent-flow option (dfl, Sect. 3.1.3) on an n^2 field in the steady separable
+    divergent flow u = 1 + 0.5 sin(2 pi x), v = 0.7 (1 + 0.4 cos(2 pi y)) at max |C| 0.25 (the
+    flow of its convergence pin), two passes, on the staged kernels: each step timed between
+    CUDA events after an L2 flush, and 10 steps against FP64 on the GPU."""
+    import numpy as np
+    import torch
+
+    from paper_1407_1309_gb300 import capi
+    from paper_1407_1309_gb300.solver import Mpdata
+    x = (np.arange(n) + 0.5) / n
+    f = (np.arange(n) + 1.0) / n
+    psi = 2.0 + np.sin(2 * np.pi * x)[None, :] * np.cos(2 * np.pi * x)[:, None]
+    u, v = 1.0 + 0.5 * np.sin(2 * np.pi * f), 0.7 * (1.0 + 0.4 * np.cos(2 * np.pi * f))
+    c = 0.25 / max(u.max(), v.max())
+    gc_np = [np.broadcast_to((c * v)[:, None], (n, n)).copy(), np.broadcast_to((c * u)[None, :], (n, n)).copy()]
+    opts = capi.DFL
+    res = {"workload": f"2d_divergent_separable_{n}x{n}_dfl_n_iters2", "path": "staged kernels"}
+    outs = {}
+    for dt in (dtype, torch.float64):
+        with Mpdata((n, n), dtype=dt, n_iters=2, opts=opts, device=dev) as m:
+            a = torch.tensor(psi, dtype=dt, device=dev)
+            b = torch.empty_like(a)
+            gc = [torch.tensor(g, dtype=dt, device=dev) for g in gc_np]
+            m.advance(a, b, gc, n_steps=10)
+            outs[dt] = b.double().cpu().numpy()
+            if dt == dtype:
+                evs = []
+                for _ in range(steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    m.advance(a, b, gc)
+                    e1.record(stream)
+                    evs.append((e0, e1))
+                    a, b = b, a
+                torch.cuda.synchronize(dev)
+                secs = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
+                res.update({"value": round(n * n * steps / secs / 1e9, 3), "unit": UNIT, "steps": steps})
+    got, ref = outs[dtype], outs[torch.float64]
+    res["err_vs_fp64_gpu_10_steps"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                                       "rel_mass_drift": float(abs(got.sum() - ref.sum()) / abs(ref.sum()))}
     return res
 
 
