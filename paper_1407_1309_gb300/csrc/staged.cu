@@ -294,10 +294,10 @@ constexpr size_t antidiff3_smem() {
   return sizeof(T) * (kA3P * kPw * kPh + (3 + 1) * kA3V * kVw * kVh);
 }
 
-template <typename T>
+template <typename T, bool ABS>
 __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __restrict__ psi, In3<T> Vin,
                                                          T vscale, const T* __restrict__ G, bool iga, bool tot,
-                                                         bool abs_psi, Out3<T> Vout) {
+                                                         Out3<T> Vout) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int nP = kPw * kPh, nV = kVw * kVh;
   T* const sP = reinterpret_cast<T*>(smem_raw);  // [kA3P][nP]
@@ -396,10 +396,11 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
       const T* vy[2] = {Vp(1, z) + cV, Vp(1, z + 1) + cV};      // y component, planes z, z+1
       const T* vx[2] = {Vp(2, z) + cV, Vp(2, z + 1) + cV};      // x component, planes z, z+1
       const T* gz[2] = {Gp(z) + cV, Gp(z + 1) + cV};
-      // variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
+      // ABS, the variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
       auto P = [&](int dz, int dy, int dx) {
         const T v = pz[dz + 1][dy * kPw + dx];
-        return abs_psi ? absv(v) : v;
+        if constexpr (ABS) return absv(v);
+        else return v;
       };
       auto Q = [&](int q, int dz, int dy, int dx) {
         return q == 0 ? vz[dz + 1][dy * kVw + dx] : (q == 1 ? vy[dz][dy * kVw + dx] : vx[dz][dy * kVw + dx]);
@@ -1056,18 +1057,23 @@ __global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps,
 template <typename T>
 size_t steps1d_smem(long long n) { return static_cast<size_t>(kSteps1dArrays) * static_cast<size_t>(n) * sizeof(T); }
 
-template <typename T>
-void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, bool abs_psi,
-                      Out3<T> out,
-                      cudaStream_t st) {
+template <typename T, bool ABS>
+void launch_antidiff3_t(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, Out3<T> out,
+                        cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_antidiff3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_antidiff3<T, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(antidiff3_smem<T>()));
     attr = true;
   }
-  k_antidiff3<T><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, abs_psi,
-                                                                                     out);
+  k_antidiff3<T, ABS><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, out);
+}
+
+template <typename T>
+void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, bool abs_psi,
+                      Out3<T> out, cudaStream_t st) {
+  if (abs_psi) launch_antidiff3_t<T, true>(g, psi, v, vscale, G, iga, tot, out, st);
+  else launch_antidiff3_t<T, false>(g, psi, v, vscale, G, iga, tot, out, st);
 }
 
 template <typename T>
