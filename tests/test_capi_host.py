@@ -59,3 +59,17 @@ def test_null_handle_is_rejected():
     assert lib.mpdata_sync(None) == capi.EINVAL
     out = ctypes.c_void_p()
     assert lib.mpdata_create(None, 2, 1, None, 0, 2, 0, None) == capi.EINVAL
+
+
+def test_python_and_oracle_constants_match_the_header():
+    """The option bits, element types, status codes and tuning knobs the binding (and the
+    oracle, for its options) use are the values include/mpdata.h declares."""
+    import oracle
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "mpdata.h")).read()
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bMPDATA_([A-Z0-9_]+)\s*=\s*(\d+)u?\b", hdr)}
+    for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "STAGED", "ABS", "DFL",
+                 "F32", "F64", "OK", "EINVAL", "EUNSUPPORTED", "ECUDA", "ECOURANT", "ETIMEOUT", "ESTOPPED", "ENOMEM",
+                 "TUNE_TILE_ROWS", "TUNE_KERNEL"):
+        assert getattr(capi, name) == enums[name], name
+    for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "ABS", "DFL"):
+        assert getattr(oracle, name) == enums[name], name
