@@ -19,7 +19,8 @@
  *   psi0 = psi (+ dt R if euler_b)
  *   psi1 = donor(psi0, GC)                                   Eqs. 4-5
  *   for k = 2..n_iters:
- *     V^k    = antidiffusive advector from V^{k-1}, psi^{k-1}  Eq. 6 (+ multi-D, tot)
+ *     V^k    = antidiffusive advector from V^{k-1}, psi^{k-1}  Eq. 6 (+ multi-D, tot, dfl;
+ *              |psi| in its psi-fractions with abs)
  *     V^k    = FCT-limited V^k (if fct)                      Sect. 3.1.4
  *     psi^k  = donor(psi^{k-1}, V^k)                         Eqs. 4-5
  *   psi^{n+1} = psi^{n_iters} (+ dt R if euler_a)
