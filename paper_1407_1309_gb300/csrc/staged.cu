@@ -179,8 +179,10 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
 // multi-D cross terms, Sect. 3.1.1, and the third-order terms, Sect. 3.1.2):
 //   (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q
 //   + tot: Gb(3C|C| - 2C^3 - C)/3 D_dd + sum_q Gb|C|C_q(1 - 2|C|) D_dq - (2/3) Gb C C_q1 C_q2 D_q1q2
+//   + dfl: -1/4 V (div_i + div_{i+e_d}) / Gb       (divergent flow, Sect. 3.1.3)
 // with C = V/Gb, C_q = Vq/Gb; each psi ratio is a difference over the sum of the psi
-// values it uses (over their count under infinite gauge).
+// values it uses (over their count under infinite gauge; of their magnitudes with abs_psi,
+// Sect. 3.1.5).
 template <typename T, int ND>
 __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vscale,
                            const T* __restrict__ G, bool iga, bool tot, bool abs_psi, bool dfl, Out3<T> Vout) {
