@@ -9,9 +9,12 @@ accumulating dL/dGC over all steps.  When one segment's tapes fit in device
 memory (`tape_budget`), the recomputation records every step's tape
 (mpdata_adjoint_record: states and intermediates in one forward sweep) and the
 walk back runs only the reverse sweeps (mpdata_adjoint_replay); otherwise each
-step's tape is recomputed inside mpdata_adjoint_step.  The recomputed states then
-come from the staged kernels, which round differently from the fused forward:
-the gradient is that of the staged trajectory from each checkpoint.  Memory is
+step's tape is recomputed inside mpdata_adjoint_step.  Where the tape has a fused
+form (2D, two passes, FCT or none, no other option) the recording runs the forward's
+own fused kernel with tape stores, so the recomputed states equal the forward's bit
+for bit; in the other cases they come from the staged kernels, which round
+differently from the fused forward, and the gradient is that of the staged
+trajectory from each checkpoint.  Memory is
 one field per checkpoint plus one segment of states (and tapes).  With
 use_graphs (default) the work of one segment is captured once as a CUDA graph
 on static buffers and replayed per segment, so the host issues one replay per

@@ -297,6 +297,23 @@ def mpdata_step_noalloc(ndims, shape, dtype, n_iters, opts, psi_in, psi_out, gc,
     """One step of one field without a handle and without any device allocation (the scratch is a
     static device array inside the library); for callers that may not allocate device memory.
     Returns the status code when raw=True, else raises on error."""
+    shape = tuple(int(v) for v in shape)
+    if int(ndims) != len(shape) or len(gc) != len(shape):
+        raise ValueError("mpdata_step_noalloc: ndims, len(shape) and len(gc) must agree")
+    n = 1
+    for v in shape:
+        n *= v
+    want = {F32: "torch.float32", F64: "torch.float64"}.get(int(dtype))
+    for name, x in [("psi_in", psi_in), ("psi_out", psi_out), ("g", g), ("r", r)] + \
+            [(f"gc[{d}]", v) for d, v in enumerate(gc)]:
+        if x is None or isinstance(x, int):
+            continue  # NULL, or a raw address the caller vouches for
+        if not getattr(x, "is_cuda", False) or not x.is_contiguous():
+            raise ValueError(f"mpdata_step_noalloc: {name} must be a contiguous CUDA tensor")
+        if want is not None and str(x.dtype) != want:
+            raise ValueError(f"mpdata_step_noalloc: {name} has dtype {x.dtype}, expected {want}")
+        if x.numel() != n:
+            raise ValueError(f"mpdata_step_noalloc: {name} has {x.numel()} elements, expected {n}")
     lib = load()
     fn = lib.mpdata_step_noalloc
     fn.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int, ctypes.c_uint32,

@@ -435,16 +435,15 @@ template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN, bool TAP
 void launch_band(BandParams<T> p, int tile_rows, cudaStream_t st) {
   constexpr int W = kBandWarps;
   auto kern = k_band2d<T, NC, W, FCT, NUG, IGA, KAHAN, TAPE>;
-  static int slots = 0;  // blocks resident on the whole GPU at the largest ring layout
-  if (slots == 0) {
+  static PerDevice<int> slots_of;  // blocks resident on the whole GPU at the largest ring layout
+  const int slots = slots_of.get([&](int dev) {
     const size_t most = band_smem<T>(5, FCT);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(most));
-    int per_sm = 0, dev = 0, sms = 0;
+    int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W * 32, band_smem<T>(3 + (NUG ? 1 : 0), FCT));
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    slots = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  });
   if (tile_rows > 0) {
     p.H = tile_rows;
   } else {  // one band per resident block: as few, tall bands as fill the GPU once

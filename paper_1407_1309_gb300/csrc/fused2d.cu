@@ -485,12 +485,11 @@ void launch(const F2Params<T>& p, cudaStream_t st) {
   const long long warps = static_cast<long long>(p.strips) * p.rowtiles;
   const unsigned blocks = static_cast<unsigned>((warps + kWarps - 1) / kWarps);
   const size_t smem = static_cast<size_t>(kWarps) * kSlots * arrs<COMP>() * cols<NC>() * sizeof(T);
-  static bool attr_set = false;  // large rings exceed the default 48 KB of dynamic shared memory
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    attr_set = true;
-  }
+  static PerDevice<bool> attr;  // large rings exceed the default 48 KB of dynamic shared memory
+  attr.get([&](int) {
+    return cudaFuncSetAttribute(k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) == cudaSuccess;
+  });
   k_fused2d<T, NC, FCT, NUG, IGA, KAHAN, COMP, TAPE><<<blocks, kWarps * 32, smem, st>>>(p);
 }
 
@@ -519,17 +518,16 @@ bool al(const void* q, size_t a) { return q == nullptr || (reinterpret_cast<uint
 template <typename T, int NC, bool FCT, bool NUG, bool IGA, bool KAHAN>
 void launch_b(const BatchParams<T>& b, cudaStream_t st) {
   const size_t smem = static_cast<size_t>(kWarps) * kSlots * arrs<false>() * cols<NC>() * sizeof(T);
-  static int grid = 0;  // persistent grid: every block that fits on the GPU at once
-  if (grid == 0) {
+  static PerDevice<int> grid_of;  // persistent grid: every block that fits on the GPU at once
+  const int grid = grid_of.get([&](int dev) {
     cudaFuncSetAttribute(k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(smem));
-    int per_sm = 0, dev = 0, sms = 0;
+    int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN>,
                                                   kWarps * 32, smem);
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-  }
+    return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  });
   const int need = (b.n_items + kWarps - 1) / kWarps;
   k_fused2d_batched<T, NC, FCT, NUG, IGA, KAHAN><<<need < grid ? need : grid, kWarps * 32, smem, st>>>(b);
 }

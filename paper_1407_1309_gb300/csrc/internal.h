@@ -4,11 +4,43 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "../../include/mpdata.h"
 
 namespace mpd {
+
+// A value computed once per device (a kernel's opt-in shared-memory attribute, a persistent
+// grid size): get() returns the value cached for the current device, computing it with
+// init(device) under a lock on the first call there, so threads that launch on several
+// devices each see their own device's set-up, and none launches before it is complete.
+// Devices past the 64th are not cached (init runs on every call, under the lock).
+template <typename V>
+class PerDevice {
+ public:
+  template <class F>
+  V get(F&& init) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    const bool cached = dev >= 0 && dev < 64;
+    const uint64_t bit = cached ? (uint64_t{1} << dev) : 0;
+    if (cached && (ready_.load(std::memory_order_acquire) & bit)) return val_[dev];
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!cached) return init(dev);
+    if (!(ready_.load(std::memory_order_relaxed) & bit)) {
+      val_[dev] = init(dev);
+      ready_.fetch_or(bit, std::memory_order_release);
+    }
+    return val_[dev];
+  }
+
+ private:
+  std::mutex mu_;
+  std::atomic<uint64_t> ready_{0};
+  V val_[64] = {};
+};
 
 // Grid of one field on three internal axes: dimension d of an nd-dimensional
 // field lives on axis 3 - nd + d; unused leading axes have extent 1.

@@ -1062,12 +1062,11 @@ size_t steps1d_smem(long long n) { return static_cast<size_t>(kSteps1dArrays) * 
 template <typename T, bool ABS>
 void launch_antidiff3_t(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool iga, bool tot, Out3<T> out,
                         cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_antidiff3<T, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(antidiff3_smem<T>()));
-    attr = true;
-  }
+  static PerDevice<bool> attr;
+  attr.get([](int) {
+    return cudaFuncSetAttribute(k_antidiff3<T, ABS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(antidiff3_smem<T>())) == cudaSuccess;
+  });
   k_antidiff3<T, ABS><<<march3_grid(g), dim3(kAx, kAy), antidiff3_smem<T>(), st>>>(g, psi, v, vscale, G, iga, tot, out);
 }
 
@@ -1081,22 +1080,22 @@ void launch_antidiff3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* 
 template <typename T>
 void launch_p1b3(const Grid& g, const T* psi, In3<T> v, T vscale, const T* G, bool kahan, T* p1, T* mx, T* mn,
                  cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_p1b3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p1b3_smem<T>()));
-    attr = true;
-  }
+  static PerDevice<bool> attr;
+  attr.get([](int) {
+    return cudaFuncSetAttribute(k_p1b3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(p1b3_smem<T>())) == cudaSuccess;
+  });
   k_p1b3<T><<<march3_grid(g), dim3(kAx, kAy), p1b3_smem<T>(), st>>>(g, psi, v, vscale, G, kahan, p1, mx, mn);
 }
 
 template <typename T>
 void launch_corr3(const Grid& g, const T* psi, In3<T> vu, const T* G, bool unit, bool kahan, const T* mx,
                   const T* mn, const T* R, T dt, bool post, Out3<T> lim, T* out, cudaStream_t st) {
-  static bool attr = false;  // the FP64 rings exceed the default 48 KB of dynamic shared memory
-  if (!attr) {
-    cudaFuncSetAttribute(k_corr3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(corr3_smem<T>()));
-    attr = true;
-  }
+  static PerDevice<bool> attr;  // the FP64 rings exceed the default 48 KB of dynamic shared memory
+  attr.get([](int) {
+    return cudaFuncSetAttribute(k_corr3<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(corr3_smem<T>())) == cudaSuccess;
+  });
   k_corr3<T><<<march3_grid(g), dim3(kAx, kAy), corr3_smem<T>(), st>>>(g, psi, vu, G, unit, kahan, mx, mn, R, dt,
                                                                       post, lim, out);
 }
@@ -1268,13 +1267,13 @@ int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* 
             int n_steps, cudaStream_t st) {
   if (g.nd != 1 || o.n_iters > 64 || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
   const size_t smem = steps1d_smem<T>(g.N);
-  static int max_smem = -1;
-  if (max_smem < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncSetAttribute(k_steps1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  }
+  static PerDevice<int> max_smem_of;
+  const int max_smem = max_smem_of.get([](int dev) {
+    int m = 0;
+    cudaDeviceGetAttribute(&m, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(k_steps1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    return m;
+  });
   if (smem > static_cast<size_t>(max_smem)) return MPDATA_EUNSUPPORTED;
   k_steps1d<T><<<1, kSteps1dThreads, smem, st>>>(static_cast<int>(g.N), n_steps, o, psi_in, psi_out, gc, G, R, dt);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;

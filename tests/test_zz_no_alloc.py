@@ -76,3 +76,89 @@ def test_noalloc_rejects_fields_beyond_the_static_scratch():
     assert capi.mpdata_step_noalloc(2, (ok, ok), capi.F32, 2, capi.FCT, p, out, g, raw=True) == capi.OK
     torch.cuda.synchronize()
     assert torch.equal(out, p)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("shape,n_iters,opts", [((40, 33), 1, 0), ((40, 33), 2, capi.FCT),
+                                                ((9, 8, 11), 1, 0), ((9, 8, 11), 2, capi.FCT),
+                                                ((9, 8, 11), 3, capi.TOT | capi.FCT)],
+                         ids=lambda c: str(c))
+def test_noalloc_in_place_matches_the_handle(shape, n_iters, opts, dtype):
+    """psi_in == psi_out is allowed: in place it gives what the handle path gives out of place,
+    for one pass (the result is copied out of the scratch) and for several (with the limiter)."""
+    rng = np.random.default_rng(7 + n_iters)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
+    gc = [t(v) for v in nondivergent(shape, rng, 0.35)]
+    psi = t(smooth_positive(shape, rng))
+    dcode = capi.F32 if dtype == torch.float32 else capi.F64
+    with Mpdata(shape, dtype=dtype, n_iters=n_iters, opts=opts) as m:
+        ref = torch.empty_like(psi)
+        m.advance(psi, ref, gc, n_steps=2)
+    p = psi.clone()
+    for _ in range(2):
+        capi.mpdata_step_noalloc(len(shape), shape, dcode, n_iters, opts, p, p, gc,
+                                 stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert close(p, ref, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+@pytest.mark.parametrize("rhs", [capi.RHS_EULER_A, capi.RHS_EULER_B], ids=["euler_a", "euler_b"])
+@pytest.mark.parametrize("inplace", [False, True], ids=["out_of_place", "in_place"])
+def test_noalloc_with_g_and_sources(rhs, inplace, dtype):
+    """Non-unit G and a source term (both Euler schemes of Sect. 4.1), in and out of place."""
+    shape = (37, 29)
+    rng = np.random.default_rng(21)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
+    gc = [t(v) for v in nondivergent(shape, rng, 0.3)]
+    psi = t(smooth_positive(shape, rng))
+    G = t(1.0 + 0.3 * rng.uniform(size=shape))
+    R = t(rng.normal(size=shape))
+    opts = capi.FCT | capi.NUG | rhs
+    dcode = capi.F32 if dtype == torch.float32 else capi.F64
+    with Mpdata(shape, dtype=dtype, n_iters=2, opts=opts) as m:
+        ref = torch.empty_like(psi)
+        m.advance(psi, ref, gc, g=G, r=R, dt=0.25, n_steps=1)
+    out = psi.clone() if inplace else torch.empty_like(psi)
+    src = out if inplace else psi
+    capi.mpdata_step_noalloc(2, shape, dcode, 2, opts, src, out, gc, g=G, r=R, dt=0.25,
+                             stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert close(out, ref, dtype)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The reason the entry point exists: after a first call (module loading may allocate), further
+    calls change neither the device's free memory nor torch's allocator."""
+    shape = (64, 48, 20)
+    rng = np.random.default_rng(3)
+    dev = torch.device("cuda")
+    gc = [torch.tensor(v, dtype=torch.float32, device=dev) for v in nondivergent(shape, rng, 0.3)]
+    psi = torch.tensor(smooth_positive(shape, rng), dtype=torch.float32, device=dev)
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    opts = capi.TOT | capi.FCT
+    capi.mpdata_step_noalloc(3, shape, capi.F32, 3, opts, psi, out, gc, stream=stream)
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(5):
+        capi.mpdata_step_noalloc(3, shape, capi.F32, 3, opts, out, out, gc, stream=stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
+def test_noalloc_wrapper_rejects_inconsistent_arguments():
+    dev = torch.device("cuda")
+    psi = torch.ones((8, 8), device=dev)
+    gc = [torch.zeros_like(psi), torch.zeros_like(psi)]
+    with pytest.raises(ValueError):
+        capi.mpdata_step_noalloc(3, (8, 8), capi.F32, 2, 0, psi, psi, gc)
+    with pytest.raises(ValueError):
+        capi.mpdata_step_noalloc(2, (8, 8), capi.F32, 2, 0, psi, psi, gc[:1])
+    with pytest.raises(ValueError):
+        capi.mpdata_step_noalloc(2, (8, 8), capi.F64, 2, 0, psi, psi, gc)
+    with pytest.raises(ValueError):
+        capi.mpdata_step_noalloc(2, (8, 9), capi.F32, 2, 0, psi, psi, gc)
