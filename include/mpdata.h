@@ -286,6 +286,17 @@ int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, int n_iters,
 int mpdata_selftest_division(const double* n, const double* d, double* q, int64_t count,
                              void* cuda_stream);
 
+/*
+ * Diagnostic (no counterpart in the paper): the GPU's fused multiply-add issue rate, the
+ * denominator of the FP32 and FP64 arithmetic rooflines.  Launches one kernel on cuda_stream
+ * (8 blocks of 256 threads per SM, each thread `iters` rounds of 8 independent FMA chains in
+ * the element type dtype, MPDATA_F32 or MPDATA_F64) and stores the number of FMA lane
+ * operations it issues in *fma_count; the caller times the launch (CUDA events on the same
+ * stream).  sink: device buffer of one element of dtype, written only in a case that never
+ * happens.  EINVAL for iters < 1, a null pointer or another dtype.
+ */
+int mpdata_selftest_fma_rate(int dtype, int64_t iters, void* sink, int64_t* fma_count, void* cuda_stream);
+
 /* Static description of a status code. */
 const char* mpdata_strerror(int code);
 

@@ -23,7 +23,7 @@ EXPORTED = (
     "mpdata_create", "mpdata_step", "mpdata_advance", "mpdata_adjoint_step", "mpdata_reduce",
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
-    "mpdata_advance_compensated", "mpdata_selftest_division",
+    "mpdata_advance_compensated", "mpdata_selftest_division", "mpdata_selftest_fma_rate",
     "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay",
 )
 TUNE_TILE_ROWS = 1
@@ -67,6 +67,7 @@ def load(build_if_needed: bool = True):
             "mpdata_advance": ([P, P, P, PP, P, P, D, I, DP], I),
             "mpdata_advance_compensated": ([P, P, P, P, P, PP, P, P, D, I, DP], I),
             "mpdata_selftest_division": ([P, P, P, I64, P], I),
+            "mpdata_selftest_fma_rate": ([I, I64, P, ctypes.POINTER(I64), P], I),
             "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
             "mpdata_adjoint_tape_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
             "mpdata_adjoint_record": ([P, P, PP, P, P, P], I),
@@ -187,6 +188,15 @@ def mpdata_selftest_division(n, d, q, stream=None):
     """q = n / d elementwise with the kernels' FP64 division (device float64 tensors)."""
     _check(load().mpdata_selftest_division(_ptr(n), _ptr(d), _ptr(q), int(q.numel()), _ptr(stream)),
            "mpdata_selftest_division")
+
+
+def mpdata_selftest_fma_rate(dtype, iters, sink, stream=None):
+    """Launch the FMA-rate kernel (F32 or F64) on `stream`; returns the FMA lane operations it
+    issues.  sink: a one-element device tensor of that dtype."""
+    n = ctypes.c_int64(0)
+    _check(load().mpdata_selftest_fma_rate(int(dtype), int(iters), _ptr(sink), ctypes.byref(n), _stream_ptr(stream)),
+           "mpdata_selftest_fma_rate")
+    return n.value
 
 
 def prepare_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1):

@@ -112,6 +112,27 @@ def test_long_run_error_below_plain_fp32():
     assert err_comp <= 1e-5
 
 
+def test_one_revolution_256_against_oracle():
+    """The rotation workload at 256^2 (FCT, two passes) over one full revolution (1609 steps),
+    both FP32 paths against the FP64 oracle on the same FP32-representable input: the
+    compensated state keeps the FP32 bars (relative L2 <= 1e-5, relative mass drift <= 1e-6);
+    the plain FP32 state's errors are checked against the bars it reaches at this size."""
+    psi, gc, rev = workloads.rotation_2d(256)
+    assert rev == workloads.rotation_steps(256) == 1609
+    psi, gc = r32(psi), [r32(v) for v in gc]
+    oracle.set_threads(0)
+    ref = oracle.step(psi, gc, n_iters=2, opts=oracle.FCT, n_steps=rev)
+    m0 = psi.sum()
+    hi, lo = run_comp(psi, gc, rev, capi.FCT)
+    comp = joined(hi, lo)
+    plain = run_plain32(psi, gc, rev, capi.FCT)
+    l2 = lambda x: float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+    drift = lambda x: float(abs(x.sum() - m0) / abs(m0))
+    assert l2(comp) <= 1e-5 and drift(comp) <= 1e-6, (l2(comp), drift(comp))
+    assert l2(plain) <= 1e-5 and drift(plain) <= 1e-6, (l2(plain), drift(plain))
+    assert drift(comp) < drift(plain)
+
+
 def test_in_place_odd_steps_and_time_dependent_scale():
     shape = (96, 136)
     rng = np.random.default_rng(5)
