@@ -7,7 +7,8 @@ package smoke check and the benchmark's CPU-baseline leg use this module; the
 CUDA library never imports, links or calls it.
 
 Parity status per function (details in the header of ``mpdata_oracle.cpp``):
-every sub-step is pinned by the tests in ``tests/test_oracle_pins.py``, except
+every sub-step is pinned by the tests in ``tests/test_oracle_pins.py`` (open edges
+in ``tests/test_oracle_open.py``), except
 the multi-dimensional cross terms of the third-order option, which are pinned
 only by the convergence order on a diagonal flow.
 """
@@ -29,6 +30,7 @@ LIB = os.path.join(BUILD_DIR, "libmpdata_oracle.so")
 FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B = 1, 2, 4, 8, 16, 32, 64
 ABS = 256  # |psi| in the psi-fractions of the pseudo-velocity (variable-sign fields)
 DFL = 512  # divergent-flow term of the pseudo-velocity
+OPEN0, OPEN1, OPEN2 = 1024, 2048, 4096  # open edges along dimension 0, 1, 2 (else periodic)
 
 _lock = threading.Lock()
 _lib = None

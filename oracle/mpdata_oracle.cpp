@@ -53,6 +53,8 @@ namespace {
 /* Option bits of the oracle (the same values the library interface defines). */
 constexpr unsigned O_FCT = 1u, O_TOT = 2u, O_IGA = 4u, O_NUG = 8u, O_KAHAN = 16u,
                    O_RHS_A = 32u, O_RHS_B = 64u, O_ABS = 256u, O_DFL = 512u;
+/* open edges (Sect. 2.4, bcond::open) along dimension d: bit O_OPEN0 << d */
+constexpr unsigned O_OPEN0 = 1024u;
 
 /* ------------------------------------------------------------------ grid */
 
@@ -60,6 +62,7 @@ struct Grid {
   int nd = 1;                 /* number of dimensions, 1..3 */
   long n[3] = {1, 1, 1};      /* extents on three internal axes; leading unused axes have extent 1 */
   long N = 1;
+  bool open[3] = {false, false, false};  /* open edges on an internal axis (else periodic) */
   int ax(int d) const { return 3 - nd + d; }  /* internal axis of dimension d */
 };
 
@@ -67,10 +70,14 @@ struct Cell { long c[3]; };
 
 inline long wrapc(long c, long n) { long r = c % n; return r < 0 ? r + n : r; }
 
-/* cell x shifted by s cells along dimension d, periodic */
+/* cell x shifted by s cells along dimension d: periodic, or, with open edges (Sect. 2.4,
+ * bcond::open), clamped to the edge cell -- the halo cells beyond an open edge hold the edge
+ * value (zero gradient) */
 inline Cell sh(const Grid& g, Cell x, int d, long s) {
   int a = g.ax(d);
-  x.c[a] = wrapc(x.c[a] + s, g.n[a]);
+  long v = x.c[a] + s;
+  if (g.open[a]) x.c[a] = v < 0 ? 0 : (v > g.n[a] - 1 ? g.n[a] - 1 : v);
+  else x.c[a] = wrapc(v, g.n[a]);
   return x;
 }
 inline long lin(const Grid& g, const Cell& x) { return (x.c[0] * g.n[1] + x.c[1]) * g.n[2] + x.c[2]; }
@@ -83,6 +90,22 @@ inline Cell cell_of(const Grid& g, long i) {
   return x;
 }
 inline long nbr(const Grid& g, long i, int d, long s) { return lin(g, sh(g, cell_of(g, i), d, s)); }
+
+/* Storage index of a face of a vector field along d: the face s faces from face i+1/2 of
+ * cell i.  Periodic: n faces, wrapped.  Open edges (Sect. 2.4: a zero-divergence condition on
+ * the domain edges): the n-1 faces between the cells are interior (indices 0 .. n-2, the
+ * advector of Sect. 3.2.5 is one shorter than the field along its own dimension), and the two
+ * boundary faces -1/2 and n-1/2 take the value of the adjacent interior face, so that every
+ * vector field -- the advector and each pass's pseudo-velocity -- has zero divergence along d
+ * in the edge cells.  The entry n-1 of a component along an open dimension is never read. */
+inline long fc(const Grid& g, long i, int d, long s) {
+  Cell x = cell_of(g, i);
+  const int a = g.ax(d);
+  long f = x.c[a] + s;
+  if (g.open[a]) x.c[a] = f < 0 ? 0 : (f > g.n[a] - 2 ? g.n[a] - 2 : f);
+  else x.c[a] = wrapc(f, g.n[a]);
+  return lin(g, x);
+}
 
 /* ------------------------------------------------------------ dual numbers */
 
@@ -171,12 +194,23 @@ template <class T, class Get> T f_post(const Ctx& c, long i, Get get) {
  * units: F(L, R, V) = [V]+ L + [V]- R with V = G*C the advector.  In the
  * corrective passes of the infinite-gauge variant psi is replaced by 1 (the
  * limit of MPDATA on psi + c for c -> infinity, Sect. 3.1.5), so F = V. */
-template <class T, class Get> T f_flux(const Ctx& c, int k, int d, long i, bool limited, Get get) {
-  T V = get(limited ? c.adv(k, d) : c.id.v(k, d), i);
+template <class T, class Get> T f_flux_at(const Ctx& c, int k, int d, long i, long s, bool limited, Get get) {
+  T V = get(limited ? c.adv(k, d) : c.id.v(k, d), fc(c.g, i, d, s));
   if (k >= 2 && c.iga) return V;
-  T L = get(c.id.psi(k - 1), i);
-  T R = get(c.id.psi(k - 1), nbr(c.g, i, d, +1));
+  T L = get(c.id.psi(k - 1), nbr(c.g, i, d, s));
+  T R = get(c.id.psi(k - 1), nbr(c.g, i, d, s + 1));
   return pos(V) * L + neg(V) * R;
+}
+template <class T, class Get> T f_flux(const Ctx& c, int k, int d, long i, bool limited, Get get) {
+  return f_flux_at<T>(c, k, d, i, 0, limited, get);
+}
+/* Flux through face i-1/2 along d: the stored flux of face (i-1)+1/2, except at an open
+ * left edge, where face -1/2 is a boundary face (no storage): its flux is formed here, with
+ * the halo value psi_0 on both sides and the advector of face 1/2. */
+template <class T, class Get> T f_flux_m(const Ctx& c, int k, int d, long i, bool limited, Get get) {
+  const int a = c.g.ax(d);
+  if (c.g.open[a] && cell_of(c.g, i).c[a] == 0) return f_flux_at<T>(c, k, d, i, -1, limited, get);
+  return get(limited ? c.id.fh(k, d) : c.id.f(k, d), nbr(c.g, i, d, -1));
 }
 
 /* Donor-cell pass, Eq. 4: psi_i - (1/G_i) sum_d [F_{i+1/2} - F_{i-1/2}], summed
@@ -188,7 +222,7 @@ template <class T, class Get> T f_donor(const Ctx& c, int k, long i, Get get) {
   const double Gi = c.Gc(i);
   for (int d = 0; d < c.g.nd; ++d) {
     T Fp = get(c.id.fh(k, d), i);
-    T Fm = get(c.id.fh(k, d), nbr(c.g, i, d, -1));
+    T Fm = f_flux_m<T>(c, k, d, i, true, get);
     T terms[2] = {-Fp / Gi, Fm / Gi};
     for (const T& t : terms) {
       if (c.kahan) {
@@ -296,7 +330,7 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
   const Cell x = cell_of(g, i);
   const long ip = lin(g, sh(g, x, d, +1));
   const double Gb = 0.5 * (c.Gc(i) + c.Gc(ip));
-  T V = get(c.adv(k - 1, d), i);
+  T V = get(c.adv(k - 1, d), fc(g, i, d, 0));
   /* variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi| */
   auto psi = [&](long j) { return c.abs ? absv(get(P, j)) : get(P, j); };
   T p0 = psi(i), p1 = psi(ip);
@@ -309,7 +343,9 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
     const Cell xp = sh(g, x, q, +1), xm = sh(g, x, q, -1);
     const long iqp = lin(g, xp), idqp = lin(g, sh(g, xp, d, +1));
     const long iqm = lin(g, xm), idqm = lin(g, sh(g, xm, d, +1));
-    Vq[q] = 0.25 * ((get(Q, i) + get(Q, ip)) + (get(Q, iqm) + get(Q, idqm)));
+    /* the q-faces q+1/2 and q-1/2 of cells i and i+e_d */
+    Vq[q] = 0.25 * ((get(Q, fc(g, i, q, 0)) + get(Q, fc(g, ip, q, 0))) +
+                    (get(Q, fc(g, i, q, -1)) + get(Q, fc(g, ip, q, -1))));
     T Tp = psi(iqp) + psi(idqp);
     T Bt = psi(iqm) + psi(idqm);
     T B = c.iga ? (Tp - Bt) * 0.25 : frac(Tp - Bt, Tp + Bt);
@@ -327,7 +363,7 @@ template <class T, class Get> T f_antidiff(const Ctx& c, int k, int d, long i, G
       T s = 0.0;
       for (int q = 0; q < g.nd; ++q) {
         const int Q = c.adv(k - 1, q);
-        s = s + (get(Q, lin(g, y)) - get(Q, lin(g, sh(g, y, q, -1))));
+        s = s + (get(Q, fc(g, lin(g, y), q, 0)) - get(Q, fc(g, lin(g, y), q, -1)));
       }
       return s;
     };
@@ -345,7 +381,7 @@ template <class T, class Get> T f_beta(const Ctx& c, int k, long i, bool up, Get
   T in = 0.0, out = 0.0;
   for (int d = 0; d < c.g.nd; ++d) {
     T Fp = get(c.id.f(k, d), i);
-    T Fm = get(c.id.f(k, d), nbr(c.g, i, d, -1));
+    T Fm = f_flux_m<T>(c, k, d, i, false, get);
     in = in + (pos(Fm) - neg(Fp));
     out = out + (pos(Fp) - neg(Fm));
   }
@@ -456,9 +492,12 @@ int setup(Ctx& c, int nd, const int64_t* shape, const double* const* gc, const d
   if (((opts & O_NUG) != 0) != (g != nullptr)) return 1;
   c.g.nd = nd;
   long N = 1;
+  if (opts & ~((O_OPEN0 << nd) - 1u) & ~1023u) return 1;  /* open bits of absent dimensions */
   for (int d = 0; d < nd; ++d) {
     if (shape[d] < 1) return 1;
     c.g.n[c.g.ax(d)] = shape[d];
+    c.g.open[c.g.ax(d)] = (opts & (O_OPEN0 << d)) != 0;
+    if (c.g.open[c.g.ax(d)] && shape[d] < 2) return 1;  /* an open dimension needs an interior face */
     N *= shape[d];
   }
   c.g.N = N;

@@ -20,6 +20,7 @@ import numpy as np
 __all__ = [
     "hello_1d", "rotation_2d", "rotation_steps", "deformational_3d", "deformational_scale",
     "ensemble_2d", "adjoint_2d", "gaussian_1d_cell_means", "low_modes", "streamfunction_advector",
+    "agnesi_1d",
 ]
 
 
@@ -30,6 +31,17 @@ def hello_1d(n=500, courant=0.5):
     psi = np.zeros(n)
     psi[50:101] = 1.0
     psi += np.exp(-0.5 * ((x - 300.0) / 15.0) ** 2)
+    return psi, [np.full(n, float(courant))]
+
+
+def agnesi_1d(n=101, dx=0.1, a=0.5, courant=0.5):
+    """The "hello world" of Sect. 3.3: n data points dx apart (the outermost ones on the domain
+    edges, which are open), a variable-sign Witch of Agnesi 8 a^3 / (x^2 + 4 a^2) centred in the
+    domain and shifted down by 0.5, constant Courant number.  Returns psi, [gc]; with open
+    edges the last advector entry is not an interior face and is not read."""
+    x = np.arange(n, dtype=np.float64) * dx
+    xc = 0.5 * (n - 1) * dx
+    psi = 8.0 * a ** 3 / ((x - xc) ** 2 + 4.0 * a ** 2) - 0.5
     return psi, [np.full(n, float(courant))]
 
 
