@@ -68,10 +68,28 @@ enum {
   MPDATA_ABS = 256u,        /* variable-sign fields: |psi| in every psi-fraction of the
                                pseudo-velocity (Sect. 3.1.5); excludes MPDATA_IGA.  Runs on
                                the one-kernel-per-sub-step path; no reverse step */
-  MPDATA_DFL = 512u         /* divergent flow (Sect. 3.1.3): the pseudo-velocity gains
+  MPDATA_DFL = 512u,        /* divergent flow (Sect. 3.1.3): the pseudo-velocity gains
                                -1/4 V (div_i + div_{i+e_d}) / Gb, div_j the advector's
                                difference summed over the dimensions across cell j; excludes
                                MPDATA_IGA.  One-kernel-per-sub-step path; no reverse step */
+  /* Open edges (Sect. 2.4, bcond::open: a zero-divergence condition on the domain edges)
+     along dimension d, bit MPDATA_OPEN0 << d; both ends of that dimension, the others stay
+     periodic.  The halo cells beyond an open edge hold the edge cell's value; the n-1 faces
+     between cells are interior (advector entries 0 .. n-2 along d, the paper's advector being
+     one shorter than the field along its own dimension, Sect. 3.2.5: entry n-1 is not read),
+     and each of the two boundary faces carries, for the advector and every pass's
+     pseudo-velocity, the value of the adjacent interior face.  An open dimension needs n >= 2.
+     One-kernel-per-sub-step path; no reverse step (MPDATA_EUNSUPPORTED) */
+  MPDATA_OPEN0 = 1024u,
+  MPDATA_OPEN1 = 2048u,
+  MPDATA_OPEN2 = 4096u,
+  /* Trapezoidal (Crank-Nicolson) source scheme (Sect. 4.1):
+     psi^{n+1} = ADV(psi^n + dt/2 R^n) + dt/2 R^{n+1}, for a system whose equations are the
+     handle's fields (all of one shape) with sources affine in the state,
+     R_e = sum_f A_ef psi_f + b_e (mpdata_set_rhs_linear).  R^{n+1} depends on psi^{n+1}, so
+     each cell solves (I - dt/2 A) psi^{n+1} = ADV(psi^n + dt/2 R^n) + dt/2 b.  Excludes the two
+     Euler bits; mpdata_step / mpdata_advance then take r = NULL and use dt */
+  MPDATA_RHS_TRAPEZ = 65536u
 };
 
 /* status codes */
@@ -97,6 +115,19 @@ enum {
  */
 int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype,
                   int n_iters, uint32_t opts, void* cuda_stream);
+
+/*
+ * Sources of the MPDATA_RHS_TRAPEZ scheme (Sect. 4.1): R_e = sum_f A[e * n_fields + f] psi_f + b_e
+ * for e, f = 0 .. n_fields - 1, the handle's fields being the system's equations (all of one
+ * shape, at most 8).  A (host, n_fields^2 doubles, row-major) is copied; b (device, the
+ * handle's total element count in its dtype, field after field, or NULL for b = 0) is kept by
+ * pointer and read at every step, so the caller keeps it alive and may change its contents
+ * between calls.  The translating oscillator of Sect. 4.2 is A = {0, omega, -omega, 0},
+ * b = NULL.  Errors: EINVAL for a handle without MPDATA_RHS_TRAPEZ, fields of different
+ * shapes, more than 8 fields, a null A, a misaligned b.  A step whose I - dt/2 A is
+ * singular returns EINVAL.
+ */
+int mpdata_set_rhs_linear(mpdata_t h, const double* A, const void* b);
 
 /*
  * Advances psi in place by n_steps >= 1 steps (the paper's advance(), Sect. 3.2.5).

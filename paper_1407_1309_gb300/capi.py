@@ -17,6 +17,8 @@ from . import build as _build
 # element types, option bits and status codes (include/mpdata.h)
 F32, F64 = 0, 1
 FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B, STAGED, ABS, DFL = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
+OPEN0, OPEN1, OPEN2 = 1024, 2048, 4096  # open edges along dimension 0, 1, 2 (Sect. 2.4)
+RHS_TRAPEZ = 65536  # trapezoidal source scheme with sources affine in the state (Sect. 4.1)
 OK, EINVAL, EUNSUPPORTED, ECUDA, ECOURANT, ETIMEOUT, ESTOPPED, ENOMEM = range(8)
 
 EXPORTED = (
@@ -25,6 +27,7 @@ EXPORTED = (
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
     "mpdata_advance_compensated", "mpdata_selftest_division", "mpdata_selftest_fma_rate",
     "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay",
+    "mpdata_set_rhs_linear", "mpdata_step_noalloc",
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
@@ -76,6 +79,7 @@ def load(build_if_needed: bool = True):
             "mpdata_diff_norms": ([P, P, P, DP, DP], I),
             "mpdata_check_courant": ([P, PP, P, DP], I),
             "mpdata_tune": ([P, I, I], I),
+            "mpdata_set_rhs_linear": ([P, DP, P], I),
             "mpdata_set_stream": ([P, P], I),
             "mpdata_request_stop": ([P], I),
             "mpdata_clear_stop": ([P], I),
@@ -188,6 +192,15 @@ def mpdata_selftest_division(n, d, q, stream=None):
     """q = n / d elementwise with the kernels' FP64 division (device float64 tensors)."""
     _check(load().mpdata_selftest_division(_ptr(n), _ptr(d), _ptr(q), int(q.numel()), _ptr(stream)),
            "mpdata_selftest_division")
+
+
+def mpdata_set_rhs_linear(h, A, b=None):
+    """Sources R = A psi + b of the trapezoidal scheme; A: n_fields x n_fields (anything numpy
+    turns into that many doubles, row-major), b: device tensor of the handle's total size or None."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.float64)).ravel()
+    arr = (ctypes.c_double * max(1, a.size))(*a.tolist())
+    _check(load().mpdata_set_rhs_linear(h, arr, _ptr(b)), "mpdata_set_rhs_linear")
 
 
 def mpdata_selftest_fma_rate(dtype, iters, sink, stream=None):

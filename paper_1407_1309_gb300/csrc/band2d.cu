@@ -473,7 +473,7 @@ bool aligned_to(const void* q, size_t a) { return q == nullptr || (reinterpret_c
 
 template <typename T>
 int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   BandParams<T> p;
@@ -509,7 +509,7 @@ int band_step(const Grid& g, const Opts& o, const StepArgs<T>& a, cudaStream_t s
 
 template <typename T>
 int band_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
     return MPDATA_EUNSUPPORTED;
   if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;

@@ -35,7 +35,7 @@ void batched_free(mpdata_s* h) {
 template <typename T>
 int batched_step(mpdata_s* h, const T* psi_in, T* psi_out, const T* const* gc, const T* g, const T* r, T dt,
                  T gc_scale, const Opts& o) {
-  if (handle_nd(h) != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (handle_nd(h) != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   const int nc = fused_batched_columns<T>();
   const int ty = o.tile_rows > 0 ? o.tile_rows : kDefaultBatchRows;
   void** slot = handle_batch(h);

@@ -33,6 +33,11 @@ struct mpdata_s {
   int tile_rows = 0;                 // MPDATA_TUNE_TILE_ROWS
   int kernel = 0;                    // MPDATA_TUNE_KERNEL
   std::atomic<int> stop{0};
+  // trapezoidal source scheme: R = A psi + b over the fields (mpdata_set_rhs_linear)
+  bool rhs_lin = false;
+  std::vector<double> rhs_A;
+  const void* rhs_b = nullptr;
+  void* trapez_buf = nullptr;        // psi^n + dt/2 R^n (total elements, on first use)
 };
 
 namespace {
@@ -52,7 +57,39 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 
 template <typename T>
 int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv, const T* g, const T* r,
-                double dt, int n_steps, const double* gc_scale) {
+                double dt, int n_steps, const double* gc_scale, bool inner = false);
+
+// The trapezoidal source scheme (Sect. 4.1): per step the sources' first half is added (all
+// equations at once, R^n = A psi^n + b), the fields are advected by one ordinary step (any
+// kernel family), and the implicit second half is solved per cell.
+template <typename T>
+int run_trapez(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv, const T* g, double dt,
+               int n_steps, const double* gc_scale) {
+  if (!h->rhs_lin) return MPDATA_EINVAL;
+  mpd::TrapezMat m;
+  if (!mpd::trapez_matrix(m, h->rhs_A.data(), h->n_fields, dt)) return MPDATA_EINVAL;
+  if (!h->trapez_buf && cudaMalloc(&h->trapez_buf, static_cast<size_t>(h->total) * sizeof(T)) != cudaSuccess) {
+    h->trapez_buf = nullptr;
+    return MPDATA_ENOMEM;
+  }
+  const long long n = h->grids[0].N;
+  T* S = static_cast<T*>(h->trapez_buf);
+  const T* b = static_cast<const T*>(h->rhs_b);
+  for (int s = 0; s < n_steps; ++s) {
+    if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
+    if (mpd::trapez_pre<T>(m, n, static_cast<T>(dt), s == 0 ? psi_in : psi_out, b, S, h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    const int rc = run_advance<T>(h, S, psi_out, gcv, g, nullptr, dt, 1, gc_scale ? gc_scale + s : nullptr, true);
+    if (rc != MPDATA_OK) return rc;
+    if (mpd::trapez_post<T>(m, n, static_cast<T>(dt), b, psi_out, h->stream) != cudaSuccess) return MPDATA_ECUDA;
+  }
+  return MPDATA_OK;
+}
+
+template <typename T>
+int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv, const T* g, const T* r,
+                double dt, int n_steps, const double* gc_scale, bool inner) {
+  if (!inner && (h->opts & MPDATA_RHS_TRAPEZ)) return run_trapez<T>(h, psi_in, psi_out, gcv, g, dt, n_steps, gc_scale);
   mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
   o.tile_rows = h->tile_rows;
   o.kernel = h->kernel;
@@ -120,6 +157,7 @@ int validate_fields(mpdata_s* h, const void* psi, const void* const* gc, const v
   const bool rhs = h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B);
   if (rhs != (r != nullptr)) return MPDATA_EINVAL;
   if (r && !aligned(r, h->esize)) return MPDATA_EINVAL;
+  if ((h->opts & MPDATA_RHS_TRAPEZ) && !h->rhs_lin) return MPDATA_EINVAL;
   return MPDATA_OK;
 }
 
@@ -140,6 +178,7 @@ void free_all(mpdata_s* h) {
   cudaFree(h->staged);
   cudaFree(h->pingpong);
   cudaFree(h->pingpong_lo);
+  cudaFree(h->trapez_buf);
   mpd::adjoint_free(h);
   cudaFree(h->d_spans);
   cudaFree(h->d_partial);
@@ -177,12 +216,14 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
   *out = nullptr;
   if (ndims < 1 || ndims > 3 || n_fields < 1 || n_iters < 1) return MPDATA_EINVAL;
   if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return MPDATA_EINVAL;
-  if (opts & ~1023u) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && n_iters != 2) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && (opts & (MPDATA_ABS | MPDATA_DFL))) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
+  if ((opts & MPDATA_RHS_TRAPEZ) && (opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B))) return MPDATA_EINVAL;
   for (long long i = 0; i < static_cast<long long>(n_fields) * ndims; ++i)
     if (shapes[i] < 1 || shapes[i] > (int64_t(1) << 30)) return MPDATA_EINVAL;
+  for (int f = 0; f < n_fields; ++f)
+    if (!mpd::valid_open_bits(ndims, opts, shapes + static_cast<long long>(f) * ndims)) return MPDATA_EINVAL;
   mpdata_s* h = new (std::nothrow) mpdata_s;
   if (!h) return MPDATA_ENOMEM;
   h->nd = ndims;
@@ -195,7 +236,7 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return MPDATA_ECUDA; }
   std::vector<mpd::FieldSpan> spans(n_fields);
   for (int f = 0; f < n_fields; ++f) {
-    mpd::Grid g = mpd::make_grid(ndims, shapes + static_cast<long long>(f) * ndims);
+    mpd::Grid g = mpd::make_grid(ndims, shapes + static_cast<long long>(f) * ndims, opts);
     h->grids.push_back(g);
     h->offsets.push_back(h->total);
     spans[f] = {h->total, g.N};
@@ -246,7 +287,7 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
   if (!aligned(psi_out, h->esize) || !aligned(lo_in, h->esize) || !aligned(lo_out, h->esize)) return MPDATA_EINVAL;
   if ((psi_in == psi_out) != (lo_in == lo_out)) return MPDATA_EINVAL;
   if (h->dtype != MPDATA_F32 || h->n_fields != 1 || h->nd != 2 || h->n_iters != 2 || (h->opts & MPDATA_TOT) ||
-      (h->opts & MPDATA_STAGED))
+      (h->opts & (MPDATA_STAGED | MPDATA_RHS_TRAPEZ | mpd::kOpenBits)))
     return MPDATA_EUNSUPPORTED;
   if (h->stop.load()) return MPDATA_ESTOPPED;
   DeviceGuard dg(h->device);
@@ -296,6 +337,19 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
   return cuda_status(cudaGetLastError());
 }
 
+int mpdata_set_rhs_linear(mpdata_t h, const double* A, const void* b) {
+  if (!h || !A || !(h->opts & MPDATA_RHS_TRAPEZ)) return MPDATA_EINVAL;
+  if (h->n_fields > mpd::kTrapezMax) return MPDATA_EINVAL;
+  for (int f = 1; f < h->n_fields; ++f)
+    for (int a = 0; a < 3; ++a)
+      if (h->grids[f].n[a] != h->grids[0].n[a]) return MPDATA_EINVAL;
+  if (b && !aligned(b, h->esize)) return MPDATA_EINVAL;
+  h->rhs_A.assign(A, A + static_cast<size_t>(h->n_fields) * h->n_fields);
+  h->rhs_b = b;
+  h->rhs_lin = true;
+  return MPDATA_OK;
+}
+
 int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, const void* r, double dt,
                 int n_steps) {
   return mpdata_advance(h, psi, psi, gc, g, r, dt, n_steps, nullptr);
@@ -304,7 +358,7 @@ int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, con
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
                         void* const* gc_bar) {
   if (!h || !psi_bar) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -324,7 +378,7 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
 // Checks shared by the reverse-step entry points: options, fields, a single-field handle.
 static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
   if (!h) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -335,7 +389,7 @@ static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, 
 
 int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes) {
   if (!h || !bytes) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   if (h->n_fields != 1 || h->n_iters > 4) return MPDATA_EUNSUPPORTED;
   *bytes = mpd::adjoint_tape_bytes(h, h->esize);

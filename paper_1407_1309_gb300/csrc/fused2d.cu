@@ -553,7 +553,7 @@ int fused_strip_stride(int nc) { return 32 * nc - 2 * kLead; }
 template <typename T>
 int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
                        const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st) {
-  if (o.n_iters != 2 || o.tot || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   BatchParams<T> b;
   b.psi = psi_in;
@@ -643,7 +643,7 @@ void launch_comp(const F2Params<float>& p, bool iga, cudaStream_t st) {
 
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   bool band_auto = false;
@@ -655,7 +655,7 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
 
 int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, const float* lo_in, float* lo_out,
                     cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   if (a.psi_out == a.psi_in || lo_out == lo_in) return MPDATA_EUNSUPPORTED;
   bool band_auto = false;
   F2Params<float> p = warp_params(g, o, a, &band_auto);  // the warp march carries the low parts
@@ -672,7 +672,7 @@ int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, cons
 
 template <typename T>
 int fused_tape(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tape, cudaStream_t st) {
-  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
+  if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open || o.kahan || o.nug || o.iga || o.rhs_a || o.rhs_b)
     return MPDATA_EUNSUPPORTED;
   if (a.psi_out == nullptr || a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;

@@ -12,6 +12,8 @@
 
 namespace mpd {
 
+constexpr uint32_t kOpenBits = MPDATA_OPEN0 | MPDATA_OPEN1 | MPDATA_OPEN2;
+
 // A value computed once per device (a kernel's opt-in shared-memory attribute, a persistent
 // grid size): get() returns the value cached for the current device, computing it with
 // init(device) under a lock on the first call there, so threads that launch on several
@@ -48,18 +50,34 @@ struct Grid {
   int nd;
   int n[3];
   long long N;
+  // open edges (MPDATA_OPEN0 << d) on each internal axis; periodic where false
+  bool open[3];
+  bool any_open() const { return open[0] || open[1] || open[2]; }
 };
 
-inline Grid make_grid(int nd, const int64_t* shape) {
+inline Grid make_grid(int nd, const int64_t* shape, uint32_t opts = 0) {
   Grid g;
   g.nd = nd;
   g.n[0] = g.n[1] = g.n[2] = 1;
+  g.open[0] = g.open[1] = g.open[2] = false;
   g.N = 1;
   for (int d = 0; d < nd; ++d) {
     g.n[3 - nd + d] = static_cast<int>(shape[d]);
+    g.open[3 - nd + d] = (opts & (MPDATA_OPEN0 << d)) != 0;
     g.N *= shape[d];
   }
   return g;
+}
+
+// Option bits a handle accepts for nd dimensions; checks shared by mpdata_create and
+// mpdata_step_noalloc.
+inline bool valid_open_bits(int nd, uint32_t opts, const int64_t* shape) {
+  // bits 0 .. 9, the open bits of the nd dimensions and the trapezoidal source scheme
+  const uint32_t all = ((MPDATA_OPEN0 << nd) - 1u) | MPDATA_RHS_TRAPEZ;
+  if (opts & ~all) return false;
+  for (int d = 0; d < nd; ++d)
+    if ((opts & (MPDATA_OPEN0 << d)) && shape[d] < 2) return false;
+  return true;
 }
 
 // Run-time options of one step.
@@ -67,6 +85,7 @@ struct Opts {
   bool fct, tot, iga, nug, kahan, rhs_a, rhs_b, staged;
   bool abs;  // |psi| in the psi-fractions of the pseudo-velocity (variable-sign fields)
   bool dfl;  // divergent-flow term of the pseudo-velocity
+  bool open; // open edges along some dimension (staged kernels only)
   int n_iters;
   int tile_rows;  // fused 2D kernels: rows per warp tile / per block band (0 = automatic)
   int kernel;     // fused 2D kernel family: 0 automatic, 1 warp march, 2 band march
@@ -84,6 +103,7 @@ inline Opts make_opts(uint32_t o, int n_iters) {
   p.staged = o & MPDATA_STAGED;
   p.abs = o & MPDATA_ABS;
   p.dfl = o & MPDATA_DFL;
+  p.open = (o & kOpenBits) != 0;
   p.n_iters = n_iters;
   p.tile_rows = 0;
   p.kernel = 0;
@@ -151,6 +171,22 @@ struct Tape {
 template <typename T>
 cudaError_t staged_forward_tape(const Grid& g, const Opts& o, const T* const* gc, const T* G,
                                 const Tape<T>& tp, T* const* psi_out_levels, T* psi_next, cudaStream_t st);
+
+// Trapezoidal source scheme (rhs.cu) for a system of E <= kTrapezMax equations of n cells each,
+// stored field after field: pre writes psi + dt/2 (A psi + b) into out; post turns the advected
+// fields into psi^{n+1} = Minv (psi* + dt/2 b) in place, Minv = (I - dt/2 A)^{-1}.
+constexpr int kTrapezMax = 8;
+struct TrapezMat {
+  int E;
+  double A[kTrapezMax * kTrapezMax];
+  double Minv[kTrapezMax * kTrapezMax];
+};
+// Minv of I - dt/2 A by Gauss-Jordan elimination with partial pivoting; false if singular.
+bool trapez_matrix(TrapezMat& m, const double* A, int E, double dt);
+template <typename T>
+cudaError_t trapez_pre(const TrapezMat& m, long long n, T dt, const T* psi, const T* b, T* out, cudaStream_t st);
+template <typename T>
+cudaError_t trapez_post(const TrapezMat& m, long long n, T dt, const T* b, T* psi, cudaStream_t st);
 
 // FP64 reductions (reduce.cu).  partial: device scratch of at least
 // kRedBlocks * n_fields doubles per output.

@@ -77,7 +77,6 @@ extern "C" int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, i
   if (!shape || !psi_in || !psi_out || !gc) return MPDATA_EINVAL;
   if (ndims < 1 || ndims > 3 || n_iters < 1) return MPDATA_EINVAL;
   if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return MPDATA_EINVAL;
-  if (opts & ~1023u) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && n_iters != 2) return MPDATA_EINVAL;
   if ((opts & MPDATA_IGA) && (opts & (MPDATA_ABS | MPDATA_DFL))) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
@@ -90,6 +89,7 @@ extern "C" int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, i
     n *= shape[d];
     if (n > (1LL << 40)) return MPDATA_EINVAL;
   }
+  if (!mpd::valid_open_bits(ndims, opts, shape) || (opts & MPDATA_RHS_TRAPEZ)) return MPDATA_EINVAL;
   const size_t es = dtype == MPDATA_F32 ? 4 : 8;
   // the staged sub-steps use kStagedArrays arrays of n elements
   if (static_cast<unsigned long long>(n) * mpd::kStagedArrays * es > kNoallocBytes) return MPDATA_EINVAL;
@@ -100,7 +100,7 @@ extern "C" int mpdata_step_noalloc(int ndims, const int64_t* shape, int dtype, i
   void* scratch = nullptr;
   const int rc = scratch_address(&scratch);
   if (rc != MPDATA_OK) return rc;
-  const mpd::Grid gr = mpd::make_grid(ndims, shape);
+  const mpd::Grid gr = mpd::make_grid(ndims, shape, opts);
   const mpd::Opts o = mpd::make_opts(opts, n_iters);
   const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (dtype == MPDATA_F32) return run<float>(gr, o, psi_in, psi_out, gc, g, r, dt, scratch, st);

@@ -40,19 +40,38 @@ struct Coord { int c[3]; };
 __device__ __forceinline__ long long lin(const Grid& g, const Coord& x) {
   return (static_cast<long long>(x.c[0]) * g.n[1] + x.c[1]) * g.n[2] + x.c[2];
 }
-// cell x moved by s cells along dimension d (periodic)
+// cell x moved by s cells along dimension d: periodic, or clamped to the edge cell along an
+// open dimension (the halo beyond an open edge holds the edge value, Sect. 2.4)
 template <int ND>
 __device__ __forceinline__ Coord sh(const Grid& g, Coord x, int d, int s) {
   const int a = 3 - ND + d;
   const int n = g.n[a];
-  // |s| <= 2: two corrections each way wrap any extent n >= 1 (no loop)
   int v = x.c[a] + s;
-  if (v < 0) v += n;
-  if (v < 0) v += n;
-  if (v >= n) v -= n;
-  if (v >= n) v -= n;
+  if (g.open[a]) {
+    v = v < 0 ? 0 : (v > n - 1 ? n - 1 : v);
+  } else {
+    // |s| <= 2: two corrections each way wrap any extent n >= 1 (no loop)
+    if (v < 0) v += n;
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if (v >= n) v -= n;
+  }
   x.c[a] = v;
   return x;
+}
+
+// storage position of face x_d + s + 1/2 of a vector component along its own dimension d:
+// periodic, or, along an open dimension, clamped to the interior faces 0 .. n-2 (a boundary
+// face carries the adjacent interior face's value: the zero-divergence condition, Sect. 2.4)
+template <int ND>
+__device__ __forceinline__ int face_pos(const Grid& g, const Coord& x, int d, int s) {
+  const int a = 3 - ND + d;
+  const int n = g.n[a];
+  int v = x.c[a] + s;
+  if (g.open[a]) return v < 0 ? 0 : (v > n - 2 ? n - 2 : v);
+  if (v < 0) v += n;
+  if (v >= n) v -= n;
+  return v;
 }
 
 // Loop over the cells of a field launched on a (fast, middle, slow) grid: coordinates come
@@ -72,13 +91,16 @@ inline dim3 cell_grid(const Grid& g, int bs) {
 
 inline dim3 march3_grid(const Grid& g);
 
-// Linear index of a cell and the index offsets of its periodic neighbours: off[d][s+2]
-// moves s = -2..2 cells along dimension d.  Shifts along different dimensions wrap
-// independently, so a diagonal neighbour is the sum of two offsets.
+// Linear index of a cell and the index offsets of its neighbours: off[d][s+2] moves s = -2..2
+// cells along dimension d (wrapped, or clamped along an open dimension); fo[d][s+1] moves to
+// the storage of face x_d + s + 1/2 of the component along d, s = -1..1 (face_pos).  Shifts
+// along different dimensions are independent, so a diagonal neighbour, or the q-face of a
+// neighbour along d, is the sum of two offsets.
 template <int ND>
 struct Nbr {
   long long i;
   long long off[ND][5];
+  long long fo[ND][3];
   __device__ __forceinline__ Nbr(const Grid& g, const Coord& x) {
     i = lin(g, x);
     long long stride = 1;
@@ -88,12 +110,17 @@ struct Nbr {
       if (d >= 0) {
 #pragma unroll
         for (int s = -2; s <= 2; ++s) off[d][s + 2] = (sh<ND>(g, x, d, s).c[a] - x.c[a]) * stride;
+#pragma unroll
+        for (int s = -1; s <= 1; ++s) fo[d][s + 1] = (face_pos<ND>(g, x, d, s) - x.c[a]) * stride;
       }
       stride *= g.n[a];
     }
   }
   __device__ __forceinline__ long long at(int d, int s) const { return i + off[d][s + 2]; }
   __device__ __forceinline__ long long at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
+  // face x_d + s + 1/2 of the component along d, of this cell or of the cell j on its row
+  __device__ __forceinline__ long long face(int d, int s) const { return i + fo[d][s + 1]; }
+  __device__ __forceinline__ long long face_of(long long j, int d, int s) const { return j + fo[d][s + 1]; }
 };
 
 // donor-cell flux of Eq. 5 in advector units; psi -> 1 under infinite gauge
@@ -125,7 +152,7 @@ __global__ void k_donor(Grid g, const T* __restrict__ psi, In3<T> V, T vscale, b
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
     const long long im = nb.at(d, -1);
-    const T vp = V.p[d][i] * vscale, vm = V.p[d][im] * vscale;
+    const T vp = V.p[d][nb.face(d, 0)] * vscale, vm = V.p[d][nb.face(d, -1)] * vscale;
     const T Fp = flux(p, psi[ip], vp, unit);
     const T Fm = flux(psi[im], p, vm, unit);
     const T t0 = G ? -qdiv(Fp, Gi) : -Fp;
@@ -197,7 +224,7 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
     const long long ip = nb.at(d, +1);
     // every 1/Gb of the face is one reciprocal, multiplied in
     const T rGb = G ? qdiv(T(1), T(0.5) * (G[i] + G[ip])) : T(1);
-    const T V = Vin.p[d][i] * vscale;
+    const T V = Vin.p[d][nb.face(d, 0)] * vscale;
     const T p1 = ps(ip);
     const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
     T out = (absv(V) - V * V * rGb) * A;
@@ -208,7 +235,9 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
       const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
       const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
       const T* Q = Vin.p[q];
-      Vq[q] = T(0.25) * ((Q[i] * vscale + Q[ip] * vscale) + (Q[iqm] * vscale + Q[idqm] * vscale));
+      // the q-faces q+1/2 and q-1/2 of cells i and i+e_d
+      Vq[q] = T(0.25) * ((Q[nb.face(q, 0)] * vscale + Q[nb.face_of(ip, q, 0)] * vscale) +
+                         (Q[nb.face(q, -1)] * vscale + Q[nb.face_of(ip, q, -1)] * vscale));
       const T Tp = ps(iqp) + ps(idqp);
       const T Bt = ps(iqm) + ps(idqm);
       const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
@@ -255,9 +284,11 @@ __global__ void k_antidiff(Grid g, const T* __restrict__ psi, In3<T> Vin, T vsca
 #pragma unroll
       for (int q = 0; q < ND; ++q) {
         const T* Q = Vin.p[q];
-        const long long jm = nb.at(q, -1);                                 // i - e_q
-        const long long pm = q == d ? i : nb.at2(d, +1, q, -1);            // i + e_d - e_q
-        div = div + ((Q[i] * vscale - Q[jm] * vscale) + (Q[ip] * vscale - Q[pm] * vscale));
+        // faces q+1/2 and q-1/2 of cell i, then of cell i+e_d (along q == d: faces x+3/2, x+1/2)
+        const long long a0 = nb.face(q, 0), a1 = nb.face(q, -1);
+        const long long b0 = q == d ? nb.face(d, +1) : nb.face_of(ip, q, 0);
+        const long long b1 = q == d ? nb.face(d, 0) : nb.face_of(ip, q, -1);
+        div = div + ((Q[a0] * vscale - Q[a1] * vscale) + (Q[b0] * vscale - Q[b1] * vscale));
       }
       out = out - T(0.25) * V * div * rGb;
     }
@@ -855,8 +886,8 @@ __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __r
   for (int d = 0; d < ND; ++d) {
     const long long ip = nb.at(d, +1);
     const long long im = nb.at(d, -1);
-    const T Fp = flux(p, psi[ip], V.p[d][i], unit);
-    const T Fm = flux(psi[im], p, V.p[d][im], unit);
+    const T Fp = flux(p, psi[ip], V.p[d][nb.face(d, 0)], unit);
+    const T Fm = flux(psi[im], p, V.p[d][nb.face(d, -1)], unit);
     in = in + (posp(Fm) - negp(Fp));
     out = out + (posp(Fp) - negp(Fm));
   }
@@ -1118,7 +1149,7 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   T* dst1 = (K == 1 && !inplace1) ? a.psi_out : s.pa;
   // FP32: pass 1 and the bounds in one z-march (FP64 is arithmetic-bound and the z-march
   // recomputes pass 1 on a one-cell halo)
-  if (ND == 3 && K >= 2 && o.fct && sizeof(T) == 4) {
+  if (ND == 3 && K >= 2 && o.fct && sizeof(T) == 4 && !o.open) {
     launch_p1b3<T>(g, p0, gc, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
   } else {
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
@@ -1136,7 +1167,7 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   for (int k = 2; k <= K; ++k) {
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
-    if (ND == 3 && !o.dfl) {
+    if (ND == 3 && !o.dfl && !o.open) {
       launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, o.dfl,
@@ -1146,7 +1177,7 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
     // FP32: factors, limiter and donor pass in one z-march (it limits each face from both sides
     // and forms the factors on a one-cell halo: cheaper than the array traffic it saves in
     // FP32, dearer in FP64, which the arithmetic bounds)
-    if (ND == 3 && o.fct && sizeof(T) == 4) {
+    if (ND == 3 && o.fct && sizeof(T) == 4 && !o.open) {
       T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
       Out3<T> lk{{nullptr, nullptr, nullptr}};
       if (k < K) lk = Out3<T>{{lim[0], lim[1], lim[2]}};
@@ -1265,7 +1296,7 @@ template StagedScratch<double> carve_staged<double>(void*, long long);
 template <typename T>
 int steps1d(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc, const T* G, const T* R, T dt,
             int n_steps, cudaStream_t st) {
-  if (g.nd != 1 || o.n_iters > 64 || o.abs || o.dfl) return MPDATA_EUNSUPPORTED;
+  if (g.nd != 1 || o.n_iters > 64 || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   const size_t smem = steps1d_smem<T>(g.N);
   static PerDevice<int> max_smem_of;
   const int max_smem = max_smem_of.get([](int dev) {

@@ -75,6 +75,13 @@ class Mpdata:
         capi.mpdata_adjoint_replay(self.h, psi_n, gc, g, tape, psi_bar, gc_bar)
         return psi_bar
 
+    def set_rhs_linear(self, A, b=None):
+        """Sources R = A psi + b of the trapezoidal scheme (handles created with RHS_TRAPEZ): the
+        handle's fields are the system's equations; b (a tensor of the handle's total size, or
+        None) is read at every step and must stay alive."""
+        self._rhs_b = b
+        capi.mpdata_set_rhs_linear(self.h, A, b)
+
     def set_stream(self, stream):
         """Send later work of the handle to `stream` (a torch.cuda.Stream)."""
         capi.mpdata_set_stream(self.h, stream)

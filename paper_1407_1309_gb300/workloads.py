@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "hello_1d", "rotation_2d", "rotation_steps", "deformational_3d", "deformational_scale",
     "ensemble_2d", "adjoint_2d", "gaussian_1d_cell_means", "low_modes", "streamfunction_advector",
-    "agnesi_1d",
+    "agnesi_1d", "oscillator_1d",
 ]
 
 
@@ -43,6 +43,17 @@ def agnesi_1d(n=101, dx=0.1, a=0.5, courant=0.5):
     xc = 0.5 * (n - 1) * dx
     psi = 8.0 * a ** 3 / ((x - xc) ** 2 + 4.0 * a ** 2) - 0.5
     return psi, [np.full(n, float(courant))]
+
+
+def oscillator_1d(n=1000, courant=0.5, dt=1.0, period=1400.0):
+    """Translating harmonic oscillator of Sect. 4.2: psi_t + (u psi)_x = omega phi,
+    phi_t + (u phi)_x = -omega psi, on n cells of 1 m (periodic), u = courant m/s, time step
+    dt s.  psi(x) = 0.5 (1 + cos(2 pi x / 100)) for 50 < x < 150 (cell centres), else 0; phi = 0.
+    The paper gives the initial condition and the 1400 s of simulated time, not omega, the grid or
+    the step; here omega = 2 pi / period.  Returns psi, phi, [gc], omega."""
+    x = np.arange(n, dtype=np.float64) + 0.5
+    psi = np.where((x > 50.0) & (x < 150.0), 0.5 * (1.0 + np.cos(2.0 * math.pi * x / 100.0)), 0.0)
+    return psi, np.zeros(n), [np.full(n, float(courant))], 2.0 * math.pi / period
 
 
 def rotation_steps(n):
