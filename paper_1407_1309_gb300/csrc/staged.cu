@@ -327,6 +327,28 @@ constexpr size_t antidiff3_smem() {
   return sizeof(T) * (kA3P * kPw * kPh + (3 + 1) * kA3V * kVw * kVh);
 }
 
+// guarded psi-fractions n1/d and n2/d with one denominator (0 when d == 0): in FP32 one
+// approximate reciprocal serves both quotients; FP64 divides each with the remainder-corrected
+// Newton-Raphson division
+template <typename T>
+__device__ __forceinline__ void frac2(T n1, T n2, T d, T& r1, T& r2) {
+  if constexpr (sizeof(T) == 4) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(d));
+    r1 = d != T(0) ? n1 * r : T(0);
+    r2 = d != T(0) ? n2 * r : T(0);
+  } else {
+    r1 = fracg(n1, d);
+    r2 = fracg(n2, d);
+  }
+}
+
+// s + j modulo n, for 0 <= s, j < n (ring slots)
+__device__ __forceinline__ int rot(int s, int j, int n) {
+  const int v = s + j;
+  return v >= n ? v - n : v;
+}
+
 template <typename T, bool ABS>
 __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __restrict__ psi, In3<T> Vin,
                                                          T vscale, const T* __restrict__ G, bool iga, bool tot,
@@ -358,13 +380,13 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
     offV[r] = wrapc(y0 - 1 + yy, ny) * nx + wrapc(x0 - 1 + (k - yy * kVw), nx);
   }
   auto zoff = [&](int z) { return static_cast<long long>(wrapc(z, nz)) * plane; };
-  auto copyP = [&](T* dst, int z) {
-    const T* src = psi + zoff(z);
+  auto copyP = [&](T* dst, long long zo) {
+    const T* src = psi + zo;
     dev::cp_async<sizeof(T)>(dst + tid, src + offP[0]);
     if (hasP1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + offP[1]);
   };
-  auto copyV = [&](T* dst, const T* base, int z) {
-    const T* src = base + zoff(z);
+  auto copyV = [&](T* dst, const T* base, long long zo) {
+    const T* src = base + zo;
     dev::cp_async<sizeof(T)>(dst + tid, src + offV[0]);
     if (hasV1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + offV[1]);
   };
@@ -373,62 +395,63 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
     dst[tid] *= vscale;
     if (hasV1) dst[tid + kT] *= vscale;
   };
-  // ring slots: psi planes zb-1 ..; the z component planes z-1, z; the y, x components and G
-  // planes z, z+1
-  auto slotP = [&](int z) { return (z - zb + 1 + kA3P) % kA3P; };
-  auto slotVz = [&](int z) { return (z - zb + 1 + kA3V) % kA3V; };
-  auto slotVq = [&](int z) { return (z - zb + kA3V) % kA3V; };
-  auto Vp = [&](int d, int z) { return sV + (d * kA3V + (d == 0 ? slotVz(z) : slotVq(z))) * nV; };
-  auto Gp = [&](int z) { return sG + slotVq(z) * nV; };
-  // the planes that become needed at step z: psi z+2, z component z, y and x components and G z+1
-  auto copy_step = [&](int z) {
-    copyP(sP + slotP(z + 2) * nP, z + 2);
-    copyV(Vp(0, z), Vin.p[0], z);
-    copyV(Vp(1, z + 1), Vin.p[1], z + 1);
-    copyV(Vp(2, z + 1), Vin.p[2], z + 1);
-    if (G) copyV(Gp(z + 1), G, z + 1);
-  };
-  auto scale_step = [&](int z) {
-    if (vscale != T(1)) {
-      scaleV(Vp(0, z));
-      scaleV(Vp(1, z + 1));
-      scaleV(Vp(2, z + 1));
-    }
-  };
+  // Ring slots, advanced by one at every step z: the psi planes z-1 .. z+2 are in slots
+  // cp .. cp+3 (mod kA3P, the fifth takes plane z+3 in flight); the z component planes z-1, z in
+  // cz, cz+1 (mod kA3V; z+1 in flight); the y, x components and G planes z, z+1 in cq, cq+1
+  // (z+2 in flight).
+  int cp = 0, cz = 0, cq = 0;
+  auto Vzs = [&](int s) { return sV + s * nV; };
+  auto Vys = [&](int s) { return sV + (kA3V + s) * nV; };
+  auto Vxs = [&](int s) { return sV + (2 * kA3V + s) * nV; };
+  auto Gs = [&](int s) { return sG + s * nV; };
 
-  copyP(sP + slotP(zb - 1) * nP, zb - 1);
-  copyP(sP + slotP(zb) * nP, zb);
-  copyP(sP + slotP(zb + 1) * nP, zb + 1);
-  copyV(Vp(0, zb - 1), Vin.p[0], zb - 1);
-  copyV(Vp(1, zb), Vin.p[1], zb);
-  copyV(Vp(2, zb), Vin.p[2], zb);
-  if (G) copyV(Gp(zb), G, zb);
-  copy_step(zb);
-  dev::cp_commit();
-  dev::cp_wait<0>();
-  if (vscale != T(1)) {
-    scaleV(Vp(0, zb - 1));
-    scaleV(Vp(1, zb));
-    scaleV(Vp(2, zb));
+  {  // prologue: psi planes zb-1 .. zb+2, z component zb-1, zb, the others and G zb, zb+1
+    for (int j = 0; j < 4; ++j) copyP(sP + j * nP, zoff(zb - 1 + j));
+    copyV(Vzs(0), Vin.p[0], zoff(zb - 1));
+    copyV(Vzs(1), Vin.p[0], zoff(zb));
+    for (int j = 0; j < 2; ++j) {
+      const long long zo = zoff(zb + j);
+      copyV(Vys(j), Vin.p[1], zo);
+      copyV(Vxs(j), Vin.p[2], zo);
+      if (G) copyV(Gs(j), G, zo);
+    }
+    dev::cp_commit();
+    dev::cp_wait<0>();
+    if (vscale != T(1)) {
+      for (int j = 0; j < 2; ++j) {
+        scaleV(Vzs(j));
+        scaleV(Vys(j));
+        scaleV(Vxs(j));
+      }
+    }
   }
-  scale_step(zb);
 
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < nx && y < ny;
   const int cP = (ty + 1) * kPw + (tx + 1), cV = (ty + 1) * kVw + (tx + 1);  // this cell in a plane
+  const long long row = static_cast<long long>(y) * nx + x;
   for (int z = zb; z < ze; ++z) {
     __syncthreads();  // step z's planes are in (each thread waited for its own copies)
-    if (z + 1 < ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    const int fp = rot(cp, 4, kA3P), fz = rot(cz, 2, kA3V), fq = rot(cq, 2, kA3V);  // in-flight slots
+    if (z + 1 < ze) {  // the next step's planes fly while this one computes
+      copyP(sP + fp * nP, zoff(z + 3));
+      copyV(Vzs(fz), Vin.p[0], zoff(z + 1));
+      const long long zo = zoff(z + 2);
+      copyV(Vys(fq), Vin.p[1], zo);
+      copyV(Vxs(fq), Vin.p[2], zo);
+      if (G) copyV(Gs(fq), G, zo);
+    }
     dev::cp_commit();
     if (inside) {
       // this cell's position in each plane of the rings; every neighbour below is a fixed
       // offset from one of these
-      const T* pz[4] = {sP + slotP(z - 1) * nP + cP, sP + slotP(z) * nP + cP, sP + slotP(z + 1) * nP + cP,
-                        sP + slotP(z + 2) * nP + cP};
-      const T* vz[2] = {Vp(0, z - 1) + cV, Vp(0, z) + cV};      // z component, planes z-1, z
-      const T* vy[2] = {Vp(1, z) + cV, Vp(1, z + 1) + cV};      // y component, planes z, z+1
-      const T* vx[2] = {Vp(2, z) + cV, Vp(2, z + 1) + cV};      // x component, planes z, z+1
-      const T* gz[2] = {Gp(z) + cV, Gp(z + 1) + cV};
+      const T* pz[4] = {sP + cp * nP + cP, sP + rot(cp, 1, kA3P) * nP + cP, sP + rot(cp, 2, kA3P) * nP + cP,
+                        sP + rot(cp, 3, kA3P) * nP + cP};
+      const int cq1 = rot(cq, 1, kA3V);
+      const T* vz[2] = {Vzs(cz) + cV, Vzs(rot(cz, 1, kA3V)) + cV};  // z component, planes z-1, z
+      const T* vy[2] = {Vys(cq) + cV, Vys(cq1) + cV};               // y component, planes z, z+1
+      const T* vx[2] = {Vxs(cq) + cV, Vxs(cq1) + cV};               // x component, planes z, z+1
+      const T* gz[2] = {Gs(cq) + cV, Gs(cq1) + cV};
       // ABS, the variable-sign option (Sect. 3.1.5): psi enters every psi-fraction as |psi|
       auto P = [&](int dz, int dy, int dx) {
         const T v = pz[dz + 1][dy * kPw + dx];
@@ -439,8 +462,8 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
         return q == 0 ? vz[dz + 1][dy * kVw + dx] : (q == 1 ? vy[dz][dy * kVw + dx] : vx[dz][dy * kVw + dx]);
       };
       auto Gv = [&](int dz, int dy, int dx) { return gz[dz][dy * kVw + dx]; };
-      const long long i = static_cast<long long>(z) * plane + static_cast<long long>(y) * nx + x;
       const T p0 = P(0, 0, 0);
+      T res[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         // unit offsets of dimension d (0 = z, 1 = y, 2 = x)
@@ -451,14 +474,23 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
         const T A = iga ? (p1 - p0) * T(0.5) : fracg(p1 - p0, p0 + p1);
         T out = (absv(V) - V * V * rGb) * A;
         T Vq[3] = {T(0), T(0), T(0)};
+        T Dq[3] = {T(0), T(0), T(0)};  // the third-order pair terms D_dq, formed with B_q
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           if (q == d) continue;
           const int qz = q == 0, qy = q == 1, qx = q == 2;
           Vq[q] = T(0.25) * ((Q(q, 0, 0, 0) + Q(q, dz, dy, dx)) + (Q(q, -qz, -qy, -qx) + Q(q, dz - qz, dy - qy, dx - qx)));
-          const T Tp = P(qz, qy, qx) + P(qz + dz, qy + dy, qx + dx);
-          const T Bt = P(-qz, -qy, -qx) + P(dz - qz, dy - qy, dx - qx);
-          const T B = iga ? (Tp - Bt) * T(0.25) : fracg(Tp - Bt, Tp + Bt);
+          const T a = P(qz, qy, qx), b = P(qz + dz, qy + dy, qx + dx);
+          const T e = P(-qz, -qy, -qx), f = P(dz - qz, dy - qy, dx - qx);
+          const T Tp = a + b, Bt = e + f;
+          T B;
+          if (iga) {
+            B = (Tp - Bt) * T(0.25);
+            Dq[q] = ((b - a) - (f - e)) * T(0.25);
+          } else {
+            // B_q and D_dq share the denominator (a + b) + (e + f) = Tp + Bt
+            frac2(Tp - Bt, (b - a) - (f - e), Tp + Bt, B, Dq[q]);
+          }
           out = out - T(0.5) * V * Vq[q] * rGb * B;
         }
         if (tot) {
@@ -472,12 +504,7 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
           for (int q = 0; q < 3; ++q) {
             if (q == d) continue;
             qs[nq++] = q;
-            const int qz = q == 0, qy = q == 1, qx = q == 2;
-            const T a = P(qz, qy, qx), b = P(qz + dz, qy + dy, qx + dx);
-            const T e = P(-qz, -qy, -qx), f = P(dz - qz, dy - qy, dx - qx);
-            const T n2 = (b - a) - (f - e);
-            const T D2 = iga ? n2 * T(0.25) : fracg(n2, (a + b) + (e + f));
-            out = out + absv(V) * Vq[q] * rGb * (T(1) - T(2) * absv(V) * rGb) * D2;
+            out = out + absv(V) * Vq[q] * rGb * (T(1) - T(2) * absv(V) * rGb) * Dq[q];
           }
           T pr[4];
           int m = 0;
@@ -496,11 +523,23 @@ __global__ void __launch_bounds__(kAx * kAy) k_antidiff3(Grid g, const T* __rest
           const T D3 = iga ? n3 * T(0.125) : fracg(n3, (pr[0] + pr[1]) + (pr[2] + pr[3]));
           out = out - (T(2) / T(3)) * V * Vq[qs[0]] * Vq[qs[1]] * (rGb * rGb) * D3;
         }
-        Vout.p[d][i] = out;
+        res[d] = out;
       }
+      // stored after all three faces, so that no store separates the shared-memory reads
+      const long long i = static_cast<long long>(z) * plane + row;
+      Vout.p[0][i] = res[0];
+      Vout.p[1][i] = res[1];
+      Vout.p[2][i] = res[2];
     }
     dev::cp_wait<0>();
-    if (z + 1 < ze) scale_step(z + 1);  // only planes copied in this step are scaled
+    if (z + 1 < ze && vscale != T(1)) {  // only planes copied in this step are scaled
+      scaleV(Vzs(fz));
+      scaleV(Vys(fq));
+      scaleV(Vxs(fq));
+    }
+    cp = rot(cp, 1, kA3P);
+    cz = rot(cz, 1, kA3V);
+    cq = rot(cq, 1, kA3V);
   }
 }
 
@@ -560,41 +599,48 @@ __global__ void __launch_bounds__(kAx * kAy) k_p1b3(Grid g, const T* __restrict_
     dev::cp_async<sizeof(T)>(dst + tid, src + off[0]);
     if (has1) dev::cp_async<sizeof(T)>(dst + tid + kT, src + off[1]);
   };
-  auto slotN = [&](int z) { return (z - zb + 10) % kP1N; };
-  auto slotX = [&](int z) { return (z - zb + 4) % kP1X; };
-  auto slotZ = [&](int z) { return (z - zb + 6) % kP1Z; };
-  auto slot1 = [&](int z) { return (z - zb + 6) % kP1Q; };
-  // the planes step z reads that step z-1 did not: psi^n z+1; the x, y, z components and G of z
-  auto copy_step = [&](int z) {
-    copy(sN + slotN(z + 1) * nB, zsrc(psi, z + 1), offB, hasB1);
-    copy(sX + slotX(z) * nX, zsrc(V.p[2], z), offX, hasX1);
-    copy(sY + slotX(z) * nX, zsrc(V.p[1], z), offX, hasX1);
-    copy(sZ + slotZ(z) * nH, zsrc(V.p[0], z), offH, hasH1);
-    if (G) copy(sG + slotX(z) * nH, zsrc(G, z), offH, hasH1);
+  // Ring slots: kn, kx, kz are the slots of plane z at step z in the rings of kP1N, kP1X and
+  // kP1Z = kP1Q planes (advanced by one per step); plane z + j sits in slot k + j (mod size).
+  int kn = kP1N - 1, kx = kP1X - 1, kz = kP1Z - 1;  // plane zb - 1
+  static_assert(kP1Z == kP1Q, "psi^(1) and the z component share their ring counter");
+  auto rj = [](int k, int j, int n) { const int v = k + j; return v >= n ? v - n : (v < 0 ? v + n : v); };
+  auto slotN = [&](int j) { return rj(kn, j, kP1N); };
+  auto slotX = [&](int j) { return rj(kx, j, kP1X); };
+  auto slotZ = [&](int j) { return rj(kz, j, kP1Z); };
+  auto slot1 = [&](int j) { return rj(kz, j, kP1Q); };
+  // the planes step zz = z + j reads that step zz-1 did not: psi^n zz+1; the x, y, z components
+  // and G of zz (z the current step)
+  auto copy_step = [&](int zz, int j) {
+    copy(sN + slotN(j + 1) * nB, zsrc(psi, zz + 1), offB, hasB1);
+    copy(sX + slotX(j) * nX, zsrc(V.p[2], zz), offX, hasX1);
+    copy(sY + slotX(j) * nX, zsrc(V.p[1], zz), offX, hasX1);
+    copy(sZ + slotZ(j) * nH, zsrc(V.p[0], zz), offH, hasH1);
+    if (G) copy(sG + slotX(j) * nH, zsrc(G, zz), offH, hasH1);
   };
 
-  copy(sN + slotN(zb - 2) * nB, zsrc(psi, zb - 2), offB, hasB1);
-  copy(sN + slotN(zb - 1) * nB, zsrc(psi, zb - 1), offB, hasB1);
-  copy(sZ + slotZ(zb - 2) * nH, zsrc(V.p[0], zb - 2), offH, hasH1);
-  copy_step(zb - 1);
+  // prologue (step zb-1): psi^n planes zb-2, zb-1, the z component of plane zb-2, then step zb-1's planes
+  copy(sN + slotN(-1) * nB, zsrc(psi, zb - 2), offB, hasB1);
+  copy(sN + slotN(0) * nB, zsrc(psi, zb - 1), offB, hasB1);
+  copy(sZ + slotZ(-1) * nH, zsrc(V.p[0], zb - 2), offH, hasH1);
+  copy_step(zb - 1, 0);
   dev::cp_commit();
   dev::cp_wait<0>();
   const int x = x0 + tx, y = y0 + ty;
   const bool inside = x < nx && y < ny;
   for (int z = zb - 1; z <= ze; ++z) {
     __syncthreads();  // step z's planes are in (each thread waited for its own copies)
-    if (z < ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    if (z < ze) copy_step(z + 1, 1);  // the next step's planes fly while this one computes
     dev::cp_commit();
     {  // pass 1 on plane z, tile and one-cell halo
-      const T* Nm = sN + slotN(z - 1) * nB;
-      const T* Nc = sN + slotN(z) * nB;
-      const T* Np = sN + slotN(z + 1) * nB;
-      const T* Zm = sZ + slotZ(z - 1) * nH;
-      const T* Zc = sZ + slotZ(z) * nH;
-      const T* Xc = sX + slotX(z) * nX;
-      const T* Yc = sY + slotX(z) * nX;
-      const T* Gc = sG + slotX(z) * nH;
-      T* const P1 = s1 + slot1(z) * nH;
+      const T* Nm = sN + slotN(-1) * nB;
+      const T* Nc = sN + slotN(0) * nB;
+      const T* Np = sN + slotN(1) * nB;
+      const T* Zm = sZ + slotZ(-1) * nH;
+      const T* Zc = sZ + slotZ(0) * nH;
+      const T* Xc = sX + slotX(0) * nX;
+      const T* Yc = sY + slotX(0) * nX;
+      const T* Gc = sG + slotX(0) * nH;
+      T* const P1 = s1 + slot1(0) * nH;
       for (int k = tid; k < nH; k += kT) {
         const int hy = k / kHw, hx = k - hy * kHw;
         const int b = (hy + 1) * kBw + (hx + 1);  // the cell in the psi^n planes
@@ -633,14 +679,14 @@ __global__ void __launch_bounds__(kAx * kAy) k_p1b3(Grid g, const T* __restrict_
     if (z - 1 >= zb && inside) {  // bounds of plane z-1
       const int zc = z - 1;
       const int b = (ty + 2) * kBw + (tx + 2), h = (ty + 1) * kHw + (tx + 1);
-      const T* N0 = sN + slotN(zc) * nB;
-      const T* Q0 = s1 + slot1(zc) * nH;
+      const T* N0 = sN + slotN(-1) * nB;  // plane zc = z - 1
+      const T* Q0 = s1 + slot1(-1) * nH;
       const T a0 = N0[b], b0 = Q0[h];
       T hi = a0 > b0 ? a0 : b0;
       T lo = a0 < b0 ? a0 : b0;
       // neighbours in k_bounds's order: z-1, z+1, y-1, y+1, x-1, x+1
-      const T cand[6][2] = {{sN[slotN(zc - 1) * nB + b], s1[slot1(zc - 1) * nH + h]},
-                            {sN[slotN(zc + 1) * nB + b], s1[slot1(zc + 1) * nH + h]},
+      const T cand[6][2] = {{sN[slotN(-2) * nB + b], s1[slot1(-2) * nH + h]},
+                            {sN[slotN(0) * nB + b], s1[slot1(0) * nH + h]},
                             {N0[b - kBw], Q0[h - kHw]},
                             {N0[b + kBw], Q0[h + kHw]},
                             {N0[b - 1], Q0[h - 1]},
@@ -659,6 +705,9 @@ __global__ void __launch_bounds__(kAx * kAy) k_p1b3(Grid g, const T* __restrict_
       mn[i] = lo;
     }
     dev::cp_wait<0>();
+    kn = rj(kn, 1, kP1N);
+    kx = rj(kx, 1, kP1X);
+    kz = rj(kz, 1, kP1Z);
   }
 }
 
@@ -725,52 +774,58 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
     dev::cp_async<sizeof(T)>(dst + tid, src + off[0]);
     if (tid + kT < count) dev::cp_async<sizeof(T)>(dst + tid + kT, src + off[1]);
   };
-  auto slot = [&](int z, int n) { return (z - zb + 4 * n) % n; };
-  auto P_ = [&](int z) { return sP + slot(z, kC3P) * nP; };
-  auto Vx_ = [&](int z) { return sVx + slot(z, kC3Vq) * nV; };
-  auto Vy_ = [&](int z) { return sVy + slot(z, kC3Vq) * nV; };
-  auto Vz_ = [&](int z) { return sVz + slot(z, kC3Vz) * nB; };
-  auto Bu_ = [&](int z) { return sBu + slot(z, kC3B) * nB; };
-  auto Bd_ = [&](int z) { return sBd + slot(z, kC3B) * nB; };
-  auto Mx_ = [&](int z) { return sMx + slot(z, kC3M) * nB; };
-  auto Mn_ = [&](int z) { return sMn + slot(z, kC3M) * nB; };
-  auto G_ = [&](int z) { return sG + slot(z, kC3G) * nB; };
-  // the planes that become needed at step z: psi z+1, the components, bounds and G of plane z
-  auto copy_step = [&](int z) {
-    copy(P_(z + 1), psi + zoff(z + 1), offP, nP);
-    copy(Vx_(z), Vu.p[2] + zoff(z), offV, nV);
-    copy(Vy_(z), Vu.p[1] + zoff(z), offV, nV);
-    copy(Vz_(z), Vu.p[0] + zoff(z), offB, nB);
-    copy(Mx_(z), mxg + zoff(z), offB, nB);
-    copy(Mn_(z), mng + zoff(z), offB, nB);
-    if (G) copy(G_(z), G + zoff(z), offB, nB);
+  // Ring slots: k5, k4, k3, k2 are the slots of plane z in the rings of 5, 4, 3 and 2 planes at
+  // step z (advanced by one per step); plane z + j sits in slot k + j (mod the ring size).
+  int k5 = kC3P - 1, k4 = kC3Vz - 1, k3 = kC3Vq - 1, k2 = kC3M - 1;  // plane zb - 1
+  static_assert(kC3P == 5 && kC3Vz == 4 && kC3Vq == 3 && kC3B == 3 && kC3G == 3 && kC3M == 2, "ring sizes");
+  auto rj = [](int k, int j, int n) { const int v = k + j; return v >= n ? v - n : (v < 0 ? v + n : v); };
+  auto P_ = [&](int j) { return sP + rj(k5, j, kC3P) * nP; };
+  auto Vx_ = [&](int j) { return sVx + rj(k3, j, kC3Vq) * nV; };
+  auto Vy_ = [&](int j) { return sVy + rj(k3, j, kC3Vq) * nV; };
+  auto Vz_ = [&](int j) { return sVz + rj(k4, j, kC3Vz) * nB; };
+  auto Bu_ = [&](int j) { return sBu + rj(k3, j, kC3B) * nB; };
+  auto Bd_ = [&](int j) { return sBd + rj(k3, j, kC3B) * nB; };
+  auto Mx_ = [&](int j) { return sMx + rj(k2, j, kC3M) * nB; };
+  auto Mn_ = [&](int j) { return sMn + rj(k2, j, kC3M) * nB; };
+  auto G_ = [&](int j) { return sG + rj(k3, j, kC3G) * nB; };
+  // the planes that become needed at step zz = z + j: psi zz+1, the components, bounds and G of
+  // plane zz (z the current step)
+  auto copy_step = [&](int zz, int j) {
+    copy(P_(j + 1), psi + zoff(zz + 1), offP, nP);
+    const long long zo = zoff(zz);
+    copy(Vx_(j), Vu.p[2] + zo, offV, nV);
+    copy(Vy_(j), Vu.p[1] + zo, offV, nV);
+    copy(Vz_(j), Vu.p[0] + zo, offB, nB);
+    copy(Mx_(j), mxg + zo, offB, nB);
+    copy(Mn_(j), mng + zo, offB, nB);
+    if (G) copy(G_(j), G + zo, offB, nB);
   };
 
-  // prologue: psi planes zb-2, zb-1, the z component of plane zb-2, then step zb-1's planes
-  copy(P_(zb - 2), psi + zoff(zb - 2), offP, nP);
-  copy(P_(zb - 1), psi + zoff(zb - 1), offP, nP);
-  copy(Vz_(zb - 2), Vu.p[0] + zoff(zb - 2), offB, nB);
-  copy_step(zb - 1);
+  // prologue (step zb-1): psi planes zb-2, zb-1, the z component of plane zb-2, then step zb-1's planes
+  copy(P_(-1), psi + zoff(zb - 2), offP, nP);
+  copy(P_(0), psi + zoff(zb - 1), offP, nP);
+  copy(Vz_(-1), Vu.p[0] + zoff(zb - 2), offB, nB);
+  copy_step(zb - 1, 0);
   dev::cp_commit();
   dev::cp_wait<0>();
 
   for (int z = zb - 1; z <= ze; ++z) {
     __syncthreads();  // step z's planes are in (each thread waited for its own copies)
-    if (z + 1 <= ze) copy_step(z + 1);  // the next step's planes fly while this one computes
+    if (z + 1 <= ze) copy_step(z + 1, 1);  // the next step's planes fly while this one computes
     dev::cp_commit();
-    const T* sMxz = Mx_(z);
-    const T* sMnz = Mn_(z);
+    const T* sMxz = Mx_(0);
+    const T* sMnz = Mn_(0);
     {  // limiting factors of plane z on the tile and a one-cell halo (k_beta)
-      const T* pm = P_(z - 1);
-      const T* p0 = P_(z);
-      const T* pp = P_(z + 1);
-      const T* vx = Vx_(z);
-      const T* vy = Vy_(z);
-      const T* vzm = Vz_(z - 1);
-      const T* vz0 = Vz_(z);
-      const T* gz = G_(z);
-      T* bu = Bu_(z);
-      T* bd = Bd_(z);
+      const T* pm = P_(-1);
+      const T* p0 = P_(0);
+      const T* pp = P_(1);
+      const T* vx = Vx_(0);
+      const T* vy = Vy_(0);
+      const T* vzm = Vz_(-1);
+      const T* vz0 = Vz_(0);
+      const T* gz = G_(0);
+      T* bu = Bu_(0);
+      T* bd = Bd_(0);
       for (int r = tid; r < nB; r += kT) {
         const int by = r / kCBw, bx = r - by * kCBw;  // cell (bx - 1, by - 1) of the tile
         const int cp = (by + 1) * kCPw + (bx + 1);    // in the psi tile
@@ -804,13 +859,14 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
     const int q = z - 1;
     const int x = x0 + tx, y = y0 + ty;
     if (q >= zb && x < nx && y < ny) {  // limit and donor of plane q (k_limit, k_donor)
-      const T* ps[3] = {P_(q - 1), P_(q), P_(q + 1)};
-      const T* bus[3] = {Bu_(q - 1), Bu_(q), Bu_(q + 1)};
-      const T* bds[3] = {Bd_(q - 1), Bd_(q), Bd_(q + 1)};
-      const T* vx = Vx_(q);
-      const T* vy = Vy_(q);
-      const T* vzm = Vz_(q - 1);
-      const T* vz0 = Vz_(q);
+      // plane q = z - 1: offsets -2 .. 0 from step z
+      const T* ps[3] = {P_(-2), P_(-1), P_(0)};
+      const T* bus[3] = {Bu_(-2), Bu_(-1), Bu_(0)};
+      const T* bds[3] = {Bd_(-2), Bd_(-1), Bd_(0)};
+      const T* vx = Vx_(-1);
+      const T* vy = Vy_(-1);
+      const T* vzm = Vz_(-2);
+      const T* vz0 = Vz_(-1);
       const int cp = (ty + 2) * kCPw + (tx + 2), cv = (ty + 2) * kCVw + (tx + 2), cb = (ty + 1) * kCBw + (tx + 1);
       const T p = ps[1][cp];
       // limited advector at a face: V m, m = min(1, factor of the upwind side, factor of the downwind side)
@@ -840,7 +896,7 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
         lim.p[1][i] = hy_p;
         lim.p[2][i] = hx_p;
       }
-      const T Gi = G ? G_(q)[cb] : T(1);
+      const T Gi = G ? G_(-1)[cb] : T(1);
       T s = p, comp = T(0);
       const T hp[3] = {hz_p, hy_p, hx_p}, hm[3] = {hz_m, hy_m, hx_m};
       const T np_[3] = {pz_p, py_p, px_p}, nm_[3] = {pz_m, py_m, px_m};
@@ -868,6 +924,10 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
       out[i] = s;
     }
     dev::cp_wait<0>();
+    k5 = rj(k5, 1, kC3P);
+    k4 = rj(k4, 1, kC3Vz);
+    k3 = rj(k3, 1, kC3Vq);
+    k2 = rj(k2, 1, kC3M);
   }
 }
 
