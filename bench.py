@@ -43,6 +43,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=REV_STEPS)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--state", choices=["compensated", "plain"], default="compensated",
+                    help="FP32 state of the timed path: compensated (hi + lo, the path that keeps the FP32 "
+                         "error bars over a revolution) or plain")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_SIDE, help="side length of the rotation workload")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / staged / e2e / oracle legs")
@@ -132,7 +135,8 @@ def measured_peaks():
 
 
 KERNEL_NAMES = {1: "k_fused2d", 2: "k_band2d"}
-KERNEL_SOURCES = {"k_fused2d": ("fused2d.cu", "stencil2d.cuh"), "k_band2d": ("band2d.cu", "stencil2d.cuh")}
+KERNEL_SOURCES = {"k_fused2d": ("fused2d.cu", "stencil2d.cuh"), "k_band2d": ("band2d.cu", "stencil2d.cuh"),
+                  "k_fused2d_comp": ("fused2d.cu", "stencil2d.cuh")}
 
 
 def kernel_sources_sha256(kernel):
@@ -163,19 +167,23 @@ def traffic_from_profiles(kernel, n, dtype, key="bytes_per_launch"):
 # from the scheme with every quantity computed once: pass 1 (Eq. 4-5) 12, pseudo-velocities with
 # the cross term (Eq. 6 and its 2D form) 19 per face, FCT bounds, in/out sums and factors 32,
 # limited pseudo-velocities 10, pass 2 12; each of the 6 divisions is a reciprocal + multiply.
-ALU_INST_PER_CELL_STEP = 104
+# The compensated state adds, per donor pass, four error-free two-sums (7 instructions each
+# instead of one add) and the renormalisation (6), and in pass 1 the low parts' own fluxes (8)
+# and their sum (1): 104 + 2 x (24 + 6) + 9 = 173.
+ALU_INST_PER_CELL_STEP = {"plain": 104, "compensated": 173}
 
 
-def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count):
+def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count, state="plain"):
     """The second bound of the step: FP32 lane-instructions against the SMs' issue rate
     (4 schedulers x 32 lanes per SM per clock at the highest SM clock)."""
     if dtype != "f32" or not sm_max_mhz:
         return None
     peak = sm_count * 128 * sm_max_mhz * 1e6 / 1e12
-    achieved = ALU_INST_PER_CELL_STEP * cells / seconds_per_step / 1e12
+    inst = ALU_INST_PER_CELL_STEP[state]
+    achieved = inst * cells / seconds_per_step / 1e12
     warp_inst = traffic_from_profiles(kernel, n, dtype, "smsp__inst_executed.sum")
     out = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tinst/s",
-           "frac": round(achieved / peak, 4), "algorithmic_inst_per_cell_step": ALU_INST_PER_CELL_STEP,
+           "frac": round(achieved / peak, 4), "algorithmic_inst_per_cell_step": inst,
            "peak_source": f"{sm_count} SMs x 128 lanes x {sm_max_mhz:.0f} MHz",
            "executed_lane_slots_per_cell_step": None, "issue_frac_of_executed": None}
     if warp_inst:
@@ -275,6 +283,47 @@ def partition_fields(sizes, world_size):
 
 # ----------------------------------------------------------------------------------- ours
 
+def _split(x):
+    """FP64 field -> FP32 pair (hi, lo) with hi + lo = x to ~1e-14 relative."""
+    import numpy as np
+    hi = x.astype(np.float32)
+    return hi, (x - hi.astype(np.float64)).astype(np.float32)
+
+
+def one_revolution_errors(n, psi_np, gc_np, dev, steps):
+    """Both FP32 states over `steps` steps (one revolution) against the FP64 GPU path from the
+    same input (which matches the FP64 oracle to 1e-12): relative L2 error and relative mass
+    drift of each, with the same inputs rounded to FP32 for the FP32 paths."""
+    import numpy as np
+    import torch
+
+    from paper_1407_1309_gb300 import capi
+    from paper_1407_1309_gb300.solver import Mpdata
+    out = {"steps": steps, "vs": "FP64 GPU path from the same input (equal to the FP64 oracle to 1e-12)"}
+    with Mpdata((n, n), dtype=torch.float64, n_iters=2, opts=capi.FCT, device=dev) as m64:
+        a = torch.tensor(psi_np, dtype=torch.float64, device=dev)
+        b = torch.empty_like(a)
+        m64.advance(a, b, [torch.tensor(v, dtype=torch.float64, device=dev) for v in gc_np], n_steps=steps)
+        ref = b.cpu().numpy()
+    m0 = psi_np.sum()
+    g32 = [torch.tensor(v.astype(np.float32), device=dev) for v in gc_np]
+    with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as m:
+        a = torch.tensor(psi_np.astype(np.float32), device=dev)
+        b = torch.empty_like(a)
+        m.advance(a, b, g32, n_steps=steps)
+        plain = b.double().cpu().numpy()
+        hi, lo = (torch.tensor(x, device=dev) for x in _split(psi_np))
+        ho, lo2 = torch.empty_like(hi), torch.empty_like(lo)
+        m.advance_compensated(hi, lo, ho, lo2, g32, n_steps=steps)
+        comp = ho.double().cpu().numpy() + lo2.double().cpu().numpy()
+    for name, x in (("compensated", comp), ("plain", plain)):
+        out[name] = {"rel_l2": float(np.linalg.norm(x - ref) / np.linalg.norm(ref)),
+                     "rel_mass_drift": float(abs(x.sum() - m0) / abs(m0)),
+                     "meets_fp32_bars": bool(np.linalg.norm(x - ref) <= 1e-5 * np.linalg.norm(ref) and
+                                             abs(x.sum() - m0) <= 1e-6 * abs(m0))}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -289,50 +338,73 @@ def run_ours(args):
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
     dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    comp = dtype == torch.float32 and args.state == "compensated"
+    state = "compensated" if comp else "plain"
     esize = 4 if dtype == torch.float32 else 8
     n = args.n
     cells = n * n
     psi_np, gc_np, _ = workloads.rotation_2d(n, REV_STEPS if n == N_SIDE else None)
     psi0 = torch.tensor(psi_np, dtype=dtype, device=dev)
     gc = [torch.tensor(v, dtype=dtype, device=dev) for v in gc_np]
-    a, b = psi0.clone(), torch.empty_like(psi0)
+    if comp:
+        hi_np, lo_np = _split(psi_np)
+        hi0, lo0 = torch.tensor(hi_np, device=dev), torch.tensor(lo_np, device=dev)
+        a, al = hi0.clone(), lo0.clone()
+        b, bl = torch.empty_like(a), torch.empty_like(al)
+    else:
+        a, b = psi0.clone(), torch.empty_like(psi0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     m = Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev)
     stream = torch.cuda.current_stream(dev)
     if args.kernel:
-        choice = (1 if args.kernel == "warp" else 2, args.tile_rows)
+        choice = (1 if args.kernel == "warp" or comp else 2, args.tile_rows)
         m.tune(capi.TUNE_KERNEL, choice[0])
         m.tune(capi.TUNE_TILE_ROWS, choice[1])
     elif args.no_tune:
         choice = None
     else:  # kernel family and tile height for this workload, timed on these buffers (not cached)
         from paper_1407_1309_gb300 import autotune
-        choice, _, _ = autotune.autotune(m, a, gc, steps=8, use_cache=False)
-    tuned = {"kernel": KERNEL_NAMES[choice[0]], "tile_rows": choice[1],
-             "chosen_by": "command line" if args.kernel else "autotuner"} \
-        if choice else {"kernel": "automatic", "chosen_by": "library default"}
+        choice, _, _ = autotune.autotune(m, a, gc, steps=8, use_cache=False, lo=al if comp else None)
+    kname = "k_fused2d_comp" if comp else (KERNEL_NAMES[choice[0]] if choice else "automatic")
+    tuned = {"kernel": kname, "tile_rows": choice[1] if choice else 0,
+             "chosen_by": "command line" if args.kernel else ("autotuner" if choice else "library default")}
 
     def timed(K, flush_l2=True):
         # arguments marshalled once per direction, so the host enqueues a step faster than the
         # device runs flush + step and no host gap falls between the events
         nonlocal a, b
-        calls = {(a.data_ptr(), b.data_ptr()): capi.prepare_advance(m.h, a, b, gc),
-                 (b.data_ptr(), a.data_ptr()): capi.prepare_advance(m.h, b, a, gc)}
+        if comp:
+            nonlocal al, bl
+            calls = {a.data_ptr(): capi.prepare_advance_compensated(m.h, a, al, b, bl, gc),
+                     b.data_ptr(): capi.prepare_advance_compensated(m.h, b, bl, a, al, gc)}
+        else:
+            calls = {a.data_ptr(): capi.prepare_advance(m.h, a, b, gc),
+                     b.data_ptr(): capi.prepare_advance(m.h, b, a, gc)}
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for e0, e1 in evs:
             if flush_l2:
                 flush.zero_()
             e0.record(stream)
-            calls[(a.data_ptr(), b.data_ptr())]()
+            calls[a.data_ptr()]()
             e1.record(stream)
             a, b = b, a
+            if comp:
+                al, bl = bl, al
         torch.cuda.synchronize(dev)
         return sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
 
     for _ in range(args.warmup):
-        m.advance(a, b, gc)
+        if comp:
+            m.advance_compensated(a, al, b, bl, gc)
+            al, bl = bl, al
+        else:
+            m.advance(a, b, gc)
         a, b = b, a
-    a.copy_(psi0)
+    if comp:
+        a.copy_(hi0)
+        al.copy_(lo0)
+    else:
+        a.copy_(psi0)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -346,34 +418,39 @@ def run_ours(args):
     secs = max_over_ranks(secs, dev)
     if ws > 1:
         dist.barrier()
-    result_after_K = a.double().cpu().numpy()
+    result_after_K = a.double().cpu().numpy() + (al.double().cpu().numpy() if comp else 0.0)
     value = job_value(cells, args.steps, ws, secs)
     ms_per_step = secs / args.steps * 1e3
 
     peaks, how = measured_peaks()
-    bytes_per_cell = 4 * esize  # read psi, gc0, gc1; write psi
+    # read psi (and lo), gc0, gc1; write psi (and lo)
+    bytes_per_cell = (6 if comp else 4) * esize
     achieved = bytes_per_cell * cells / (secs / args.steps) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": traffic_from_profiles(tuned["kernel"], n, args.dtype),
+                "traffic": traffic_from_profiles(kname, n, args.dtype),
                 "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs, burst copy)" if how == "measured" else "fallback",
-                "algorithmic_bytes_per_cell_step": bytes_per_cell, "kernel": tuned["kernel"]}
+                "algorithmic_bytes_per_cell_step": bytes_per_cell, "kernel": kname}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
            "data": "synthetic (seeded rotating-cone workload, no dataset)",
-           "config": config(args, {"wall_s_timed_region_incl_flushes": round(wall, 3), "kernel": tuned}),
+           "config": config(args, {"wall_s_timed_region_incl_flushes": round(wall, 3), "kernel": tuned,
+                                   "fp32_state": ("compensated: psi = hi + lo, both FP32 arrays; every quantity "
+                                                  "of the step in FP32" if comp else
+                                                  ("plain FP32" if dtype == torch.float32 else "FP64"))}),
            "roofline": roofline,
-           "alu_roofline": alu_roofline(cells, secs / args.steps, tuned["kernel"], n, args.dtype,
-                                        clk.get("sm_max_mhz"),
-                                        torch.cuda.get_device_properties(dev).multi_processor_count),
+           "alu_roofline": alu_roofline(cells, secs / args.steps, kname, n, args.dtype, clk.get("sm_max_mhz"),
+                                        torch.cuda.get_device_properties(dev).multi_processor_count, state),
            "gpu_launches": args.steps, "clocks": clk}
 
     if rank == 0 and not args.no_extras:
         extras = {}
-        # accuracy of this run's arithmetic: the same K steps in FP64 on the GPU (FP64 path matches
-        # the FP64 oracle to 1e-12), and 10 steps against the oracle itself
+        # accuracy of the headline arithmetic over one full revolution (independent of --steps),
+        # and of this run's K steps against the FP64 GPU path
+        if dtype == torch.float32 and n == N_SIDE:
+            out["err_one_revolution"] = one_revolution_errors(n, psi_np, gc_np, dev, REV_STEPS)
         with Mpdata((n, n), dtype=torch.float64, n_iters=2, opts=capi.FCT, device=dev) as m64:
             p64 = torch.tensor(psi_np, dtype=torch.float64, device=dev)
             g64 = [torch.tensor(v, dtype=torch.float64, device=dev) for v in gc_np]
@@ -382,16 +459,16 @@ def run_ours(args):
             q = torch.empty_like(p64)
             k64 = min(args.steps, 1000)
             t0.record(stream)
-            for s in range(args.steps):
+            for s_ in range(args.steps):
                 m64.advance(p64, q, g64)
                 p64, q = q, p64
-                if s + 1 == k64:
+                if s_ + 1 == k64:
                     t1.record(stream)
             torch.cuda.synchronize(dev)
             s64 = t0.elapsed_time(t1) / 1e3
             ref64 = p64.cpu().numpy()
         e = result_after_K - ref64
-        extras["err_vs_fp64_gpu_after_K_steps"] = {
+        out["err_vs_fp64_gpu_after_K_steps"] = {
             "rel_l2": float(np.linalg.norm(e) / np.linalg.norm(ref64)),
             "max_abs": float(np.abs(e).max()),
             "rel_mass_drift": float(abs(result_after_K.sum() - psi_np.sum()) / abs(psi_np.sum()))}
@@ -400,38 +477,25 @@ def run_ours(args):
         extras["fp64_path"] = {"value": round(cells * k64 / s64 / 1e9, 3), "unit": UNIT, "steps": k64,
                                "l2": "not flushed (ALU-bound: FP64 arithmetic, not HBM, limits it)",
                                "roofline": fp64_roofline(cells * k64 / s64, "2d", rates)}
-        if dtype == torch.float32:
-            # the same K steps on the compensated FP32 state (hi + lo, mpdata_advance_compensated),
-            # from the FP64 initial field split exactly; the first kc steps timed like the headline
-            hi32 = psi_np.astype(np.float32)
-            hi = torch.tensor(hi32, device=dev)
-            lo = torch.tensor((psi_np - hi32.astype(np.float64)).astype(np.float32), device=dev)
-            hn, ln = torch.empty_like(hi), torch.empty_like(lo)
-            kc = min(args.steps, 1000)
-            with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as mc:
-                mc.tune(capi.TUNE_TILE_ROWS, tuned.get("tile_rows", 0) if tuned["kernel"] == "k_fused2d" else 0)
-                evs = []
-                for _ in range(kc):
-                    flush.zero_()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    capi.mpdata_advance_compensated(mc.h, hi, lo, hn, ln, gc)
-                    e1.record(stream)
-                    evs.append((e0, e1))
-                    hi, hn, lo, ln = hn, hi, ln, lo
-                if args.steps > kc:
-                    capi.mpdata_advance_compensated(mc.h, hi, lo, hi, lo, gc, n_steps=args.steps - kc)
-                torch.cuda.synchronize(dev)
-            sc = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
-            got = hi.double().cpu().numpy() + lo.double().cpu().numpy()
-            ec = got - ref64
-            extras["fp32_compensated_state"] = {
-                "value": round(cells * kc / sc / 1e9, 3), "unit": UNIT, "steps_timed": kc,
-                "bytes_per_cell_step": 24, "kernel": "k_fused2d (compensated)",
-                "err_vs_fp64_gpu_after_K_steps": {
-                    "rel_l2": float(np.linalg.norm(ec) / np.linalg.norm(ref64)),
-                    "max_abs": float(np.abs(ec).max()),
-                    "rel_mass_drift": float(abs(got.sum() - psi_np.sum()) / abs(psi_np.sum()))}}
+        if comp:
+            # the plain FP32 state, timed like the headline (autotuned family and tile height)
+            from paper_1407_1309_gb300 import autotune
+            with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as mp:
+                x = psi0.clone()
+                pchoice, _, _ = autotune.autotune(mp, x, gc, steps=8, use_cache=False)
+                kp = min(args.steps, 1000)
+                sp = autotune.time_steps(mp, x, gc, steps=kp)
+                pk = KERNEL_NAMES[pchoice[0]]
+            extras["fp32_plain_state"] = {
+                "value": round(cells / sp / 1e9, 3), "unit": UNIT, "steps_timed": kp,
+                "kernel": {"kernel": pk, "tile_rows": pchoice[1]}, "bytes_per_cell_step": 16,
+                "roofline": {"bound": "hbm", "achieved": round(16 * cells / sp / 1e9, 1), "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": round(16 * cells / sp / 1e9 / peaks["hbm_gbs"], 4),
+                             "traffic": traffic_from_profiles(pk, n, "f32")},
+                "alu_roofline": alu_roofline(cells, sp, pk, n, "f32", clk.get("sm_max_mhz"),
+                                             torch.cuda.get_device_properties(dev).multi_processor_count),
+                "note": "fails the FP32 bars over a revolution (err_one_revolution.plain): the background of "
+                        "1.0 sits on a binade edge, where the rounding of psi + flux divergence is biased"}
         # staged path (one kernel per sub-step) for comparison
         with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT | capi.STAGED, device=dev) as ms:
             x, y = psi0.clone(), torch.empty_like(psi0)
@@ -451,15 +515,21 @@ def run_ours(args):
                                      "kernels_per_step": 6}
         extras["abs_variable_sign"] = bench_abs(psi_np, gc_np, dtype, dev, stream, flush, min(args.steps, 300))
         extras["dfl_divergent_flow"] = bench_dfl(n, dtype, dev, stream, flush, min(args.steps, 300))
-        out["e2e"] = run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
-        def gpu_steps(k):  # this build's step from the same FP32 input, for the oracle leg's comparison
+        out["e2e"] = run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws, comp)
+
+        def gpu_steps(k):  # this build's headline step from the same input, for the oracle leg's comparison
             with Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev) as mm:
+                if comp:
+                    h0, l0 = hi0.clone(), lo0.clone()
+                    h1, l1 = torch.empty_like(h0), torch.empty_like(l0)
+                    mm.advance_compensated(h0, l0, h1, l1, gc, n_steps=k)
+                    return h1.double().cpu().numpy() + l1.double().cpu().numpy()
                 x, y = psi0.clone(), torch.empty_like(psi0)
                 mm.advance(x, y, gc, n_steps=k)
                 return y.double().cpu().numpy()
 
-        out["cpu_baseline"] = cpu_baseline(psi0.double().cpu().numpy(), [v.double().cpu().numpy() for v in gc],
-                                           gpu_steps=gpu_steps)
+        out["cpu_baseline"] = cpu_baseline(psi_np if comp else psi0.double().cpu().numpy(),
+                                           [v.double().cpu().numpy() for v in gc], gpu_steps=gpu_steps)
         out["extras"] = extras
         configs = {}
         for name, fn in (("1d", bench_config1), ("3d", bench_config3), ("ensemble", bench_config4),
@@ -470,7 +540,7 @@ def run_ours(args):
                 configs[name] = {"error": f"{type(ex).__name__}: {str(ex)[:300]}"}
         out["other_configs"] = configs
     elif not args.no_extras:
-        run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws)
+        run_e2e(m, psi_np, gc_np, dtype, dev, stream, min(args.steps, 1000), ws, comp)
     m.close()
     if ws > 1:
         dist.barrier()
@@ -600,26 +670,34 @@ def bench_config1(dev):
             "path": "one launch of one block for all steps (field and intermediates in shared memory; FP64 rate of one SM)"}
 
 
-def bench_config3(dev, n=256, steps=20):
+def bench_config3(dev, n=256, steps=20, oracle_steps=1):
     """3D deformational flow, n^3, G != 1, FP32; n_iters = 3 + tot + fct, and the infinite-gauge
-    variant (n_iters = 2, tot, fct, blobs of +/-1)."""
+    variant (n_iters = 2, tot, fct, blobs of +/-1).  Each variant: FP32 and FP64 timed over
+    `steps` steps; both compared with the FP64 oracle after its first `oracle_steps` steps
+    (every cell), and FP32 with FP64 after all steps."""
     import numpy as np
     import torch
 
+    import oracle
     from paper_1407_1309_gb300 import capi, workloads
     from paper_1407_1309_gb300.solver import Mpdata
     out = {}
     peaks, _ = measured_peaks()
+    rates = measure_fma_rates(dev)
+    oracle.set_threads(0)
     for label, iga in (("n_iters3_tot_fct", False), ("iga_n_iters2_tot_fct", True)):
         psi, gc, G = workloads.deformational_3d(n, iga=iga)
         K = 2 if iga else 3
         opts = capi.TOT | capi.FCT | capi.NUG | (capi.IGA if iga else 0)
         scales = [workloads.deformational_scale(s) for s in range(steps)]
-        res = {}
+        res, first = {}, {}
         for dt in (torch.float32, torch.float64):
             t = lambda x: torch.tensor(x, dtype=dt, device=dev)
             with Mpdata((n, n, n), dtype=dt, n_iters=K, opts=opts, device=dev) as m:
                 a, b, g, Gt = t(psi), torch.empty(n, n, n, dtype=dt, device=dev), [t(v) for v in gc], t(G)
+                m.advance(a, b, g, Gt, None, 0.0, oracle_steps, scales[:oracle_steps])
+                torch.cuda.synchronize(dev)
+                first[dt] = b.double().cpu().numpy()
                 m.advance(a, b, g, Gt, None, 0.0, 2, scales[:2])
                 e0, e1 = _events()
                 e0.record()
@@ -627,20 +705,39 @@ def bench_config3(dev, n=256, steps=20):
                 e1.record()
                 torch.cuda.synchronize(dev)
                 res[dt] = (e0.elapsed_time(e1) / 1e3, b.double().cpu().numpy())
+        # the oracle from the FP64 inputs (FP64 path) and from the FP32-rounded inputs (FP32 path)
+        errs = {}
+        for dt in (torch.float64, torch.float32):
+            r = (lambda x: x.astype(np.float32).astype(np.float64)) if dt == torch.float32 else (lambda x: x)
+            ref = r(psi)
+            for s_ in scales[:oracle_steps]:
+                ref = oracle.step(ref, [r(v) * s_ for v in gc], g=r(G), n_iters=K, opts=int(opts) & ~capi.NUG)
+            got = first[dt]
+            key = "f64" if dt == torch.float64 else "f32"
+            errs[key] = {"max_rel": float(np.abs(got - ref).max() / np.abs(ref).max()),
+                         "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                         "rel_mass_drift": float(abs(got.sum() - ref.sum()) / np.abs(ref).sum())}
         secs32, o32 = res[torch.float32]
         o64 = res[torch.float64][1]
         cells = n ** 3
         bpc = 24  # psi, gc0..2, G read; psi written
         achieved = bpc * cells * steps / secs32 / 1e9
+        v64 = cells * steps / res[torch.float64][0]
         out[label] = {"workload": f"3d_deformational_{n}^3_{label}_G", "steps": steps,
                       "value": round(cells * steps / secs32 / 1e9, 3), "unit": UNIT,
-                      "fp64_value": round(cells * steps / res[torch.float64][0] / 1e9, 3),
+                      "fp64_value": round(v64 / 1e9, 3),
                       "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                                    "algorithmic_bytes_per_cell_step": bpc},
+                      "err_vs_oracle_first_steps": {"steps": oracle_steps, **errs},
                       "err_fp32_vs_fp64_gpu": {"rel_l2": float(np.linalg.norm(o32 - o64) / np.linalg.norm(o64)),
                                                "rel_mass_drift": float(abs(o32.sum() - o64.sum()) / np.abs(o64).sum())},
-                      "path": "staged kernels"}
+                      "path": ("z-march kernels: pass 1 + bounds, then per corrective pass the pseudo-advector "
+                               "and the limited donor pass (5 launches per step)" if not iga else
+                               "z-march kernels: pass 1 + bounds, the pseudo-advector, the limited donor pass "
+                               "(3 launches per step)")}
+        if not iga:
+            out[label]["fp64_roofline"] = fp64_roofline(v64, "3d", rates)
     return out
 
 
@@ -874,19 +971,23 @@ def run_ensemble(args):
             "gpu_launches": args.steps, "clocks": clk}), flush=True)
 
 
-def run_e2e(m, psi_np, gc_np, dtype, dev, stream, K, ws):
+def run_e2e(m, psi_np, gc_np, dtype, dev, stream, K, ws, comp=False):
     """Same metric through the public API with host buffers: every step copies its inputs
-    (psi, gc0, gc1) from pinned host memory and reads its result back into pinned host
-    memory.  The copies of neighbouring steps overlap the step in between: host-to-device
-    copies, steps and device-to-host copies run on three streams over two buffer sets,
-    ordered by events (a buffer set is refilled only after the step and the read-back
-    that used it two steps earlier have finished)."""
+    (psi -- hi and lo for the compensated state --, gc0, gc1) from pinned host memory and reads
+    its result (psi, or hi and lo) back into pinned host memory.  The copies of neighbouring
+    steps overlap the step in between: host-to-device copies, steps and device-to-host copies
+    run on three streams over two buffer sets, ordered by events (a buffer set is refilled only
+    after the step and the read-back that used it two steps earlier have finished)."""
     import torch
-    hp = torch.tensor(psi_np, dtype=dtype).pin_memory()
+    if comp:
+        hi_np, lo_np = _split(psi_np)
+        hstate = [torch.tensor(hi_np).pin_memory(), torch.tensor(lo_np).pin_memory()]
+    else:
+        hstate = [torch.tensor(psi_np, dtype=dtype).pin_memory()]
     hg = [torch.tensor(v, dtype=dtype).pin_memory() for v in gc_np]
-    ho = [torch.empty_like(hp).pin_memory() for _ in range(2)]
-    dp = [torch.empty(hp.shape, dtype=dtype, device=dev) for _ in range(2)]
-    dq = [torch.empty_like(dp[0]) for _ in range(2)]
+    ho = [[torch.empty_like(h).pin_memory() for h in hstate] for _ in range(2)]
+    dp = [[torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hstate] for _ in range(2)]
+    dq = [[torch.empty_like(x) for x in dp[0]] for _ in range(2)]
     dg = [[torch.empty(v.shape, dtype=dtype, device=dev) for v in hg] for _ in range(2)]
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     ev = lambda: torch.cuda.Event()
@@ -901,28 +1002,34 @@ def run_e2e(m, psi_np, gc_np, dtype, dev, stream, K, ws):
         with torch.cuda.stream(s_in):
             if k >= 2:
                 s_in.wait_event(stepped[b])     # step k-2 no longer reads dp[b], dg[b]
-            dp[b].copy_(hp, non_blocking=True)
+            for d, h in zip(dp[b], hstate):
+                d.copy_(h, non_blocking=True)
             for d, h in zip(dg[b], hg):
                 d.copy_(h, non_blocking=True)
             copied[b].record(s_in)
         stream.wait_event(copied[b])
         if k >= 2:
             stream.wait_event(read[b])          # read-back k-2 no longer reads dq[b]
-        m.advance(dp[b], dq[b], dg[b])
+        if comp:
+            m.advance_compensated(dp[b][0], dp[b][1], dq[b][0], dq[b][1], dg[b])
+        else:
+            m.advance(dp[b][0], dq[b][0], dg[b])
         stepped[b].record(stream)
         with torch.cuda.stream(s_out):
             s_out.wait_event(stepped[b])
-            ho[b].copy_(dq[b], non_blocking=True)
+            for h, d in zip(ho[b], dq[b]):
+                h.copy_(d, non_blocking=True)
             read[b].record(s_out)
     s_out.wait_stream(stream)
     s_out.wait_stream(s_in)
     e1.record(s_out)
     torch.cuda.synchronize(dev)
     secs = e0.elapsed_time(e1) / 1e3
-    cells = hp.numel()
-    es = hp.element_size()
+    cells = hstate[0].numel()
+    state_bytes = sum(h.numel() * h.element_size() for h in hstate)
+    gc_bytes = sum(h.numel() * h.element_size() for h in hg)
     return {"value": round(cells * K * ws / secs / 1e9, 4), "unit": UNIT, "steps": K,
-            "h2d_bytes_per_step": 3 * cells * es, "d2h_bytes_per_step": cells * es,
+            "h2d_bytes_per_step": state_bytes + gc_bytes, "d2h_bytes_per_step": state_bytes,
             "overlap": "copies of neighbouring steps overlap the step (3 streams, 2 buffer sets)"}
 
 
@@ -1050,11 +1157,12 @@ def run_deform3d(args, n=256):
             "vs_baseline": None, "dtype": args.dtype, "data": "synthetic (seeded deformational flow, no dataset)",
             "config": {"workload": f"3d_deformational_{n}^3_n_iters3_tot_fct_G", "grid": [n, n, n],
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{ws}",
-                       "path": "staged kernels (one kernel per sub-step)"},
+                       "path": "z-march kernels: pass 1 + bounds, then per corrective pass the pseudo-advector "
+                               "and the limited donor pass"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
                          "algorithmic_bytes_per_cell_step": bpc},
-            "gpu_launches": 10 * args.steps, "clocks": clk}), flush=True)
+            "gpu_launches": (5 if dtype == torch.float32 else 10) * args.steps, "clocks": clk}), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()

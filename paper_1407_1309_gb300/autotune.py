@@ -1,7 +1,8 @@
 """Autotuner: picks the fused 2D kernel family (warp march or band march) and its
 tile height for a handle by timing candidates on the caller's own buffers, and
 remembers the choice in a JSON cache keyed by device, field shapes, element type,
-passes and options.
+passes and options (and whether the step runs on the compensated FP32 state, whose
+kernel is the warp march: only its tile height is searched).
 
 The cache lives in $MPDATA_GB300_TUNE_CACHE, else
 $XDG_CACHE_HOME/mpdata_gb300/autotune.json (~/.cache/... by default).
@@ -77,6 +78,27 @@ def time_steps(solver, psi, gc, g=None, r=None, dt=0.0, steps=20, flush_bytes=25
     return sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3 / steps
 
 
+def time_steps_comp(solver, hi, lo, gc, g=None, r=None, dt=0.0, steps=20, flush_bytes=256 << 20):
+    """time_steps for mpdata_advance_compensated on the state hi + lo."""
+    dev = solver.device
+    stream = torch.cuda.current_stream(dev)
+    a, al = hi.clone(), lo.clone()
+    b, bl = torch.empty_like(hi), torch.empty_like(lo)
+    flush = torch.empty(flush_bytes // 4, dtype=torch.float32, device=dev) if flush_bytes else None
+    solver.advance_compensated(a, al, b, bl, gc, g, r, dt, 2)
+    fwd = capi.prepare_advance_compensated(solver.h, a, al, b, bl, gc, g, r, dt, 1)
+    bwd = capi.prepare_advance_compensated(solver.h, b, bl, a, al, gc, g, r, dt, 1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k, (e0, e1) in enumerate(evs):
+        if flush is not None:
+            flush.zero_()
+        e0.record(stream)
+        (fwd if k % 2 == 0 else bwd)()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3 / steps
+
+
 def _apply(solver, choice):
     kernel, rows = choice
     solver.tune(capi.TUNE_KERNEL, int(kernel))
@@ -84,11 +106,14 @@ def _apply(solver, choice):
 
 
 def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, steps=20, use_cache=True,
-             flush_bytes=256 << 20):
+             flush_bytes=256 << 20, lo=None):
     """Choose (MPDATA_TUNE_KERNEL, MPDATA_TUNE_TILE_ROWS) for `solver` (an Mpdata handle); returns
     ((kernel, tile_rows), seconds per step, {candidate: seconds}).  The handle is left tuned to
-    the winner."""
-    key = key_of(solver)
+    the winner.  With lo (the low parts of a compensated FP32 state psi = hi + lo) the
+    compensated step is timed, over the warp-march candidates."""
+    key = key_of(solver) + ("|compensated" if lo is not None else "")
+    if lo is not None:
+        candidates = tuple(c for c in candidates if c[0] == 1)
     if use_cache:
         with _lock:
             hit = _load_cache().get(key)
@@ -99,7 +124,10 @@ def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, ste
     timings = {}
     for c in candidates:
         _apply(solver, c)
-        timings[c] = time_steps(solver, psi, gc, g, r, dt, steps, flush_bytes)
+        if lo is not None:
+            timings[c] = time_steps_comp(solver, psi, lo, gc, g, r, dt, steps, flush_bytes)
+        else:
+            timings[c] = time_steps(solver, psi, gc, g, r, dt, steps, flush_bytes)
     best = min(timings, key=timings.get)
     _apply(solver, best)
     if use_cache:

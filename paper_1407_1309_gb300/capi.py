@@ -229,6 +229,21 @@ def prepare_advance(h, psi_in, psi_out, gc, g=None, r=None, dt=0.0, n_steps=1):
     return call
 
 
+def prepare_advance_compensated(h, psi_in, lo_in, psi_out, lo_out, gc, g=None, r=None, dt=0.0, n_steps=1):
+    """mpdata_advance_compensated with its arguments marshalled once (as prepare_advance)."""
+    gcp, keep = _ptr_array(gc)
+    fn = load().mpdata_advance_compensated
+    args = (h, _ptr(psi_in), _ptr(lo_in), _ptr(psi_out), _ptr(lo_out), gcp, _ptr(g), _ptr(r), float(dt),
+            int(n_steps), None)
+
+    def call():
+        rc = fn(*args)
+        if rc != 0:
+            _check(rc, "mpdata_advance_compensated")
+    call._keep = keep
+    return call
+
+
 def mpdata_adjoint_step(h, psi_n, gc, g, psi_bar, gc_bar=None, *, raw=False):
     gcp, _k1 = _ptr_array(gc)
     gbp = None

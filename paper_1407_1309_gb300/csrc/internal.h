@@ -188,6 +188,16 @@ cudaError_t trapez_pre(const TrapezMat& m, long long n, T dt, const T* psi, cons
 template <typename T>
 cudaError_t trapez_post(const TrapezMat& m, long long n, T dt, const T* b, T* psi, cudaStream_t st);
 
+// Vectorised FP32 pseudo-advector z-march for 3D fields (march3.cu): launched, and true
+// returned, when the x extent is a multiple of 4 and at least 128, no edge is open and every
+// array is 16-byte aligned; false (nothing launched) otherwise.
+bool antidiff3_vec(const Grid& g, const float* psi, const float* const* v, float vscale, const float* G, bool iga,
+                   bool tot, bool abs_psi, float* const* out, cudaStream_t st);
+
+// Vectorised FP32 pass-1-and-bounds z-march (march3.cu), same conditions.
+bool p1b3_vec(const Grid& g, const float* psi, const float* const* v, float vscale, const float* G, bool kahan,
+              float* p1, float* mx, float* mn, cudaStream_t st);
+
 // FP64 reductions (reduce.cu).  partial: device scratch of at least
 // kRedBlocks * n_fields doubles per output.
 constexpr int kRedBlocks = 256;

@@ -1210,7 +1210,9 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
   // FP32: pass 1 and the bounds in one z-march (FP64 is arithmetic-bound and the z-march
   // recomputes pass 1 on a one-cell halo)
   if (ND == 3 && K >= 2 && o.fct && sizeof(T) == 4 && !o.open) {
-    launch_p1b3<T>(g, p0, gc, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) done = p1b3_vec(g, p0, gc.p, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
+    if (!done) launch_p1b3<T>(g, p0, gc, a.gc_scale, G, o.kahan, s.pa, s.mx, s.mn, st);
   } else {
     k_donor<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, p0, gc, a.gc_scale, false, G, o.kahan, a.r, a.dt,
                                       K == 1 && o.rhs_a, dst1);
@@ -1228,7 +1230,10 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
     T* const* lim = (k % 2 == 0) ? s.va : s.vb;
     Out3<T> vk{{o.fct ? s.vu[0] : lim[0], o.fct ? s.vu[1] : lim[1], o.fct ? s.vu[2] : lim[2]}};
     if (ND == 3 && !o.dfl && !o.open) {
-      launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk, st);
+      bool done = false;
+      if constexpr (sizeof(T) == 4)
+        done = antidiff3_vec(g, prev, vprev.p, vscale, G, o.iga, o.tot, o.abs, vk.p, st);
+      if (!done) launch_antidiff3<T>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, prev, vprev, vscale, G, o.iga, o.tot, o.abs, o.dfl,
                                                          vk);

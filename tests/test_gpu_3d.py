@@ -27,8 +27,9 @@ CASES = {
     "tot3_fct": (3, capi.TOT | capi.FCT),
     "it2_fct": (2, capi.FCT),
 }
-# (z, y, x): x above 32 and ragged, y above 8, z above 16 and ragged
-SEAM_SHAPES = [(37, 19, 70), (17, 9, 33), (33, 17, 65)]
+# (z, y, x): x above 32 and ragged, y above 8, z above 16 and ragged (scalar z-march); x a
+# multiple of 4 above the 64- and 128-cell tiles of the vectorised z-march, the last tile partial
+SEAM_SHAPES = [(37, 19, 70), (17, 9, 33), (33, 17, 65), (37, 19, 136), (17, 9, 260), (21, 11, 68), (18, 3, 4)]
 
 
 def rounded(a, dtype):
