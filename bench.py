@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and time the library's automatic kernel choice")
     ap.add_argument("--n3d", type=int, default=256, help="side length of the deform3d workload")
-    ap.add_argument("--kernel", choices=["warp", "band"], default=None,
+    ap.add_argument("--kernel", choices=["warp", "band", "warp2"], default=None,
                     help="time this fused kernel family (skips the autotuner)")
     ap.add_argument("--tile-rows", type=int, default=0, help="tile / band rows with --kernel (0 = automatic)")
     ap.add_argument("--workload", choices=["rotation", "ensemble", "deform3d", "adjoint"], default="rotation",
@@ -134,9 +134,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-KERNEL_NAMES = {1: "k_fused2d", 2: "k_band2d"}
+KERNEL_NAMES = {1: "k_fused2d", 2: "k_band2d", 3: "k_fused2d_nc2"}
 KERNEL_SOURCES = {"k_fused2d": ("fused2d.cu", "stencil2d.cuh"), "k_band2d": ("band2d.cu", "stencil2d.cuh"),
-                  "k_fused2d_comp": ("fused2d.cu", "stencil2d.cuh")}
+                  "k_fused2d_comp": ("fused2d.cu", "stencil2d.cuh"), "k_fused2d_nc2": ("fused2d.cu", "stencil2d.cuh"),
+                  "k_fused2d_comp_nc2": ("fused2d.cu", "stencil2d.cuh")}
 
 
 def kernel_sources_sha256(kernel):
@@ -193,16 +194,18 @@ def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count
     return out
 
 
-# Algorithmic FP64 operations per cell-step, counted from the same scheme as the FP32 table
-# with the FP64 division the kernels use (approximate reciprocal, two Newton-Raphson steps and
-# a remainder-corrected quotient: 8 FP64 operations instead of 2):
-#   2D (n_iters = 2, FCT, G = 1): 104 - 6 x 2 + 6 x 8 = 140
-#   3D (n_iters = 3 + tot + FCT + G): pass 1 with the bounds 80 (18 flux/update operations,
-#   6 divisions by G, 14 extrema); per corrective pass 612: per face the 1/Gb reciprocal 10,
-#   A 11, its coefficient 4, two cross terms 21 each, the third-order terms 93 (D_dd 23, two
-#   D_dq 21 each, the triple term 28), times three faces, then the FCT factors 48, the
-#   limited advector 18 and the donor pass with its six divisions by G 66.
-FP64_OPS_PER_CELL_STEP = {"2d": 140, "3d": 80 + 2 * 612}
+# Algorithmic FP64 operations per cell-step (adds, multiplies and fused multiply-adds, the work of
+# the FP64 pipe; comparisons and selections not counted), counted from the formulas as the
+# kernels evaluate them, a division being the Newton-Raphson division with remainder correction
+# (7 operations):
+#   2D (n_iters = 2, FCT, G = 1), 94: pass 1 6 (two face fluxes, three flux differences, the
+#   update), pseudo-velocities 29 per face (A and B 9 each, V_q 3, the combination 7, the flux 1),
+#   FCT 24 (in/out sums 8, two factors 8 each), limited fluxes 2, pass 2 4;
+#   3D (n_iters = 3 + tot + FCT + G), 1164: pass 1 72 (six fluxes 3 each, six divisions by G,
+#   six additions, the advector scale), per corrective pass 546: per face 140 (1/Gb 9, A 9, its
+#   coefficient 4, two cross terms 19 each, D_dd with coefficient 25, two D_dq 16 each, the triple
+#   term 23) times three, the factors 48, the limited advector 12, the donor pass 66.
+FP64_OPS_PER_CELL_STEP = {"2d": 94, "3d": 72 + 2 * 546}
 
 
 def measure_fma_rates(dev):
@@ -357,7 +360,8 @@ def run_ours(args):
     m = Mpdata((n, n), dtype=dtype, n_iters=2, opts=capi.FCT, device=dev)
     stream = torch.cuda.current_stream(dev)
     if args.kernel:
-        choice = (1 if args.kernel == "warp" or comp else 2, args.tile_rows)
+        choice = ({"warp": 1, "band": 2, "warp2": 3}[args.kernel] if not comp or args.kernel != "band" else 1,
+                  args.tile_rows)
         m.tune(capi.TUNE_KERNEL, choice[0])
         m.tune(capi.TUNE_TILE_ROWS, choice[1])
     elif args.no_tune:
@@ -365,7 +369,10 @@ def run_ours(args):
     else:  # kernel family and tile height for this workload, timed on these buffers (not cached)
         from paper_1407_1309_gb300 import autotune
         choice, _, _ = autotune.autotune(m, a, gc, steps=8, use_cache=False, lo=al if comp else None)
-    kname = "k_fused2d_comp" if comp else (KERNEL_NAMES[choice[0]] if choice else "automatic")
+    if comp:
+        kname = "k_fused2d_comp_nc2" if choice and choice[0] == 3 else "k_fused2d_comp"
+    else:
+        kname = KERNEL_NAMES[choice[0]] if choice else "automatic"
     tuned = {"kernel": kname, "tile_rows": choice[1] if choice else 0,
              "chosen_by": "command line" if args.kernel else ("autotuner" if choice else "library default")}
 

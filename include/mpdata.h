@@ -260,7 +260,9 @@ int mpdata_clear_stop(mpdata_t h);
  *   0 = automatic (band march where the warp march cannot fill the GPU: FP32
  *   fields with fewer than ~600 warp tiles of 8 rows, FP64 fields whose warp
  *   tiles would be 16 rows or less; warp march otherwise), 1 = warp march,
- *   2 = band march.  Batched handles always use the warp march's persistent kernel.
+ *   2 = band march, 3 = warp march with lanes of 2 columns instead of 4 (FP32; twice
+ *   the warps on a small field; for the FP64 fields, whose lanes already own 2, the warp
+ *   march).  Batched handles always use the warp march's persistent kernel.
  * Returns EINVAL for an unknown knob or value.
  */
 enum { MPDATA_TUNE_TILE_ROWS = 1, MPDATA_TUNE_KERNEL = 2 };

@@ -17,8 +17,10 @@ import torch
 
 from . import capi
 
-# (MPDATA_TUNE_KERNEL, MPDATA_TUNE_TILE_ROWS): warp-march tile heights, band heights
+# (MPDATA_TUNE_KERNEL, MPDATA_TUNE_TILE_ROWS): warp-march tile heights (lanes of 4 and of 2
+# columns), band heights
 CANDIDATES = tuple([(1, r) for r in (0, 6, 8, 12, 16, 24, 32, 48, 64)] +
+                   [(3, r) for r in (6, 8, 12, 16, 24, 32)] +
                    [(2, r) for r in (0, 16, 32, 64, 128, 256)])
 _lock = threading.Lock()
 
@@ -113,7 +115,9 @@ def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, ste
     compensated step is timed, over the warp-march candidates."""
     key = key_of(solver) + ("|compensated" if lo is not None else "")
     if lo is not None:
-        candidates = tuple(c for c in candidates if c[0] == 1)
+        candidates = tuple(c for c in candidates if c[0] in (1, 3))
+    if solver.dtype != torch.float32:
+        candidates = tuple(c for c in candidates if c[0] != 3)
     if use_cache:
         with _lock:
             hit = _load_cache().get(key)

@@ -296,7 +296,8 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
     return MPDATA_ENOMEM;
   }
   mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
-  o.tile_rows = h->kernel == 1 || h->kernel == 0 ? h->tile_rows : 0;  // band heights do not apply
+  o.tile_rows = h->kernel != 2 ? h->tile_rows : 0;  // band heights do not apply
+  o.kernel = h->kernel == 3 ? 3 : 0;
   const float* gcf[3] = {static_cast<const float*>(gc[0]), static_cast<const float*>(gc[1]), nullptr};
   // as in mpdata_advance: the result alternates between the outputs and the ping-pong
   // pair so that the last step lands in (psi_out, lo_out)
@@ -499,7 +500,7 @@ int mpdata_tune(mpdata_t h, int knob, int value) {
     return MPDATA_OK;
   }
   if (knob == MPDATA_TUNE_KERNEL) {
-    if (value < 0 || value > 2) return MPDATA_EINVAL;
+    if (value < 0 || value > 3) return MPDATA_EINVAL;
     h->kernel = value;
     return MPDATA_OK;
   }

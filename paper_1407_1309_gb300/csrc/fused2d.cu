@@ -590,11 +590,11 @@ template int fused_batched_step<double>(const BatchTable&, const Opts&, const do
 namespace {
 
 // Warp-march parameters of one step of one field; *band is set when the automatic choice is
-// the band march.
-template <typename T>
+// the band march.  NC columns per lane: FP32 lanes own 4 (16-byte copies) or, with
+// MPDATA_TUNE_KERNEL = 3, 2 (twice the strips, so twice the warps on a small field), FP64
+// lanes 2 (register budget).
+template <typename T, int NC = (sizeof(T) == 4 ? 4 : 2)>
 F2Params<T> warp_params(const Grid& g, const Opts& o, const StepArgs<T>& a, bool* band) {
-  // FP32 lanes own 4 columns (16-byte copies), FP64 lanes 2 (register budget)
-  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   F2Params<T> p;
   p.psi = a.psi_in;
   p.out = a.psi_out;
@@ -633,10 +633,10 @@ F2Params<T> warp_params(const Grid& g, const Opts& o, const StepArgs<T>& a, bool
   return p;
 }
 
-template <bool FCT, bool NUG>
+template <bool FCT, bool NUG, int NC = 4>
 void launch_comp(const F2Params<float>& p, bool iga, cudaStream_t st) {
-  if (iga) launch<float, 4, FCT, NUG, true, false, true>(p, st);
-  else launch<float, 4, FCT, NUG, false, false, true>(p, st);
+  if (iga) launch<float, NC, FCT, NUG, true, false, true>(p, st);
+  else launch<float, NC, FCT, NUG, false, false, true>(p, st);
 }
 
 }  // namespace
@@ -647,6 +647,10 @@ int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T*, cudaStrea
   if (a.psi_out == a.psi_in) return MPDATA_EUNSUPPORTED;
   constexpr int NC = sizeof(T) == 4 ? 4 : 2;
   bool band_auto = false;
+  if (o.kernel == 3 && sizeof(T) == 4) {  // narrow lanes (FP32)
+    launch_all<T, 2>(warp_params<T, 2>(g, o, a, &band_auto), o, st);
+    return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+  }
   const F2Params<T> p = warp_params(g, o, a, &band_auto);
   if (o.kernel == 2 || (o.kernel == 0 && band_auto)) return band_step<T>(g, o, a, st);
   launch_all<T, NC>(p, o, st);
@@ -658,6 +662,14 @@ int fused_step_comp(const Grid& g, const Opts& o, const StepArgs<float>& a, cons
   if (g.nd != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
   if (a.psi_out == a.psi_in || lo_out == lo_in) return MPDATA_EUNSUPPORTED;
   bool band_auto = false;
+  if (o.kernel == 3 && o.fct && !o.nug) {  // narrow lanes, the common case
+    F2Params<float> p = warp_params<float, 2>(g, o, a, &band_auto);
+    p.lo = lo_in;
+    p.lo_out = lo_out;
+    p.vec = p.vec && al(lo_in, 8) && al(lo_out, 8);
+    launch_comp<true, false, 2>(p, o.iga, st);
+    return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
+  }
   F2Params<float> p = warp_params(g, o, a, &band_auto);  // the warp march carries the low parts
   p.lo = lo_in;
   p.lo_out = lo_out;

@@ -32,10 +32,11 @@ def joined(hi, lo):
     return hi.double().cpu().numpy() + lo.double().cpu().numpy()
 
 
-def run_comp(psi, gc, steps, opts, G=None, R=None, dt=0.0, scale=None, rows=0):
+def run_comp(psi, gc, steps, opts, G=None, R=None, dt=0.0, scale=None, rows=0, kernel=0):
     f = lambda a: None if a is None else torch.tensor(a, dtype=torch.float32, device=DEV)
     o = opts | (capi.NUG if G is not None else 0)
     with Mpdata(psi.shape, dtype=torch.float32, n_iters=2, opts=o) as m:
+        m.tune(capi.TUNE_KERNEL, kernel)
         m.tune(capi.TUNE_TILE_ROWS, rows)
         hi, lo = split(psi)
         ho, lout = torch.empty_like(hi), torch.empty_like(lo)
@@ -61,8 +62,9 @@ OPTS = {"basic": 0, "fct": capi.FCT, "iga_fct": capi.IGA | capi.FCT}
 @pytest.mark.parametrize("shape", [(200, 130), (57, 123), (9, 250)], ids=lambda s: f"{s[0]}x{s[1]}")
 @pytest.mark.parametrize("name", sorted(OPTS))
 @pytest.mark.parametrize("extra", ["plain", "nug", "euler_a", "euler_b"])
-@pytest.mark.parametrize("rows", [0, 5])
-def test_short_run_parity(shape, name, extra, rows):
+@pytest.mark.parametrize("rows,kernel", [(0, 0), (5, 0), (0, 3), (12, 3)], ids=lambda v: str(v))
+def test_short_run_parity(shape, name, extra, rows, kernel):
+    """kernel 3: lanes of 2 columns (taken for FCT without G; other options fall back to 4)."""
     opts = OPTS[name]
     rng = np.random.default_rng(zlib.crc32(repr((shape, name, extra)).encode()))
     gc = [r32(v) for v in nondivergent(shape, rng, 0.35)]
@@ -74,7 +76,7 @@ def test_short_run_parity(shape, name, extra, rows):
     rhs = extra if extra.startswith("euler") else "euler_a"
     o = opts | (capi.RHS_EULER_A if extra == "euler_a" else capi.RHS_EULER_B if extra == "euler_b" else 0)
     dt = float(np.float32(0.1))
-    hi, lo = run_comp(psi, gc, 5, o, G, R, dt, rows=rows)
+    hi, lo = run_comp(psi, gc, 5, o, G, R, dt, rows=rows, kernel=kernel)
     ref = oracle.step(psi, gc, g=G, r=R, dt=dt, n_iters=2, opts=opts, n_steps=5, rhs=rhs)
     got = joined(hi, lo)
     assert np.linalg.norm(got - ref) <= 2e-6 * np.linalg.norm(ref)
@@ -91,6 +93,8 @@ def test_mass_conserved_to_roundoff_of_the_low_parts():
     hi, lo = run_comp(psi, gc, 400, capi.FCT)
     m0 = psi.sum()
     drift_comp = abs(joined(hi, lo).sum() - m0) / m0
+    h2, l2 = run_comp(psi, gc, 400, capi.FCT, kernel=3)  # lanes of 2 columns
+    assert abs(joined(h2, l2).sum() - m0) / m0 <= 1e-11
     drift_plain = abs(run_plain32(r32(psi), gc, 400, capi.FCT).sum() - r32(psi).sum()) / m0
     assert drift_comp <= 1e-11, (drift_comp, drift_plain)
     assert drift_comp < 1e-2 * max(drift_plain, 1e-12)

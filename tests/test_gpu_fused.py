@@ -30,7 +30,8 @@ FUSED_OPTS = {
 
 
 # kernel family (MPDATA_TUNE_KERNEL) and tile / band rows (MPDATA_TUNE_TILE_ROWS)
-KERNELS = {"warp": (1, 0), "band": (2, 0), "band_h5": (2, 5), "band_h64": (2, 64)}
+KERNELS = {"warp": (1, 0), "band": (2, 0), "band_h5": (2, 5), "band_h64": (2, 64), "warp2": (3, 0),
+           "warp2_h12": (3, 12)}
 _ORACLE = {}
 
 
