@@ -189,3 +189,66 @@ def step_trapez(psis, gcs, A, b=None, dt=1.0, n_iters=2, opts=0, n_steps=1, g=No
         new = np.linalg.solve(M, rhs)
         state = [new[e].reshape(state[0].shape) for e in range(E)]
     return state
+
+
+def vip_advector(h, qs, u_prev, dt, dx, eps=1e-8, opened=()):
+    """Prognosed-velocity advector (Sect. 5.1-5.2): velocities u_d = q_d / h where h > eps (else 0)
+    at the cell centres, extrapolated linearly in time to n + 1/2 (1.5 u^n - 0.5 u^{n-1}; u^{n-1} =
+    u^n at the first step, u_prev None), interpolated linearly to the cell walls and turned into
+    Courant numbers (times dt / dx).  Face i+1/2 along d sits at index i (between cells i and
+    i+e_d); along an open dimension the last entry is not an interior face (copied there from the
+    last interior face, never read by the step).  Returns (advector components, u^n)."""
+    u = [np.where(h > eps, q / np.where(h > eps, h, 1.0), 0.0) for q in qs]
+    prev = u if u_prev is None else u_prev
+    gc = []
+    for d, (un, up) in enumerate(zip(u, prev)):
+        ue = 1.5 * un - 0.5 * up
+        right = np.roll(ue, -1, axis=d)
+        c = 0.5 * (ue + right) * (dt / dx)
+        if d in opened:
+            idx = [slice(None)] * ue.ndim
+            idx[d] = -1
+            src = [slice(None)] * ue.ndim
+            src[d] = -2
+            c[tuple(idx)] = c[tuple(src)]
+        gc.append(c)
+    return gc, u
+
+
+def sw_forcing(h, dx, opened=()):
+    """Shallow-water momentum sources of Sect. 5.3-5.4, R_d = -h dh/dx_d (g = 1), the gradient a
+    centred difference (h_{i+e_d} - h_{i-e_d}) / (2 dx); beyond an open edge h is the edge value."""
+    out = []
+    for d in range(h.ndim):
+        hp, hm = np.roll(h, -1, axis=d), np.roll(h, 1, axis=d)
+        if d in opened:
+            first = [slice(None)] * h.ndim
+            first[d] = 0
+            last = [slice(None)] * h.ndim
+            last[d] = -1
+            hm[tuple(first)] = h[tuple(first)]
+            hp[tuple(last)] = h[tuple(last)]
+        out.append(-h * (hp - hm) / (2.0 * dx))
+    return out
+
+
+def step_shallow_water(h, qs, dt, dx, n_iters=2, opts=0, n_steps=1, eps=1e-8, u_prev=None):
+    """Shallow-water system with prognosed velocity (Sect. 5): h_t + div(u h) = 0,
+    (q_d)_t + div(u q_d) = -h dh/dx_d with q_d = u_d h, advanced by the trapezoidal scheme of
+    Sect. 4.1 (Eq. trapez), whose second half is explicit here because h has no source (the
+    footnote of Sect. 5.3): per step the advector at n + 1/2 comes from vip_advector, the momenta
+    get dt/2 R^n, h and the momenta are advected by one MPDATA step each (step(), the given
+    options, G = 1), and the momenta get dt/2 R^{n+1} from the new h.  Open edges as the OPEN
+    bits of opts say.  Returns (h, [q_d], u^n of the last step) for continuing a run."""
+    h = np.array(h, dtype=np.float64)
+    qs = [np.array(q, dtype=np.float64) for q in qs]
+    opened = tuple(d for d in range(h.ndim) if int(opts) & (OPEN0 << d))
+    for _ in range(int(n_steps)):
+        gc, u_prev = vip_advector(h, qs, u_prev, dt, dx, eps, opened)
+        R = sw_forcing(h, dx, opened)
+        qs = [q + 0.5 * dt * r for q, r in zip(qs, R)]
+        h = step(h, gc, n_iters=n_iters, opts=opts)
+        qs = [step(q, gc, n_iters=n_iters, opts=opts) for q in qs]
+        R = sw_forcing(h, dx, opened)
+        qs = [q + 0.5 * dt * r for q, r in zip(qs, R)]
+    return h, qs, u_prev
