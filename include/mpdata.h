@@ -89,7 +89,10 @@ enum {
      R_e = sum_f A_ef psi_f + b_e (mpdata_set_rhs_linear).  R^{n+1} depends on psi^{n+1}, so
      each cell solves (I - dt/2 A) psi^{n+1} = ADV(psi^n + dt/2 R^n) + dt/2 b.  Excludes the two
      Euler bits; mpdata_step / mpdata_advance then take r = NULL and use dt */
-  MPDATA_RHS_TRAPEZ = 65536u
+  MPDATA_RHS_TRAPEZ = 65536u,
+  /* Shallow-water system with prognosed velocity (Sect. 5): the handle's ndims + 1 fields (one
+     shape, G = 1) are the depth h and the momenta q_d = u_d h; advanced by mpdata_sw_advance */
+  MPDATA_SW = 131072u
 };
 
 /* status codes */
@@ -128,6 +131,24 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
  * singular returns EINVAL.
  */
 int mpdata_set_rhs_linear(mpdata_t h, const double* A, const void* b);
+
+/*
+ * Shallow-water system with prognosed velocity (Sect. 5, the drop of Sect. 5.3-5.4): advances
+ * state = [h, q_0, .., q_{ndims-1}] (device, n cells each, the handle's field order) in place by
+ * n_steps steps of
+ *   h_t + div(u h) = 0,   (q_d)_t + div(u q_d) = -h dh/dx_d   (dimensionless, g = 1),
+ * each step: the advector at n+1/2 from the velocities u_d = q_d / h (0 where h <= eps) at n and
+ * n-1, extrapolated linearly (1.5 u^n - 0.5 u^{n-1}; u^{n-1} = u^n at the first step after
+ * creation or mpdata_sw_reset) and interpolated to the cell walls, times dt/dx; then the
+ * trapezoidal scheme (Sect. 4.1) for the momentum sources, centred differences of h, its second
+ * half explicit because h has no source; the MPDATA step of each field with the handle's
+ * options (FCT, ABS, DFL, IGA, OPEN...).  The handle keeps u^{n-1} between calls (allocated on
+ * first use: ENOMEM).  Requires a handle created with MPDATA_SW, n_fields = ndims + 1 of one
+ * shape, without NUG and the source bits (EINVAL otherwise, or for dt, dx <= 0).
+ */
+int mpdata_sw_advance(mpdata_t h, void* state, double dt, double dx, double eps, int n_steps);
+/* Forgets u^{n-1}: the next mpdata_sw_advance step starts a run. */
+int mpdata_sw_reset(mpdata_t h);
 
 /*
  * Advances psi in place by n_steps >= 1 steps (the paper's advance(), Sect. 3.2.5).

@@ -19,6 +19,7 @@ F32, F64 = 0, 1
 FCT, TOT, IGA, NUG, KAHAN, RHS_EULER_A, RHS_EULER_B, STAGED, ABS, DFL = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512
 OPEN0, OPEN1, OPEN2 = 1024, 2048, 4096  # open edges along dimension 0, 1, 2 (Sect. 2.4)
 RHS_TRAPEZ = 65536  # trapezoidal source scheme with sources affine in the state (Sect. 4.1)
+SW = 131072  # shallow-water system with prognosed velocity (Sect. 5)
 OK, EINVAL, EUNSUPPORTED, ECUDA, ECOURANT, ETIMEOUT, ESTOPPED, ENOMEM = range(8)
 
 EXPORTED = (
@@ -27,7 +28,7 @@ EXPORTED = (
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
     "mpdata_advance_compensated", "mpdata_selftest_division", "mpdata_selftest_fma_rate",
     "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay",
-    "mpdata_set_rhs_linear", "mpdata_step_noalloc",
+    "mpdata_set_rhs_linear", "mpdata_step_noalloc", "mpdata_sw_advance", "mpdata_sw_reset",
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
@@ -80,6 +81,8 @@ def load(build_if_needed: bool = True):
             "mpdata_check_courant": ([P, PP, P, DP], I),
             "mpdata_tune": ([P, I, I], I),
             "mpdata_set_rhs_linear": ([P, DP, P], I),
+            "mpdata_sw_advance": ([P, P, D, D, D, I], I),
+            "mpdata_sw_reset": ([P], I),
             "mpdata_set_stream": ([P, P], I),
             "mpdata_request_stop": ([P], I),
             "mpdata_clear_stop": ([P], I),
@@ -201,6 +204,18 @@ def mpdata_set_rhs_linear(h, A, b=None):
     a = np.ascontiguousarray(np.asarray(A, dtype=np.float64)).ravel()
     arr = (ctypes.c_double * max(1, a.size))(*a.tolist())
     _check(load().mpdata_set_rhs_linear(h, arr, _ptr(b)), "mpdata_set_rhs_linear")
+
+
+def mpdata_sw_advance(h, state, dt, dx, eps=1e-8, n_steps=1, *, raw=False):
+    """Shallow-water steps of a MPDATA_SW handle on state = [h, q_0, ..] (one device tensor)."""
+    rc = load().mpdata_sw_advance(h, _ptr(state), float(dt), float(dx), float(eps), int(n_steps))
+    if raw:
+        return rc
+    _check(rc, "mpdata_sw_advance")
+
+
+def mpdata_sw_reset(h):
+    _check(load().mpdata_sw_reset(h), "mpdata_sw_reset")
 
 
 def mpdata_selftest_fma_rate(dtype, iters, sink, stream=None):

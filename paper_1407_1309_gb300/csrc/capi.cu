@@ -38,6 +38,9 @@ struct mpdata_s {
   std::vector<double> rhs_A;
   const void* rhs_b = nullptr;
   void* trapez_buf = nullptr;        // psi^n + dt/2 R^n (total elements, on first use)
+  // shallow-water system: u^{n-1}, extrapolated velocities, advector (3 x nd arrays, first use)
+  void* sw_buf = nullptr;
+  bool sw_first = true;
 };
 
 namespace {
@@ -179,6 +182,7 @@ void free_all(mpdata_s* h) {
   cudaFree(h->pingpong);
   cudaFree(h->pingpong_lo);
   cudaFree(h->trapez_buf);
+  cudaFree(h->sw_buf);
   mpd::adjoint_free(h);
   cudaFree(h->d_spans);
   cudaFree(h->d_partial);
@@ -208,6 +212,67 @@ void handle_tuning(const mpdata_s* h, int* kernel, int* tile_rows) {
 }
 }  // namespace mpd
 
+namespace {
+
+// The shallow-water system (Sect. 5): per step the prognosed advector, the first half of the
+// momentum sources, one MPDATA step of every field with that advector (any kernel family), the
+// second half with the new depth.  The result alternates between the state and the handle's
+// ping-pong buffer so that the last step lands in the state.
+template <typename T>
+int run_sw(mpdata_s* h, T* state, double dt, double dx, double eps, int n_steps) {
+  const mpd::Grid& gr = h->grids[0];
+  const long long n = gr.N;
+  const int nd = h->nd;
+  if (!h->sw_buf && cudaMalloc(&h->sw_buf, static_cast<size_t>(3 * nd) * n * sizeof(T)) != cudaSuccess) {
+    h->sw_buf = nullptr;
+    return MPDATA_ENOMEM;
+  }
+  T* uprev = static_cast<T*>(h->sw_buf);
+  T* ext = uprev + static_cast<long long>(nd) * n;
+  T* adv = ext + static_cast<long long>(nd) * n;
+  mpd::Opts o = mpd::make_opts(h->opts, h->n_iters);
+  o.tile_rows = h->tile_rows;
+  o.kernel = h->kernel;
+  const mpd::StagedScratch<T> ss = mpd::carve_staged<T>(h->staged, h->n_max);
+  T* X = state;
+  T* P = static_cast<T*>(h->pingpong);
+  T* cur = X;
+  if (n_steps % 2 == 1) {
+    if (cudaMemcpyAsync(P, X, sizeof(T) * h->total, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    cur = P;
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
+    T* dst = ((n_steps - 1 - s) % 2 == 0) ? X : P;
+    if (mpd::vip_advector<T>(gr, cur, uprev, ext, adv, h->sw_first, static_cast<T>(eps), static_cast<T>(dt / dx),
+                             h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    h->sw_first = false;
+    if (mpd::sw_force<T>(gr, cur, static_cast<T>(0.5 * dt), static_cast<T>(dx), h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    for (int f = 0; f <= nd; ++f) {
+      mpd::StepArgs<T> a;
+      a.psi_in = cur + static_cast<long long>(f) * n;
+      a.psi_out = dst + static_cast<long long>(f) * n;
+      for (int d = 0; d < 3; ++d) a.gc[d] = d < nd ? adv + static_cast<long long>(d) * n : nullptr;
+      a.g = nullptr;
+      a.r = nullptr;
+      a.dt = static_cast<T>(dt);
+      a.gc_scale = T(1);
+      int rc = o.staged ? MPDATA_EUNSUPPORTED : mpd::fused_step<T>(gr, o, a, nullptr, h->stream);
+      if (rc == MPDATA_EUNSUPPORTED) rc = cuda_status(mpd::staged_step<T>(gr, o, a, ss, h->stream));
+      if (rc != MPDATA_OK) return rc;
+    }
+    if (mpd::sw_force<T>(gr, dst, static_cast<T>(0.5 * dt), static_cast<T>(dx), h->stream) != cudaSuccess)
+      return MPDATA_ECUDA;
+    cur = dst;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
 extern "C" {
 
 int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes, int dtype, int n_iters,
@@ -220,6 +285,14 @@ int mpdata_create(mpdata_t* out, int ndims, int n_fields, const int64_t* shapes,
   if ((opts & MPDATA_IGA) && (opts & (MPDATA_ABS | MPDATA_DFL))) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_EULER_A) && (opts & MPDATA_RHS_EULER_B)) return MPDATA_EINVAL;
   if ((opts & MPDATA_RHS_TRAPEZ) && (opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B))) return MPDATA_EINVAL;
+  if (opts & MPDATA_SW) {  // h and one momentum per dimension, of one shape, G = 1, no other sources
+    if (n_fields != ndims + 1 ||
+        (opts & (MPDATA_NUG | MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_RHS_TRAPEZ)))
+      return MPDATA_EINVAL;
+    for (int f = 1; f < n_fields; ++f)
+      for (int d = 0; d < ndims; ++d)
+        if (shapes[static_cast<long long>(f) * ndims + d] != shapes[d]) return MPDATA_EINVAL;
+  }
   for (long long i = 0; i < static_cast<long long>(n_fields) * ndims; ++i)
     if (shapes[i] < 1 || shapes[i] > (int64_t(1) << 30)) return MPDATA_EINVAL;
   for (int f = 0; f < n_fields; ++f)
@@ -338,6 +411,22 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
   return cuda_status(cudaGetLastError());
 }
 
+int mpdata_sw_advance(mpdata_t h, void* state, double dt, double dx, double eps, int n_steps) {
+  if (!h || !state || n_steps < 1 || !(h->opts & MPDATA_SW) || !(dt > 0.0) || !(dx > 0.0) || !(eps >= 0.0))
+    return MPDATA_EINVAL;
+  if (!aligned(state, h->esize)) return MPDATA_EINVAL;
+  if (h->stop.load()) return MPDATA_ESTOPPED;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32) return run_sw<float>(h, static_cast<float*>(state), dt, dx, eps, n_steps);
+  return run_sw<double>(h, static_cast<double*>(state), dt, dx, eps, n_steps);
+}
+
+int mpdata_sw_reset(mpdata_t h) {
+  if (!h || !(h->opts & MPDATA_SW)) return MPDATA_EINVAL;
+  h->sw_first = true;
+  return MPDATA_OK;
+}
+
 int mpdata_set_rhs_linear(mpdata_t h, const double* A, const void* b) {
   if (!h || !A || !(h->opts & MPDATA_RHS_TRAPEZ)) return MPDATA_EINVAL;
   if (h->n_fields > mpd::kTrapezMax) return MPDATA_EINVAL;
@@ -359,7 +448,7 @@ int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, con
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
                         void* const* gc_bar) {
   if (!h || !psi_bar) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -379,7 +468,7 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
 // Checks shared by the reverse-step entry points: options, fields, a single-field handle.
 static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
   if (!h) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -390,7 +479,7 @@ static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, 
 
 int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes) {
   if (!h || !bytes) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_TOT | MPDATA_ABS | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   if (h->n_fields != 1 || h->n_iters > 4) return MPDATA_EUNSUPPORTED;
   *bytes = mpd::adjoint_tape_bytes(h, h->esize);

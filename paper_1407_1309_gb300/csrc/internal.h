@@ -72,8 +72,9 @@ inline Grid make_grid(int nd, const int64_t* shape, uint32_t opts = 0) {
 // Option bits a handle accepts for nd dimensions; checks shared by mpdata_create and
 // mpdata_step_noalloc.
 inline bool valid_open_bits(int nd, uint32_t opts, const int64_t* shape) {
-  // bits 0 .. 9, the open bits of the nd dimensions and the trapezoidal source scheme
-  const uint32_t all = ((MPDATA_OPEN0 << nd) - 1u) | MPDATA_RHS_TRAPEZ;
+  // bits 0 .. 9, the open bits of the nd dimensions, the trapezoidal source scheme and the
+  // shallow-water system
+  const uint32_t all = ((MPDATA_OPEN0 << nd) - 1u) | MPDATA_RHS_TRAPEZ | MPDATA_SW;
   if (opts & ~all) return false;
   for (int d = 0; d < nd; ++d)
     if ((opts & (MPDATA_OPEN0 << d)) && shape[d] < 2) return false;
@@ -197,6 +198,17 @@ bool antidiff3_vec(const Grid& g, const float* psi, const float* const* v, float
 // Vectorised FP32 pass-1-and-bounds z-march (march3.cu), same conditions.
 bool p1b3_vec(const Grid& g, const float* psi, const float* const* v, float vscale, const float* G, bool kahan,
               float* p1, float* mx, float* mn, cudaStream_t st);
+
+// Prognosed velocity and shallow-water sources (vip.cu).  state: h then the momenta q_d, n cells
+// each.  vip_advector: the advector of the step (adv, nd arrays) from the velocities q/h (h > eps)
+// extrapolated to n + 1/2 (ext: nd scratch arrays; uprev: u^{n-1} in, u^n out, ignored when
+// first) and interpolated to the walls, times courant = dt/dx.  sw_force: q_d += half_dt R_d,
+// R_d = -h dh/dx_d by centred differences.
+template <typename T>
+cudaError_t vip_advector(const Grid& g, const T* state, T* uprev, T* ext, T* adv, bool first, T eps, T courant,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t sw_force(const Grid& g, T* state, T half_dt, T dx, cudaStream_t st);
 
 // FP64 reductions (reduce.cu).  partial: device scratch of at least
 // kRedBlocks * n_fields doubles per output.

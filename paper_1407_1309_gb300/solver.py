@@ -82,6 +82,16 @@ class Mpdata:
         self._rhs_b = b
         capi.mpdata_set_rhs_linear(self.h, A, b)
 
+    def sw_advance(self, state, dt, dx, eps=1e-8, n_steps=1):
+        """Shallow-water system (handles created with SW): state = [h, q_0, ..] concatenated,
+        advanced in place; the handle keeps the previous step's velocities for the next call."""
+        capi.mpdata_sw_advance(self.h, state, dt, dx, eps, n_steps)
+        return state
+
+    def sw_reset(self):
+        """The next sw_advance step starts a new run (no previous velocities)."""
+        capi.mpdata_sw_reset(self.h)
+
     def set_stream(self, stream):
         """Send later work of the handle to `stream` (a torch.cuda.Stream)."""
         capi.mpdata_set_stream(self.h, stream)

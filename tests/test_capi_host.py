@@ -46,6 +46,9 @@ def test_status_strings_and_version():
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.OPEN2),
     dict(ndims=2, shapes=[(4, 1)], dtype=0, n_iters=2, opts=capi.OPEN1),
     dict(ndims=1, shapes=[(4,)], dtype=0, n_iters=2, opts=capi.RHS_TRAPEZ | capi.RHS_EULER_B),
+    dict(ndims=1, shapes=[(4,)], dtype=0, n_iters=2, opts=capi.SW),
+    dict(ndims=1, shapes=[(4,), (5,)], dtype=0, n_iters=2, opts=capi.SW),
+    dict(ndims=1, shapes=[(4,), (4,)], dtype=0, n_iters=2, opts=capi.SW | capi.NUG),
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.DFL | capi.IGA),
     dict(ndims=2, shapes=[(4, 4)], dtype=0, n_iters=2, opts=capi.ABS | capi.IGA),
 ])
@@ -72,7 +75,7 @@ def test_python_and_oracle_constants_match_the_header():
     enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bMPDATA_([A-Z0-9_]+)\s*=\s*(\d+)u?\b", hdr)}
     for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "STAGED", "ABS", "DFL",
                  "F32", "F64", "OK", "EINVAL", "EUNSUPPORTED", "ECUDA", "ECOURANT", "ETIMEOUT", "ESTOPPED", "ENOMEM",
-                 "TUNE_TILE_ROWS", "TUNE_KERNEL", "OPEN0", "OPEN1", "OPEN2", "RHS_TRAPEZ"):
+                 "TUNE_TILE_ROWS", "TUNE_KERNEL", "OPEN0", "OPEN1", "OPEN2", "RHS_TRAPEZ", "SW"):
         assert getattr(capi, name) == enums[name], name
     for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "ABS", "DFL",
                  "OPEN0", "OPEN1", "OPEN2"):
