@@ -540,7 +540,7 @@ def run_ours(args):
         out["extras"] = extras
         configs = {}
         for name, fn in (("1d", bench_config1), ("3d", bench_config3), ("ensemble", bench_config4),
-                         ("adjoint", bench_config5)):
+                         ("adjoint", bench_config5), ("next_rows", bench_next_rows)):
             try:
                 configs[name] = fn(dev)
             except Exception as ex:  # one failing leg must not sink the headline line
@@ -745,6 +745,88 @@ def bench_config3(dev, n=256, steps=20, oracle_steps=1):
                                "(3 launches per step)")}
         if not iga:
             out[label]["fp64_roofline"] = fp64_roofline(v64, "3d", rates)
+    return out
+
+
+def bench_next_rows(dev):
+    """The scope table's later rows on their paper workloads, FP64, each against the oracle:
+    open edges (the hello world of Sect. 3.3: 101 points, 100 steps, the default options), the
+    trapezoidal sources (the translating oscillator of Sect. 4.2: 1000 cells, 1400 steps) and the
+    prognosed-velocity shallow-water system (the 1D drop of Sect. 5.3 to t = 3, and the 2D drop of
+    Sect. 5.4 on 320^2 cells to t = 3 against the paper's closed form).  These workloads are small:
+    their times are launch latency, reported for completeness."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1407_1309_gb300 import capi, workloads
+    from paper_1407_1309_gb300.solver import Mpdata
+    out = {}
+    f64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        e0, e1 = _events()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    # open edges: Sect. 3.3
+    psi, gc = workloads.agnesi_1d()
+    opts = capi.FCT | capi.IGA | capi.KAHAN | capi.OPEN0
+    ref = oracle.step(psi, gc, n_iters=2, opts=int(opts), n_steps=100)
+    with Mpdata((101,), dtype=torch.float64, n_iters=2, opts=opts, device=dev) as m:
+        a, b = f64(psi), torch.empty(101, dtype=torch.float64, device=dev)
+        g = [f64(gc[0])]
+        secs = timed(lambda: m.advance(a, b, g, n_steps=100))
+        got = b.cpu().numpy()
+    out["open_edges_hello_world"] = {"cells": 101, "steps": 100, "time_ms": round(secs * 1e3, 3),
+                                     "max_rel_err_vs_oracle": float(np.abs(got - ref).max() / np.abs(ref).max())}
+    # trapezoidal sources: Sect. 4.2
+    psi0, phi0, gc, omega = workloads.oscillator_1d()
+    A = [[0.0, omega], [-omega, 0.0]]
+    opts = capi.FCT | capi.IGA | capi.KAHAN | capi.RHS_TRAPEZ
+    ref = np.stack(oracle.step_trapez([psi0, phi0], gc, A, dt=1.0, n_iters=2, opts=int(opts & ~capi.RHS_TRAPEZ),
+                                      n_steps=1400))
+    with Mpdata([(1000,), (1000,)], dtype=torch.float64, n_iters=2, opts=opts, device=dev) as m:
+        st = torch.cat([f64(psi0), f64(phi0)])
+        o = torch.empty_like(st)
+        g = [torch.cat([f64(gc[0])] * 2)]
+        m.set_rhs_linear(A)
+        secs = timed(lambda: m.advance(st, o, g, dt=1.0, n_steps=1400))
+        got = o.cpu().numpy().reshape(2, 1000)
+    out["trapez_oscillator"] = {"cells": 1000, "equations": 2, "steps": 1400, "time_ms": round(secs * 1e3, 3),
+                                "max_rel_err_vs_oracle": float(np.abs(got - ref).max() / np.abs(ref).max()),
+                                "phase_after_one_period": {"max_abs_phi": float(np.abs(got[1]).max())}}
+    # shallow water: Sect. 5.3 (1D) and 5.4 (2D)
+    for nd, n, dx, dt, steps in ((1, 320, 0.05, 0.01, 300), (2, 320, 0.05, 0.01, 300)):
+        c = -0.5 * n * dx + (np.arange(n) + 0.5) * dx
+        if nd == 1:
+            h0 = np.where(np.abs(c) <= 1.0, 1.0 - c ** 2, 0.0)
+        else:
+            X, Y = np.meshgrid(c, c, indexing="ij")
+            h0 = np.maximum(1.0 - X ** 2 - Y ** 2, 0.0)
+        opts = capi.ABS | capi.FCT | capi.DFL | sum(capi.OPEN0 << d for d in range(nd))
+        with Mpdata([h0.shape] * (nd + 1), dtype=torch.float64, n_iters=2, opts=opts | capi.SW, device=dev) as m:
+            state = torch.cat([f64(h0).flatten()] + [torch.zeros(h0.size, dtype=torch.float64, device=dev)] * nd)
+            secs = timed(lambda: m.sw_advance(state, dt, dx, n_steps=steps))
+            got = state.cpu().numpy().reshape(nd + 1, *h0.shape)
+        res = {"cells": int(h0.size), "steps": steps, "time_ms": round(secs * 1e3, 3),
+               "value": round(h0.size * steps / secs / 1e9, 4), "unit": UNIT}
+        if nd == 1:
+            h, qs, _ = oracle.step_shallow_water(h0, [np.zeros_like(h0)], dt, dx, n_iters=2, opts=int(opts),
+                                                 n_steps=steps)
+            want = np.stack([h] + qs)
+            res["max_rel_err_vs_oracle"] = float(np.abs(got - want).max() / np.abs(want).max())
+        else:
+            lam = math.sqrt(2 * (steps * dt) ** 2 + 1)
+            ha = np.maximum(1 / lam ** 2 - (X ** 2 + Y ** 2) / lam ** 4, 0.0)
+            res["rel_l2_err_h_vs_closed_form"] = float(np.linalg.norm(got[0] - ha) / np.linalg.norm(ha))
+            res["depth_conservation_rel"] = float(abs(got[0].sum() - h0.sum()) / h0.sum())
+        out[f"shallow_water_{nd}d_drop"] = res
     return out
 
 
