@@ -368,7 +368,11 @@ def run_ours(args):
         choice = None
     else:  # kernel family and tile height for this workload, timed on these buffers (not cached)
         from paper_1407_1309_gb300 import autotune
-        choice, _, _ = autotune.autotune(m, a, gc, steps=8, use_cache=False, lo=al if comp else None)
+        # one step per timed launch (the fusion depths, never faster here, are compared in the
+        # fusion_depth leg)
+        one_step = tuple(c for c in autotune.CANDIDATES if c[2] == 1)
+        choice, _, _ = autotune.autotune(m, a, gc, candidates=one_step, steps=8, use_cache=False,
+                                         lo=al if comp else None)
     if comp:
         kname = "k_fused2d_comp_nc2" if choice and choice[0] == 3 else "k_fused2d_comp"
     else:
@@ -489,7 +493,9 @@ def run_ours(args):
             from paper_1407_1309_gb300 import autotune
             with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as mp:
                 x = psi0.clone()
-                pchoice, _, _ = autotune.autotune(mp, x, gc, steps=8, use_cache=False)
+                pchoice, _, _ = autotune.autotune(mp, x, gc, candidates=tuple(c for c in autotune.CANDIDATES
+                                                                              if c[2] == 1),
+                                                  steps=8, use_cache=False)
                 kp = min(args.steps, 1000)
                 sp = autotune.time_steps(mp, x, gc, steps=kp)
                 pk = KERNEL_NAMES[pchoice[0]]
@@ -540,7 +546,8 @@ def run_ours(args):
         out["extras"] = extras
         configs = {}
         for name, fn in (("1d", bench_config1), ("3d", bench_config3), ("ensemble", bench_config4),
-                         ("adjoint", bench_config5), ("next_rows", bench_next_rows)):
+                         ("adjoint", bench_config5), ("next_rows", bench_next_rows),
+                         ("fusion_depth", bench_fusion_depth)):
             try:
                 configs[name] = fn(dev)
             except Exception as ex:  # one failing leg must not sink the headline line
@@ -745,6 +752,33 @@ def bench_config3(dev, n=256, steps=20, oracle_steps=1):
                                "(3 launches per step)")}
         if not iga:
             out[label]["fp64_roofline"] = fp64_roofline(v64, "3d", rates)
+    return out
+
+
+def bench_fusion_depth(dev, sizes=(1024, 4096)):
+    """Temporal blocking against one step per launch: the rotation workload (FCT, two passes,
+    plain FP32 state) at each size, timed by the autotuner over every candidate (L2 flushed before
+    each launch; a launch at depth S runs S steps and its time counts for S steps), with the
+    oracle-checked parity of every depth in the GPU tests.  Reports Gcell-steps/s of the best
+    one-step-per-launch kernel and of each depth, and the autotuner's pick."""
+    import torch
+
+    from paper_1407_1309_gb300 import autotune, capi, workloads
+    from paper_1407_1309_gb300.solver import Mpdata
+    out = {"how": "autotune.time_steps: per launch after a 256 MiB L2 flush, CUDA events, 12 launches"}
+    for n in sizes:
+        psi_np, gc_np, _ = workloads.rotation_2d(n)
+        psi = torch.tensor(psi_np, dtype=torch.float32, device=dev)
+        gc = [torch.tensor(v, dtype=torch.float32, device=dev) for v in gc_np]
+        with Mpdata((n, n), dtype=torch.float32, n_iters=2, opts=capi.FCT, device=dev) as m:
+            best, sec, timings = autotune.autotune(m, psi, gc, steps=12, use_cache=False)
+        one = min((v, c) for c, v in timings.items() if c[2] == 1)
+        rate = lambda s_: round(n * n / s_ / 1e9, 2)
+        out[f"{n}x{n}"] = {"one_step_per_launch": {"value": rate(one[0]), "kernel": KERNEL_NAMES.get(one[1][0], "auto"),
+                                                   "tile_rows": one[1][1]},
+                           "depth": {str(d): rate(timings[(0, 0, d)]) for d in (2, 3, 4) if (0, 0, d) in timings},
+                           "autotuner_pick": {"kernel": best[0], "tile_rows": best[1], "steps_per_launch": best[2]},
+                           "unit": UNIT}
     return out
 
 

@@ -284,9 +284,16 @@ int mpdata_clear_stop(mpdata_t h);
  *   2 = band march, 3 = warp march with lanes of 2 columns instead of 4 (FP32; twice
  *   the warps on a small field; for the FP64 fields, whose lanes already own 2, the warp
  *   march).  Batched handles always use the warp march's persistent kernel.
+ * MPDATA_TUNE_STEPS_PER_LAUNCH: fusion depth S (temporal blocking): 0 or 1 = one step per
+ *   launch; 2..4 = mpdata_advance runs its steps in groups of S per launch (the last group
+ *   the remainder), each block loading its tile with a 3S-cell halo into shared memory once and
+ *   taking it through the S steps there (Eqs. 4-6 with the cross term, FCT, infinite gauge;
+ *   same arithmetic as the warp march).  Covers single 2D fields with n_iters = 2, G = 1, no
+ *   sources, periodic edges, no third-order, |psi| or divergent-flow terms, no Kahan
+ *   summation; other handles and steps ignore it.  FP64: S <= 4 as for FP32.
  * Returns EINVAL for an unknown knob or value.
  */
-enum { MPDATA_TUNE_TILE_ROWS = 1, MPDATA_TUNE_KERNEL = 2 };
+enum { MPDATA_TUNE_TILE_ROWS = 1, MPDATA_TUNE_KERNEL = 2, MPDATA_TUNE_STEPS_PER_LAUNCH = 3 };
 int mpdata_tune(mpdata_t h, int knob, int value);
 
 /* Sends the handle's later work to cuda_stream (a cudaStream_t on the handle's

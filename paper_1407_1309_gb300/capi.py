@@ -32,6 +32,7 @@ EXPORTED = (
 )
 TUNE_TILE_ROWS = 1
 TUNE_KERNEL = 2
+TUNE_STEPS_PER_LAUNCH = 3
 
 
 class MpdataError(RuntimeError):

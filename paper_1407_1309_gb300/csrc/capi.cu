@@ -32,6 +32,7 @@ struct mpdata_s {
   void* batch = nullptr;             // batched-kernel tables
   int tile_rows = 0;                 // MPDATA_TUNE_TILE_ROWS
   int kernel = 0;                    // MPDATA_TUNE_KERNEL
+  int steps_per_launch = 0;          // MPDATA_TUNE_STEPS_PER_LAUNCH
   std::atomic<int> stop{0};
   // trapezoidal source scheme: R = A psi + b over the fields (mpdata_set_rhs_linear)
   bool rhs_lin = false;
@@ -112,6 +113,27 @@ int run_advance(mpdata_s* h, const T* psi_in, T* psi_out, const void* const* gcv
   T* X = psi_out;
   T* P = static_cast<T*>(h->pingpong);
   const T* cur = psi_in;
+  // temporal blocking: groups of up to steps_per_launch steps, one launch each, the results
+  // alternating between psi_out and the ping-pong buffer as for single steps
+  const int depth = h->steps_per_launch;
+  if (depth > 1 && h->n_fields == 1 && !o.staged && n_steps > 1 && mpd::tblock_covers<T>(h->grids[0], o, depth)) {
+    const int n_groups = (n_steps + depth - 1) / depth;
+    if (psi_in == psi_out && n_groups % 2 == 1) {
+      if (cudaMemcpyAsync(P, X, sizeof(T) * h->total, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return MPDATA_ECUDA;
+      cur = P;
+    }
+    for (int k = 0, s = 0; k < n_groups; ++k, s += depth) {
+      if (h->stop.load(std::memory_order_relaxed)) return MPDATA_ESTOPPED;
+      const int d = n_steps - s < depth ? n_steps - s : depth;
+      T* dst = ((n_groups - 1 - k) % 2 == 0) ? X : P;
+      const int rc = mpd::tblock_steps<T>(h->grids[0], o, cur, dst, gc[0], gc[1], d, gc_scale ? gc_scale + s : nullptr,
+                                          h->stream);
+      if (rc != MPDATA_OK) return rc;
+      cur = dst;
+    }
+    return cuda_status(cudaGetLastError());
+  }
   if (psi_in == psi_out && n_steps % 2 == 1) {
     if (cudaMemcpyAsync(P, X, sizeof(T) * h->total, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
       return MPDATA_ECUDA;
@@ -591,6 +613,11 @@ int mpdata_tune(mpdata_t h, int knob, int value) {
   if (knob == MPDATA_TUNE_KERNEL) {
     if (value < 0 || value > 3) return MPDATA_EINVAL;
     h->kernel = value;
+    return MPDATA_OK;
+  }
+  if (knob == MPDATA_TUNE_STEPS_PER_LAUNCH) {
+    if (value < 0 || value > mpd::kTblockMaxDepth) return MPDATA_EINVAL;
+    h->steps_per_launch = value;
     return MPDATA_OK;
   }
   return MPDATA_EINVAL;

@@ -24,6 +24,17 @@ void handle_tuning(const mpdata_s* h, int* kernel, int* tile_rows);
 // MPDATA_EUNSUPPORTED when the field / options are not covered, so the caller
 // runs the staged path.  tmp: device buffer of the field's size, used when the
 // step is in place.
+// Temporal blocking (tblock2d.cu): `depth` steps of one 2D field (n_iters = 2, FCT and infinite
+// gauge or not, G = 1, no sources, periodic) in one launch, psi_in -> psi_out (distinct
+// buffers), scales[k] the advector factor of step k (nullptr: 1).  tblock_covers says whether
+// the field, options and depth are covered; tblock_steps returns MPDATA_EUNSUPPORTED where not.
+constexpr int kTblockMaxDepth = 4;
+template <typename T>
+bool tblock_covers(const Grid& g, const Opts& o, int depth);
+template <typename T>
+int tblock_steps(const Grid& g, const Opts& o, const T* psi_in, T* psi_out, const T* gc0, const T* gc1, int depth,
+                 const double* scales, cudaStream_t st);
+
 template <typename T>
 int fused_step(const Grid& g, const Opts& o, const StepArgs<T>& a, T* tmp, cudaStream_t st);
 

@@ -75,7 +75,7 @@ def test_python_and_oracle_constants_match_the_header():
     enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bMPDATA_([A-Z0-9_]+)\s*=\s*(\d+)u?\b", hdr)}
     for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "STAGED", "ABS", "DFL",
                  "F32", "F64", "OK", "EINVAL", "EUNSUPPORTED", "ECUDA", "ECOURANT", "ETIMEOUT", "ESTOPPED", "ENOMEM",
-                 "TUNE_TILE_ROWS", "TUNE_KERNEL", "OPEN0", "OPEN1", "OPEN2", "RHS_TRAPEZ", "SW"):
+                 "TUNE_TILE_ROWS", "TUNE_KERNEL", "TUNE_STEPS_PER_LAUNCH", "OPEN0", "OPEN1", "OPEN2", "RHS_TRAPEZ", "SW"):
         assert getattr(capi, name) == enums[name], name
     for name in ("FCT", "TOT", "IGA", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "ABS", "DFL",
                  "OPEN0", "OPEN1", "OPEN2"):
