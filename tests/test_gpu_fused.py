@@ -110,7 +110,7 @@ def test_fused_time_dependent_advector(shape, kernel):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
-@pytest.mark.parametrize("kernel", ["warp", "band"])
+@pytest.mark.parametrize("kernel", ["warp", "band", "warp2"])
 def test_rotation_1024_short_run(dtype, kernel):
     """Full-size 2D rotation workload (1024^2, FCT, two passes) for 10 steps in the
     launch configuration the benchmark times, against the oracle element by element."""
@@ -142,8 +142,9 @@ def test_kernel_families_agree(name, dtype):
     band = run("band")
     for k in ("band_h5", "band_h64"):
         assert np.array_equal(run(k), band)
-    warp = run("warp")
-    if dtype == torch.float64:
-        assert np.abs(warp - band).max() <= 1e-14 * np.abs(band).max()
-    else:
-        assert np.linalg.norm(warp - band) <= 1e-6 * np.linalg.norm(band)
+    for k in ("warp", "warp2"):  # lanes of 4 (FP64: 2) and of 2 columns
+        warp = run(k)
+        if dtype == torch.float64:
+            assert np.abs(warp - band).max() <= 1e-14 * np.abs(band).max(), k
+        else:
+            assert np.linalg.norm(warp - band) <= 1e-6 * np.linalg.norm(band), k
