@@ -301,3 +301,66 @@ def test_fused_tape_matches_staged_tape(shape, opts, family, dtype):
         scale = max(np.abs(ref[j]).max(), 1e-30)
         tol = (1e-3 if j >= 7 else 1e-5) if f32 else (1e-9 if j >= 7 else 1e-13)  # factors: small flux sums
         assert np.abs(fused[j] - ref[j]).max() <= tol * max(scale, 1.0), j
+
+
+@pytest.mark.parametrize("shape", [(70, 45), (33, 97), (5, 200), (130, 3)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", ["basic", "fct"])
+def test_adjoint_matches_oracle_on_larger_2d_fields(shape, name):
+    """2D fields of several thread blocks with ragged edges, and fields narrower than the
+    stencil: FP64 against the oracle adjoint to 1e-12, FP32 (inputs rounded to FP32) to 1e-5
+    relative L2."""
+    n_iters, opts = CASES[name]
+    rng = np.random.default_rng(sum(shape) + n_iters)
+    psi = smooth_positive(shape, rng)
+    gc = nondivergent(shape, rng, 0.35)
+    y = rng.normal(size=shape)
+    dev = torch.device("cuda")
+    for dtype in (torch.float64, torch.float32):
+        r = (lambda a: a) if dtype == torch.float64 else (lambda a: a.astype(np.float32).astype(np.float64))
+        p_, g_, y_ = r(psi), [r(v) for v in gc], r(y)
+        ref_pb, ref_gcb = oracle.adj_step(p_, g_, y_, n_iters=n_iters, opts=opts)
+        t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
+        with Mpdata(shape, dtype=dtype, n_iters=n_iters, opts=opts) as m:
+            pb = t(y_)
+            gcb = [torch.full(shape, 0.5, dtype=dtype, device=dev) for _ in shape]
+            m.adjoint_step(t(p_), [t(v) for v in g_], pb, gc_bar=gcb)
+            torch.cuda.synchronize()
+            got_pb = pb.double().cpu().numpy()
+            got_gcb = [v.double().cpu().numpy() - 0.5 for v in gcb]
+        if dtype == torch.float64:
+            scale = max(np.abs(ref_pb).max(), max(np.abs(v).max() for v in ref_gcb))
+            assert np.abs(got_pb - ref_pb).max() <= 1e-12 * scale
+            for a, b in zip(got_gcb, ref_gcb):
+                assert np.abs(a - b).max() <= 1e-12 * scale
+        else:
+            assert np.linalg.norm(got_pb - ref_pb) <= 1e-5 * np.linalg.norm(ref_pb)
+            for a, b in zip(got_gcb, ref_gcb):
+                assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", ["basic", "fct"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_reverse_from_fused_tape_matches_staged_tape_512(name, dtype):
+    """The reverse step on the 512^2 adjoint workload from the tape the fused step kernel
+    records against the one the staged kernels record (MPDATA_STAGED): FP64 to 1e-12 (max-norm,
+    relative to the largest adjoint), FP32 to 1e-5 relative L2 (the two FP32 tapes differ by
+    rounding, which the ratios of Eq. 6 amplify where psi1 + psi1' is small)."""
+    n_iters, opts = CASES[name]
+    psi0_np, gc_np, pert = workloads.adjoint_2d(512, seed=5)
+    y = np.random.default_rng(9).normal(size=psi0_np.shape)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=dtype, device=dev)
+    res = []
+    for staged in (False, True):
+        with Mpdata(psi0_np.shape, dtype=dtype, n_iters=n_iters, opts=opts | (capi.STAGED if staged else 0)) as m:
+            pb = t(y)
+            gcb = [torch.zeros(psi0_np.shape, dtype=dtype, device=dev) for _ in range(2)]
+            m.adjoint_step(t(psi0_np), [t(v) for v in gc_np], pb, gc_bar=gcb)
+            torch.cuda.synchronize()
+            res.append([pb.double().cpu().numpy()] + [v.double().cpu().numpy() for v in gcb])
+    scale = max(np.abs(a).max() for a in res[1])
+    for a, b in zip(res[0], res[1]):
+        if dtype == torch.float64:
+            assert np.abs(a - b).max() <= 1e-12 * scale
+        else:
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
