@@ -283,7 +283,8 @@ int mpdata_clear_stop(mpdata_t h);
  *   tiles would be 16 rows or less; warp march otherwise), 1 = warp march,
  *   2 = band march, 3 = warp march with lanes of 2 columns instead of 4 (FP32; twice
  *   the warps on a small field; for the FP64 fields, whose lanes already own 2, the warp
- *   march).  Batched handles always use the warp march's persistent kernel.
+ *   march).  Batched handles always use the warp march's persistent kernel, with lanes of 2
+ *   columns for FP32 when this knob is 3 (4 otherwise).
  * MPDATA_TUNE_STEPS_PER_LAUNCH: fusion depth S (temporal blocking): 0 or 1 = one step per
  *   launch; 2..4 = mpdata_advance runs its steps in groups of S per launch (the last group
  *   the remainder), each block loading its tile with a 3S-cell halo into shared memory once and

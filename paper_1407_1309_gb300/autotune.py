@@ -25,6 +25,9 @@ CANDIDATES = tuple([(1, r, 1) for r in (0, 6, 8, 12, 16, 24, 32, 48, 64)] +
                    [(3, r, 1) for r in (6, 8, 12, 16, 24, 32)] +
                    [(2, r, 1) for r in (0, 16, 32, 64, 128, 256)] +
                    [(0, 0, d) for d in (2, 3, 4)])
+# batched handles (several fields, one persistent launch per step): lanes of 4 or 2 columns and the
+# tile height of the work items
+BATCH_CANDIDATES = tuple((k, r, 1) for k in (1, 3) for r in (24, 32, 48, 64, 96, 128))
 # options the temporal-blocking kernel does not cover
 _TBLOCK_EXCLUDED = ("TOT", "ABS", "DFL", "NUG", "KAHAN", "RHS_EULER_A", "RHS_EULER_B", "RHS_TRAPEZ", "STAGED",
                     "OPEN0", "OPEN1", "OPEN2", "SW")
@@ -130,9 +133,11 @@ def autotune(solver, psi, gc, g=None, r=None, dt=0.0, candidates=CANDIDATES, ste
     `solver` (an Mpdata handle); returns ((kernel, tile_rows, depth), seconds per step,
     {candidate: seconds}).  The handle is left tuned to the winner.  Fusion depths above 1 are
     tried only where the temporal-blocking kernel covers the handle, and are timed per step
-    over calls of `depth` steps.  With lo (the low parts of a compensated FP32 state psi = hi +
+    over calls of `depth` steps.  Batched handles search BATCH_CANDIDATES by default.  With lo (the low parts of a compensated FP32 state psi = hi +
     lo) the compensated step is timed, over the warp-march candidates at depth 1."""
     key = key_of(solver) + ("|compensated" if lo is not None else "")
+    if len(solver.shapes) > 1 and candidates is CANDIDATES:
+        candidates = BATCH_CANDIDATES
     if lo is not None:
         candidates = tuple(c for c in candidates if c[0] in (1, 3) and c[2] == 1)
     if solver.dtype != torch.float32:

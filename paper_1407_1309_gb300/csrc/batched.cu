@@ -36,7 +36,8 @@ template <typename T>
 int batched_step(mpdata_s* h, const T* psi_in, T* psi_out, const T* const* gc, const T* g, const T* r, T dt,
                  T gc_scale, const Opts& o) {
   if (handle_nd(h) != 2 || o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
-  const int nc = fused_batched_columns<T>();
+  // lanes of 2 columns for FP32 when the handle asks for them (MPDATA_TUNE_KERNEL = 3)
+  const int nc = (o.kernel == 3 && sizeof(T) == 4) ? 2 : fused_batched_columns<T>();
   const int ty = o.tile_rows > 0 ? o.tile_rows : kDefaultBatchRows;
   void** slot = handle_batch(h);
   auto* th = static_cast<TableHolder*>(*slot);
@@ -74,7 +75,8 @@ int batched_step(mpdata_s* h, const T* psi_in, T* psi_out, const T* const* gc, c
     cudaMemcpy(th->tab.item_field, item_field.data(), sizeof(int) * item_field.size(), cudaMemcpyHostToDevice);
     *slot = th;
   }
-  return fused_batched_step<T>(th->tab, o, psi_in, psi_out, gc[0], gc[1], g, r, dt, gc_scale, handle_stream(h));
+  return fused_batched_step<T>(th->tab, o, psi_in, psi_out, gc[0], gc[1], g, r, dt, gc_scale, handle_stream(h),
+                               th->nc);
 }
 
 template int batched_step<float>(mpdata_s*, const float*, float*, const float* const*, const float*, const float*,

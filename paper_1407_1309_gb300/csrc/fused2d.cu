@@ -550,11 +550,11 @@ template int fused_batched_columns<double>();
 
 int fused_strip_stride(int nc) { return 32 * nc - 2 * kLead; }
 
-template <typename T>
-int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
-                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st) {
-  if (o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
-  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
+namespace {
+
+template <typename T, int NC>
+int batched_launch(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0, const T* gc1,
+                   const T* G, const T* R, T dt, T scale, cudaStream_t st) {
   BatchParams<T> b;
   b.psi = psi_in;
   b.out = psi_out;
@@ -582,10 +582,23 @@ int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T*
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
+}  // namespace
+
+template <typename T>
+int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
+                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st, int nc) {
+  if (o.n_iters != 2 || o.tot || o.abs || o.dfl || o.open) return MPDATA_EUNSUPPORTED;
+  if (sizeof(T) == 4 && nc == 2)
+    return batched_launch<T, 2>(tab, o, psi_in, psi_out, gc0, gc1, G, R, dt, scale, st);
+  if (nc != fused_batched_columns<T>()) return MPDATA_EINVAL;
+  return batched_launch<T, sizeof(T) == 4 ? 4 : 2>(tab, o, psi_in, psi_out, gc0, gc1, G, R, dt, scale, st);
+}
+
 template int fused_batched_step<float>(const BatchTable&, const Opts&, const float*, float*, const float*,
-                                       const float*, const float*, const float*, float, float, cudaStream_t);
+                                       const float*, const float*, const float*, float, float, cudaStream_t, int);
 template int fused_batched_step<double>(const BatchTable&, const Opts&, const double*, double*, const double*,
-                                        const double*, const double*, const double*, double, double, cudaStream_t);
+                                        const double*, const double*, const double*, double, double, cudaStream_t,
+                                        int);
 
 namespace {
 

@@ -75,7 +75,7 @@ int fused_batched_columns();
 int fused_strip_stride(int nc);
 template <typename T>
 int fused_batched_step(const BatchTable& tab, const Opts& o, const T* psi_in, T* psi_out, const T* gc0,
-                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st);
+                       const T* gc1, const T* G, const T* R, T dt, T scale, cudaStream_t st, int nc);
 
 // One step of all fields of a batched handle in one persistent launch
 // (batched.cu); MPDATA_EUNSUPPORTED when not covered.

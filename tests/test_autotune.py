@@ -59,6 +59,11 @@ def test_candidates_cover_every_kernel_family_and_fusion_depth():
     assert {d for _, _, d in autotune.CANDIDATES} == {1, 2, 3, 4}
 
 
+def test_batched_handles_search_lane_widths_and_tile_heights():
+    fams = {k for k, _, _ in autotune.BATCH_CANDIDATES}
+    assert fams == {1, 3} and all(d == 1 and 4 <= r <= 65536 for _, r, d in autotune.BATCH_CANDIDATES)
+
+
 def test_fusion_depth_only_where_the_temporal_blocking_kernel_covers_the_handle():
     s = FakeSolver()
     assert autotune.tblock_applies(s)

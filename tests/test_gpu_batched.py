@@ -25,7 +25,7 @@ def ensemble(shapes, seed, var=False):
     return out
 
 
-def run_batch(fields, dtype, n_iters, opts, n_steps, G=None, tile_rows=0):
+def run_batch(fields, dtype, n_iters, opts, n_steps, G=None, tile_rows=0, kernel=0):
     dev = torch.device("cuda")
     shapes = [p.shape for p, _ in fields]
     cat = lambda arrs: torch.tensor(np.concatenate([a.ravel() for a in arrs]), dtype=dtype, device=dev)
@@ -35,6 +35,8 @@ def run_batch(fields, dtype, n_iters, opts, n_steps, G=None, tile_rows=0):
     with Mpdata(shapes, dtype=dtype, n_iters=n_iters, opts=opts | (capi.NUG if G is not None else 0)) as m:
         if tile_rows:
             m.tune(capi.TUNE_TILE_ROWS, tile_rows)
+        if kernel:
+            m.tune(capi.TUNE_KERNEL, kernel)
         out = torch.empty_like(psi)
         m.advance(psi, out, gc, Gt, None, 0.0, n_steps)
         masses = m.mass(out, Gt)
@@ -117,3 +119,21 @@ def test_cuda_graph_replay_equals_direct_run(batched):
         m.advance(direct, again, gc, n_steps=10)
         torch.cuda.synchronize()
         assert torch.equal(out, again)
+
+
+@pytest.mark.parametrize("tile_rows", [0, 8, 48])
+@pytest.mark.parametrize("name,opts", [("fct", capi.FCT), ("iga_fct", capi.IGA | capi.FCT), ("basic", 0)])
+def test_batched_lanes_of_two_columns(name, opts, tile_rows):
+    """MPDATA_TUNE_KERNEL = 3 on a batched FP32 handle: the persistent kernel with lanes of 2
+    columns (strips of 56 outputs), against the oracle field by field (FP32 bars) and against
+    the 4-column lanes (to rounding)."""
+    fields = ensemble(SHAPES, 3, var=bool(opts & capi.IGA))
+    fields = [(p.astype(np.float32).astype(np.float64), [g.astype(np.float32).astype(np.float64) for g in gc])
+              for p, gc in fields]
+    got, masses = run_batch(fields, torch.float32, 2, opts, 5, tile_rows=tile_rows, kernel=3)
+    wide, _ = run_batch(fields, torch.float32, 2, opts, 5, tile_rows=tile_rows)
+    for f, ((p, gc), a, b) in enumerate(zip(fields, got, wide)):
+        ref = oracle.step(p, gc, n_iters=2, opts=opts, n_steps=5)
+        assert np.linalg.norm(a - ref) <= 1e-5 * np.linalg.norm(ref)
+        assert np.linalg.norm(a - b) <= 1e-6 * max(np.linalg.norm(b), 1e-30)
+        assert abs(masses[f] - oracle.mass(p, None)) <= 1e-6 * oracle.mass(np.abs(p), None)
