@@ -168,10 +168,10 @@ def traffic_from_profiles(kernel, n, dtype, key="bytes_per_launch"):
 # from the scheme with every quantity computed once: pass 1 (Eq. 4-5) 12, pseudo-velocities with
 # the cross term (Eq. 6 and its 2D form) 19 per face, FCT bounds, in/out sums and factors 32,
 # limited pseudo-velocities 10, pass 2 12; each of the 6 divisions is a reciprocal + multiply.
-# The compensated state adds, per donor pass, four error-free two-sums (7 instructions each
-# instead of one add) and the renormalisation (6), and in pass 1 the low parts' own fluxes (8)
-# and their sum (1): 104 + 2 x (24 + 6) + 9 = 173.
-ALU_INST_PER_CELL_STEP = {"plain": 104, "compensated": 173}
+# The compensated state adds, per donor pass, an error-free two-sum of psi + divergence (6
+# instructions instead of one add), the error's addition to lo (2) and the renormalisation (6),
+# and in pass 1 the low parts' own fluxes (8) and their sum (1): 104 + 2 x 13 + 9 = 139.
+ALU_INST_PER_CELL_STEP = {"plain": 104, "compensated": 139}
 
 
 def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count, state="plain"):

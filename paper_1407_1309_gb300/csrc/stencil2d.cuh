@@ -101,32 +101,28 @@ __device__ __forceinline__ void two_sum_acc(T& s, T& e, T t) {
   e = e + err;
 }
 
-// Donor-cell update of Eq. 4 on a compensated state psi = hi + lo: the four face fluxes
-// of the high parts (the same terms, in the same order, as the Kahan form) are added with
-// two-sums whose rounding errors collect in lo, the low parts move with their own face
-// fluxes (lo_div), and the pair is renormalised so that the returned hi is the value of
-// the representable sum nearest hi + lo.  Every flux leaves one cell and enters its
-// neighbour with the same value, so sum(hi + lo) changes only by the rounding of the small
-// lo additions.
+// Donor-cell update of Eq. 4 on a compensated state psi = hi + lo: the flux divergence of
+// the high parts is formed in FP32 as in the plain update (fluxes differenced first), added to
+// hi with a two-sum whose rounding error joins lo together with the low parts' own flux
+// divergence (lo_div), and the pair is renormalised so that the returned hi is the value of
+// the representable sum nearest hi + lo.  The rounding of psi + divergence, at the scale of
+// psi, is the one that biases the plain FP32 state over long runs; it is kept exactly.
 // lo_div: the divergence of the low parts' own face fluxes (added to lo, scaled by 1/G).
 template <typename T, bool NUG>
 __device__ __forceinline__ T donor_comp(T p, T lo, T Fp0, T Fm0, T Fp1, T Fm1, T rG, T lo_div, T& lo_out) {
+  T div = (Fm0 - Fp0) + (Fm1 - Fp1);
   if (NUG) {
-    Fp0 *= rG;
-    Fm0 *= rG;
-    Fp1 *= rG;
-    Fm1 *= rG;
+    div *= rG;
     lo_div *= rG;
   }
-  T s = p, e = lo + lo_div;
-  two_sum_acc(s, e, -Fp0);
-  two_sum_acc(s, e, Fm0);
-  two_sum_acc(s, e, -Fp1);
-  two_sum_acc(s, e, Fm1);
+  const T s = p + div;
+  const T bp = s - p;
+  const T err = (p - (s - bp)) + (div - bp);
+  const T e = (lo + lo_div) + err;
   // renormalise with a full two-sum: after cancellation |e| may exceed |s|
   const T h = s + e;
-  const T bp = h - s;
-  lo_out = (s - (h - bp)) + (e - bp);
+  const T bq = h - s;
+  lo_out = (s - (h - bq)) + (e - bq);
   return h;
 }
 
