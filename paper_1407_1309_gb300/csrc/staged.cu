@@ -739,15 +739,8 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* const sm = reinterpret_cast<T*>(smem_raw);
   constexpr int nP = kCPw * kCPh, nV = kCVw * kCVh, nB = kCBw * kCBh;
-  T* const sP = sm;                    // [kC3P][nP]
-  T* const sVx = sP + kC3P * nP;       // [kC3Vq][nV]
-  T* const sVy = sVx + kC3Vq * nV;     // [kC3Vq][nV]
-  T* const sVz = sVy + kC3Vq * nV;     // [kC3Vz][nB]
-  T* const sBu = sVz + kC3Vz * nB;     // [kC3B][nB]
-  T* const sBd = sBu + kC3B * nB;      // [kC3B][nB]
-  T* const sMx = sBd + kC3B * nB;      // [kC3M][nB]
-  T* const sMn = sMx + kC3M * nB;      // [kC3M][nB]
-  T* const sG = sMn + kC3M * nB;       // [kC3G][nB]
+  // layout of sm: psi [kC3P][nP], x and y components [kC3Vq][nV] each, then the z component
+  // [kC3Vz][nB], the factors [kC3B][nB] each, the bounds [kC3M][nB] each and G [kC3G][nB]
   const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kAx + tx;
   constexpr int kT = kAx * kAy;
@@ -774,62 +767,91 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
     dev::cp_async<sizeof(T)>(dst + tid, src + off[0]);
     if (tid + kT < count) dev::cp_async<sizeof(T)>(dst + tid + kT, src + off[1]);
   };
-  // Ring slots: k5, k4, k3, k2 are the slots of plane z in the rings of 5, 4, 3 and 2 planes at
-  // step z (advanced by one per step); plane z + j sits in slot k + j (mod the ring size).
-  int k5 = kC3P - 1, k4 = kC3Vz - 1, k3 = kC3Vq - 1, k2 = kC3M - 1;  // plane zb - 1
+  // Ring planes as pointers indexed by the plane's offset from the current step z, rotated by
+  // one slot per step: P[i] plane z-2+i (i = 0..4), Vx/Vy[i] z-1+i, Vz[i] z-2+i, Bu/Bd[i]
+  // z-2+i, Mx/Mn[i] z+i, G[i] z-1+i.  The last slot of each input ring takes the next step's
+  // plane (cp.async) while this step computes.
   static_assert(kC3P == 5 && kC3Vz == 4 && kC3Vq == 3 && kC3B == 3 && kC3G == 3 && kC3M == 2, "ring sizes");
-  auto rj = [](int k, int j, int n) { const int v = k + j; return v >= n ? v - n : (v < 0 ? v + n : v); };
-  auto P_ = [&](int j) { return sP + rj(k5, j, kC3P) * nP; };
-  auto Vx_ = [&](int j) { return sVx + rj(k3, j, kC3Vq) * nV; };
-  auto Vy_ = [&](int j) { return sVy + rj(k3, j, kC3Vq) * nV; };
-  auto Vz_ = [&](int j) { return sVz + rj(k4, j, kC3Vz) * nB; };
-  auto Bu_ = [&](int j) { return sBu + rj(k3, j, kC3B) * nB; };
-  auto Bd_ = [&](int j) { return sBd + rj(k3, j, kC3B) * nB; };
-  auto Mx_ = [&](int j) { return sMx + rj(k2, j, kC3M) * nB; };
-  auto Mn_ = [&](int j) { return sMn + rj(k2, j, kC3M) * nB; };
-  auto G_ = [&](int j) { return sG + rj(k3, j, kC3G) * nB; };
-  // the planes that become needed at step zz = z + j: psi zz+1, the components, bounds and G of
-  // plane zz (z the current step)
-  auto copy_step = [&](int zz, int j) {
-    copy(P_(j + 1), psi + zoff(zz + 1), offP, nP);
-    const long long zo = zoff(zz);
-    copy(Vx_(j), Vu.p[2] + zo, offV, nV);
-    copy(Vy_(j), Vu.p[1] + zo, offV, nV);
-    copy(Vz_(j), Vu.p[0] + zo, offB, nB);
-    copy(Mx_(j), mxg + zo, offB, nB);
-    copy(Mn_(j), mng + zo, offB, nB);
-    if (G) copy(G_(j), G + zo, offB, nB);
+  int P[kC3P], VX[kC3Vq], VY[kC3Vq], VZ[kC3Vz], BU[kC3B], BD[kC3B], MX[kC3M], MN[kC3M], GG[kC3G];  // offsets in sm
+#pragma unroll
+  for (int i = 0; i < kC3P; ++i) P[i] = i * nP;
+#pragma unroll
+  for (int i = 0; i < kC3Vq; ++i) { VX[i] = kC3P * nP + i * nV; VY[i] = kC3P * nP + (kC3Vq + i) * nV; }
+  constexpr int oB = kC3P * nP + 2 * kC3Vq * nV;  // start of the [nB] rings
+#pragma unroll
+  for (int i = 0; i < kC3Vz; ++i) VZ[i] = oB + i * nB;
+#pragma unroll
+  for (int i = 0; i < kC3B; ++i) {
+    BU[i] = oB + (kC3Vz + i) * nB;
+    BD[i] = oB + (kC3Vz + kC3B + i) * nB;
+    GG[i] = oB + (kC3Vz + 2 * kC3B + 2 * kC3M + i) * nB;
+  }
+#pragma unroll
+  for (int i = 0; i < kC3M; ++i) {
+    MX[i] = oB + (kC3Vz + 2 * kC3B + i) * nB;
+    MN[i] = oB + (kC3Vz + 2 * kC3B + kC3M + i) * nB;
+  }
+  // the planes that become needed at step zz (its psi plane zz+1 into psi slot jp; the
+  // components, bounds and G of plane zz into slots jq, jz, jm, jg)
+  auto copy_step = [&](long long zo_p, long long zo, int jp, int jq, int jz, int jm, int jg) {
+    copy(sm + P[jp], psi + zo_p, offP, nP);
+    copy(sm + VX[jq], Vu.p[2] + zo, offV, nV);
+    copy(sm + VY[jq], Vu.p[1] + zo, offV, nV);
+    copy(sm + VZ[jz], Vu.p[0] + zo, offB, nB);
+    copy(sm + MX[jm], mxg + zo, offB, nB);
+    copy(sm + MN[jm], mng + zo, offB, nB);
+    if (G) copy(sm + GG[jg], G + zo, offB, nB);
   };
-
+  // wrapped plane indices advanced by one per step
+  auto next = [&](int v) { return v + 1 == nz ? 0 : v + 1; };
+  int zq = wrapc(zb - 1, nz);  // plane z (step z = zb - 1 first)
   // prologue (step zb-1): psi planes zb-2, zb-1, the z component of plane zb-2, then step zb-1's planes
-  copy(P_(-1), psi + zoff(zb - 2), offP, nP);
-  copy(P_(0), psi + zoff(zb - 1), offP, nP);
-  copy(Vz_(-1), Vu.p[0] + zoff(zb - 2), offB, nB);
-  copy_step(zb - 1, 0);
+  copy(sm + P[1], psi + zoff(zb - 2), offP, nP);
+  copy(sm + P[2], psi + static_cast<long long>(zq) * plane, offP, nP);
+  copy(sm + VZ[1], Vu.p[0] + zoff(zb - 2), offB, nB);
+  copy_step(static_cast<long long>(next(zq)) * plane, static_cast<long long>(zq) * plane, 3, 1, 2, 0, 1);
   dev::cp_commit();
   dev::cp_wait<0>();
+  // the factor cells of this thread (the tile and a one-cell ring: nB cells, two passes of the
+  // block at most), fixed for the whole march
+  constexpr int kFac = (nB + kT - 1) / kT;
+  int fr[kFac], fcp[kFac], fcv[kFac];
+#pragma unroll
+  for (int j = 0; j < kFac; ++j) {
+    const int r = tid + j * kT;
+    const int by = r / kCBw, bx = r - by * kCBw;  // cell (bx - 1, by - 1) of the tile
+    fr[j] = r < nB ? r : -1;
+    fcp[j] = (by + 1) * kCPw + (bx + 1);  // in the psi tile
+    fcv[j] = (by + 1) * kCVw + (bx + 1);  // in the x, y component tiles
+  }
+  const int x = x0 + tx, y = y0 + ty;
+  const int cpc = (ty + 2) * kCPw + (tx + 2), cvc = (ty + 2) * kCVw + (tx + 2), cbc = (ty + 1) * kCBw + (tx + 1);
+  // this thread's cell of plane q = z - 1 (first step z = zb - 1)
+  long long oq = static_cast<long long>(zb - 2) * plane + static_cast<long long>(y) * nx + x;
 
   for (int z = zb - 1; z <= ze; ++z) {
     __syncthreads();  // step z's planes are in (each thread waited for its own copies)
-    if (z + 1 <= ze) copy_step(z + 1, 1);  // the next step's planes fly while this one computes
+    const int zn = next(zq);           // plane z + 1
+    if (z + 1 <= ze) copy_step(static_cast<long long>(next(zn)) * plane, static_cast<long long>(zn) * plane, 4, 2, 3, 1, 2);
     dev::cp_commit();
-    const T* sMxz = Mx_(0);
-    const T* sMnz = Mn_(0);
     {  // limiting factors of plane z on the tile and a one-cell halo (k_beta)
-      const T* pm = P_(-1);
-      const T* p0 = P_(0);
-      const T* pp = P_(1);
-      const T* vx = Vx_(0);
-      const T* vy = Vy_(0);
-      const T* vzm = Vz_(-1);
-      const T* vz0 = Vz_(0);
-      const T* gz = G_(0);
-      T* bu = Bu_(0);
-      T* bd = Bd_(0);
-      for (int r = tid; r < nB; r += kT) {
-        const int by = r / kCBw, bx = r - by * kCBw;  // cell (bx - 1, by - 1) of the tile
-        const int cp = (by + 1) * kCPw + (bx + 1);    // in the psi tile
-        const int cv = (by + 1) * kCVw + (bx + 1);    // in the x, y component tiles
+      const T* pm = sm + P[1];
+      const T* p0 = sm + P[2];
+      const T* pp = sm + P[3];
+      const T* vx = sm + VX[1];
+      const T* vy = sm + VY[1];
+      const T* vzm = sm + VZ[1];
+      const T* vz0 = sm + VZ[2];
+      const T* gz = sm + GG[1];
+      const T* sMxz = sm + MX[0];
+      const T* sMnz = sm + MN[0];
+      T* bu = sm + BU[2];
+      T* bd = sm + BD[2];
+#pragma unroll
+      for (int j = 0; j < kFac; ++j) {
+        const int r = fr[j];
+        if (r < 0) continue;
+        const int cp = fcp[j], cv = fcv[j];
         const T p = p0[cp];
         T in = T(0), ou = T(0);
         {  // dimension 0 (z)
@@ -857,17 +879,16 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
     }
     __syncthreads();
     const int q = z - 1;
-    const int x = x0 + tx, y = y0 + ty;
     if (q >= zb && x < nx && y < ny) {  // limit and donor of plane q (k_limit, k_donor)
-      // plane q = z - 1: offsets -2 .. 0 from step z
-      const T* ps[3] = {P_(-2), P_(-1), P_(0)};
-      const T* bus[3] = {Bu_(-2), Bu_(-1), Bu_(0)};
-      const T* bds[3] = {Bd_(-2), Bd_(-1), Bd_(0)};
-      const T* vx = Vx_(-1);
-      const T* vy = Vy_(-1);
-      const T* vzm = Vz_(-2);
-      const T* vz0 = Vz_(-1);
-      const int cp = (ty + 2) * kCPw + (tx + 2), cv = (ty + 2) * kCVw + (tx + 2), cb = (ty + 1) * kCBw + (tx + 1);
+      // plane q = z - 1: ring offsets 0 .. 2 of psi and the factors
+      const T* ps[3] = {sm + P[0], sm + P[1], sm + P[2]};
+      const T* bus[3] = {sm + BU[0], sm + BU[1], sm + BU[2]};
+      const T* bds[3] = {sm + BD[0], sm + BD[1], sm + BD[2]};
+      const T* vx = sm + VX[0];
+      const T* vy = sm + VY[0];
+      const T* vzm = sm + VZ[0];
+      const T* vz0 = sm + VZ[1];
+      const int cp = cpc, cv = cvc, cb = cbc;
       const T p = ps[1][cp];
       // limited advector at a face: V m, m = min(1, factor of the upwind side, factor of the downwind side)
       auto limit = [&](T L, T Rr, T V, T buL, T bdL, T buR, T bdR) {
@@ -890,13 +911,13 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
       const T hy_m = limit(py_m, p, vy[cv - kCVw], bus[1][cb - kCBw], bds[1][cb - kCBw], bus[1][cb], bds[1][cb]);
       const T hx_p = limit(p, px_p, vx[cv], bus[1][cb], bds[1][cb], bus[1][cb + 1], bds[1][cb + 1]);
       const T hx_m = limit(px_m, p, vx[cv - 1], bus[1][cb - 1], bds[1][cb - 1], bus[1][cb], bds[1][cb]);
-      const long long i = static_cast<long long>(q) * plane + static_cast<long long>(y) * nx + x;
+      const long long i = oq;
       if (lim.p[0]) {
         lim.p[0][i] = hz_p;
         lim.p[1][i] = hy_p;
         lim.p[2][i] = hx_p;
       }
-      const T Gi = G ? G_(-1)[cb] : T(1);
+      const T Gi = G ? sm[GG[0] + cb] : T(1);
       T s = p, comp = T(0);
       const T hp[3] = {hz_p, hy_p, hx_p}, hm[3] = {hz_m, hy_m, hx_m};
       const T np_[3] = {pz_p, py_p, px_p}, nm_[3] = {pz_m, py_m, px_m};
@@ -923,11 +944,28 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
       if (post) s = s + dt * R[i];
       out[i] = s;
     }
+    oq += plane;
     dev::cp_wait<0>();
-    k5 = rj(k5, 1, kC3P);
-    k4 = rj(k4, 1, kC3Vz);
-    k3 = rj(k3, 1, kC3Vq);
-    k2 = rj(k2, 1, kC3M);
+    // rotate the rings by one plane
+    {
+      int t = P[0];
+#pragma unroll
+      for (int k = 0; k < kC3P - 1; ++k) P[k] = P[k + 1];
+      P[kC3P - 1] = t;
+      t = VZ[0];
+#pragma unroll
+      for (int k = 0; k < kC3Vz - 1; ++k) VZ[k] = VZ[k + 1];
+      VZ[kC3Vz - 1] = t;
+      const int tx_ = VX[0], ty_ = VY[0], tu = BU[0], td = BD[0], tg = GG[0];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        VX[k] = VX[k + 1]; VY[k] = VY[k + 1]; BU[k] = BU[k + 1]; BD[k] = BD[k + 1]; GG[k] = GG[k + 1];
+      }
+      VX[2] = tx_; VY[2] = ty_; BU[2] = tu; BD[2] = td; GG[2] = tg;
+      t = MX[0]; MX[0] = MX[1]; MX[1] = t;
+      t = MN[0]; MN[0] = MN[1]; MN[1] = t;
+    }
+    zq = zn;
   }
 }
 
