@@ -88,6 +88,35 @@ struct Nbr {
   __device__ __forceinline__ long long at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
 };
 
+// 2D: 32-bit cell indices (the reverse step refuses 2D fields of 2^31 cells or more) and the
+// wrap of each neighbour formed from the cell's own row and column
+template <>
+struct Nbr<2> {
+  int i;
+  int off[2][5];
+  __device__ __forceinline__ Nbr(const Grid& g, const Coord& x) {
+    const int n1 = g.n[1], n2 = g.n[2], r = x.c[1], c = x.c[2];
+    i = r * n2 + c;
+#pragma unroll
+    for (int s = -2; s <= 2; ++s) {
+      int v = r + s;
+      if (v < 0) v += n1;
+      if (v < 0) v += n1;
+      if (v >= n1) v -= n1;
+      if (v >= n1) v -= n1;
+      off[0][s + 2] = (v - r) * n2;
+      int u = c + s;
+      if (u < 0) u += n2;
+      if (u < 0) u += n2;
+      if (u >= n2) u -= n2;
+      if (u >= n2) u -= n2;
+      off[1][s + 2] = u - c;
+    }
+  }
+  __device__ __forceinline__ int at(int d, int s) const { return i + off[d][s + 2]; }
+  __device__ __forceinline__ int at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
+};
+
 template <typename T> __device__ __forceinline__ T flux(T L, T R, T V, bool unit) {
   return unit ? V : posp(V) * L + negp(V) * R;
 }
@@ -121,7 +150,7 @@ cudaError_t launch_after(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStre
       for (int c2_ = blockIdx.x * blockDim.x + threadIdx.x; c2_ < g.n[2];               \
            c2_ += gridDim.x * blockDim.x) {                                           \
         const Nbr<ND> nb(g, Coord{{c0_, c1_, c2_}});                                   \
-        const long long i = nb.i;
+        const auto i = nb.i;
 #define CELL_END }
 
 // Reverse of the donor-cell pass k, psi_k = psi_{k-1} + sum_d (F_{i-e_d} - F_i)/G_i with
@@ -140,7 +169,7 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
   T acc = pb[i];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
+    const auto ip = nb.at(d, +1), im = nb.at(d, -1);
     const T gp = G ? adiv(pb[ip], G[ip]) : pb[ip];
     const T gm = G ? adiv(pb[im], G[im]) : pb[im];
     const T fp = gp - gi;  // dL/dF on the face (d, i)
@@ -171,10 +200,10 @@ __global__ void ka_donor_flux(Grid g, const T* __restrict__ pb, const T* __restr
 //   out = (|V| - V^2/Gb) A - sum_q 0.5 V Vq/Gb B_q,  A = (p1-p0)/(p0+p1),  B = (T-Bt)/(T+Bt)
 // (A = (p1-p0)/2 and B = (T-Bt)/4 under infinite gauge); scatters to pb and vhb.
 template <typename T, int ND>
-__device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const long long i, const int d, const T gout,
+__device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const decltype(Nbr<ND>::i) i, const int d, const T gout,
                                                   const T* __restrict__ psi, const P3<T>& Vin,
                                                   const T* __restrict__ G, const bool iga, T* pb, const W3<T>& vhb) {
-  const long long ip = nb.at(d, +1);
+  const auto ip = nb.at(d, +1);
   const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
   const T V = Vin.p[d][i];
   const T p0 = psi[i], p1 = psi[ip];
@@ -198,8 +227,8 @@ __device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const long 
 #pragma unroll
   for (int q = 0; q < ND; ++q) {
     if (q == d) continue;
-    const long long iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
-    const long long iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
+    const auto iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
+    const auto iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
     const T* Q = Vin.p[q];
     const T Vq = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
     const T Tp = psi[iqp] + psi[idqp], Bt = psi[iqm] + psi[idqm];
@@ -283,10 +312,10 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
   T acc = pb[i];
   T gu = T(0), gd = T(0);  // adjoints of beta_up and beta_dn of this cell
   T Fp[3], Fm[3];
-  long long im[3];
+  decltype(nb.i) im[3];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = nb.at(d, +1);
+    const auto ip = nb.at(d, +1);
     im[d] = nb.at(d, -1);
     const T pp = psi[ip], pm = psi[im[d]];
     const T v = Vu.p[d][i], vm = Vu.p[d][im[d]];
@@ -352,9 +381,9 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
 // candidate (order: the cell, then per dimension its -e_d and +e_d neighbours; psi^n before
 // psi^(1)).
 template <typename T, int ND>
-__device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const long long i, const T gmx, const T gmn,
+__device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const decltype(Nbr<ND>::i) i, const T gmx, const T gmn,
                                            const T* __restrict__ p0, const T* __restrict__ p1, T* pb0, T* pb1) {
-  long long loc[7];
+  decltype(Nbr<ND>::i) loc[7];
   int nl = 0;
   loc[nl++] = i;
 #pragma unroll
@@ -364,7 +393,7 @@ __device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const long long i,
   }
   T hi = p0[i], lo = p0[i];
   int ha = 0, la = 0;
-  long long hj = i, lj = i;
+  auto hj = i, lj = i;
   for (int j = 0; j < nl; ++j) {
     const T a = p0[loc[j]], b = p1[loc[j]];
     if (a > hi) { hi = a; ha = 0; hj = loc[j]; }
@@ -391,7 +420,7 @@ __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi,
   T acc = T(0);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const long long ip = nb.at(d, +1), im = nb.at(d, -1);
+    const auto ip = nb.at(d, +1), im = nb.at(d, -1);
     const T fp = fb.p[d][i], fm = fb.p[d][im];
     const T v = Vu.p[d][i], vm = Vu.p[d][im];
     T dv = T(1);
@@ -622,6 +651,7 @@ int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const 
   handle_tuning(h, &o.kernel, &o.tile_rows);  // the fused recording follows the forward's kernel
   if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
   const Grid& gr = handle_grids(h)[0];
+  if (gr.nd == 2 && gr.N >= (1LL << 31)) return MPDATA_EUNSUPPORTED;  // 32-bit indices of Nbr<2>
   const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
                     gr.nd > 2 ? static_cast<const T*>(gcv[2]) : nullptr};
   const T* G = o.nug ? g : nullptr;
