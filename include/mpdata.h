@@ -206,8 +206,8 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
  * passes the derivative of its first extremal candidate.  The step is
  * recomputed internally, as mpdata_adjoint_record records it; the adjoint scratch
  * is allocated on first use and kept with the handle.  Errors: EINVAL;
- * EUNSUPPORTED for batched handles, for the third-order, abs and dfl options, for source terms
- * and for n_iters > 4; ENOMEM; ECUDA.
+ * EUNSUPPORTED for batched handles, for the third-order, abs and dfl options, for source terms,
+ * for n_iters > 4 and for 2D fields of 2^31 cells or more; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
                         void* psi_bar, void* const* gc_bar);
