@@ -216,17 +216,17 @@ __global__ void __launch_bounds__(W * 32, 2) k_band2d(const BandParams<T> p) {
           // factor: m = min(beta_dn of the upwind cell, beta_up of the downwind cell).
           {  // face (r+1/2, c)
             const T F = u0m[c];
-            const bool right = F > T(0);
+            const bool right = gt0(F);
             h0[c] = F * minv(right ? bd_c[c] : bu_c[c], right ? bun[c] : bdn[c]);
           }
           {  // face (r-1/2, c)
             const T F = u0mm[c];
-            const bool right = F > T(0);
+            const bool right = gt0(F);
             h0c[c] = F * minv(right ? bd_m[c] : bu_m[c], right ? bu_c[c] : bd_c[c]);
           }
           {  // face (r, c+1/2)
             const T F = u1c[c];
-            const bool right = F > T(0);
+            const bool right = gt0(F);
             const T x = right ? bd_c[c] : bu_c[c];
             const T y = right ? right_of(bu_c, c, buR) : right_of(bd_c, c, bdR);
             h1[c] = F * minv(x, y);

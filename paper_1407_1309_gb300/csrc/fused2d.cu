@@ -336,12 +336,12 @@ __device__ __forceinline__ void march_tile(const F2Params<T>& p, const int strip
           // factor: m = min(beta_dn of the upwind cell, beta_up of the downwind cell).
           {  // face (r+1/2, c) between rows r and r+1
             const T F = u0[0][c];
-            const bool right = F > T(0);
+            const bool right = gt0(F);
             h0[c] = F * minv(right ? bd[0][c] : bu[0][c], right ? bu[1][c] : bd[1][c]);
           }
           {  // face (r, c+1/2)
             const T F = u1[0][c];
-            const bool right = F > T(0);
+            const bool right = gt0(F);
             const T a = right ? bd[0][c] : bu[0][c];
             const T b = right ? right_of(bu[0], c, buR) : right_of(bd[0], c, bdR);
             h1[c] = F * minv(a, b);

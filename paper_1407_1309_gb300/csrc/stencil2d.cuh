@@ -50,6 +50,35 @@ template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return 
 // psi-fraction of Eq. 6 with the zero-denominator guard
 template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return d != T(0) ? fdiv(n, d) : T(0); }
 
+// x > 0 (the upwind choice of a flux, the limiter's direction)
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+
+// FP64: sign tests, extrema and magnitudes on the integer pipe.  GB300's FP64 pipe runs at a
+// small fraction of the FP32 rate and bounds the FP64 step, so the operations that need no
+// FP64 arithmetic (comparisons with zero, ordering of two values, |x|) are taken off it.  For
+// finite arguments they give the floating-point forms' results, up to the sign of a zero
+// result (an ordering key makes -0 < +0).
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool lt0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+// a signed integer in the order of the doubles (finite arguments)
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+template <> __device__ __forceinline__ double posp<double>(double x) { return gt0(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double negp<double>(double x) { return lt0(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double absv<double>(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+template <> __device__ __forceinline__ double maxv<double>(double a, double b) { return order_key(a) > order_key(b) ? a : b; }
+template <> __device__ __forceinline__ double minv<double>(double a, double b) { return order_key(a) < order_key(b) ? a : b; }
+template <> __device__ __forceinline__ double flux<double>(double L, double R, double V) { return V * (gt0(V) ? L : R); }
+template <> __device__ __forceinline__ double ratio<double>(double n, double d) { return nonzero(d) ? fdiv(n, d) : 0.0; }
+
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
