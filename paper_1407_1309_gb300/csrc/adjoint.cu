@@ -34,6 +34,23 @@ template <typename T> __device__ __forceinline__ T dpos(T x) { return x > T(0) ?
 template <typename T> __device__ __forceinline__ T dneg(T x) { return x < T(0) ? T(1) : (x > T(0) ? T(0) : T(0.5)); }
 template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
+// x > 0, x < 0, x != 0 and a < b: native for FP32; FP64 on the integer pipe (the FP64 kernels
+// are bound by the FP64 pipe; stencil2d.cuh), the same results for finite arguments up to the
+// sign of a zero
+__device__ __forceinline__ bool gtz(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool ltz(float x) { return x < 0.0f; }
+__device__ __forceinline__ bool nez(float x) { return x != 0.0f; }
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool gtz(double x) { return dev::gt0(x); }
+__device__ __forceinline__ bool ltz(double x) { return dev::lt0(x); }
+__device__ __forceinline__ bool nez(double x) { return dev::nonzero(x); }
+__device__ __forceinline__ bool lt(double a, double b) { return dev::order_key(a) < dev::order_key(b); }
+template <> __device__ __forceinline__ double posp<double>(double x) { return gtz(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double negp<double>(double x) { return ltz(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double dpos<double>(double x) { return gtz(x) ? 1.0 : (ltz(x) ? 0.0 : 0.5); }
+template <> __device__ __forceinline__ double dneg<double>(double x) { return ltz(x) ? 1.0 : (gtz(x) ? 0.0 : 0.5); }
+template <> __device__ __forceinline__ double sgn<double>(double x) { return gtz(x) ? 1.0 : (ltz(x) ? -1.0 : 0.0); }
+template <> __device__ __forceinline__ double absv<double>(double x) { return dev::absv(x); }
 // n / d as in the forward kernels: fast division in FP32, Newton-Raphson division (within one
 // ulp) in FP64; every divisor here is a G, a nonzero psi sum or a nonzero flux sum
 template <typename T> __device__ __forceinline__ T adiv(T n, T d);
@@ -212,7 +229,7 @@ __device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const declt
     A = (p1 - p0) * T(0.5); dA0 = T(-0.5); dA1 = T(0.5);
   } else {
     const T s = p0 + p1;
-    if (s != T(0)) {
+    if (dev::divisible(s)) {
       const T r = adiv(T(1), s);
       A = (p1 - p0) * r; dA0 = T(-2) * p1 * (r * r); dA1 = T(2) * p0 * (r * r);
     } else {
@@ -237,7 +254,7 @@ __device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const declt
       B = (Tp - Bt) * T(0.25); dBT = T(0.25); dBB = T(-0.25);
     } else {
       const T S = Tp + Bt;
-      if (S != T(0)) {
+      if (dev::divisible(S)) {
         const T r = adiv(T(1), S);
         B = (Tp - Bt) * r; dBT = T(2) * Bt * (r * r); dBB = T(-2) * Tp * (r * r);
       } else {
@@ -268,7 +285,7 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const T gout = vb.p[d][i];
-    if (gout != T(0)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
+    if (nez(gout)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
   }
   CELL_END
 }
@@ -279,13 +296,13 @@ __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> V
 template <typename T>
 __device__ __forceinline__ T limit_choice(const T F, const T v, const T* __restrict__ bu, const T* __restrict__ bd,
                                           const long long l, const long long r, bool& right, int& sel) {
-  right = F > T(0) || (F == T(0) && v > T(0));
+  right = gtz(F) || (!nez(F) && gtz(v));
   const T a = right ? bd[l] : bu[l];
   const T b = right ? bu[r] : bd[r];
   T m = T(1);
   sel = 0;
-  if (a < m) { m = a; sel = 1; }
-  if (b < m) { m = b; sel = 2; }
+  if (lt(a, m)) { m = a; sel = 1; }
+  if (lt(b, m)) { m = b; sel = 2; }
   return m;
 }
 
@@ -350,21 +367,21 @@ __global__ void ka_fct_a(Grid g, const T* __restrict__ pb, const T* __restrict__
   }
   const T Gi = G ? G[i] : T(1);
   T gin = T(0), gout = T(0), pacc = T(0), dmx = T(0), dmn = T(0);
-  if (in > T(0) && gu != T(0)) {
+  if (gtz(in) && nez(gu)) {
     const T beta = adiv(Gi * posp(mx[i] - p), in);
     const T t = adiv(gu * Gi * dpos(mx[i] - p), in);
     dmx = t;
     pacc -= t;
     gin = adiv(-gu * beta, in);
   }
-  if (ou > T(0) && gd != T(0)) {
+  if (gtz(ou) && nez(gd)) {
     const T beta = adiv(Gi * posp(p - mn[i]), ou);
     const T t = adiv(gd * Gi * dpos(p - mn[i]), ou);
     pacc += t;
     dmn = -t;
     gout = adiv(-gd * beta, ou);
   }
-  if (gin != T(0) || gout != T(0)) {
+  if (nez(gin) || nez(gout)) {
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       atomicAdd(&fb.p[d][i], -gin * dneg(Fp[d]) + gout * dpos(Fp[d]));
@@ -396,13 +413,13 @@ __device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const decltype(Nbr
   auto hj = i, lj = i;
   for (int j = 0; j < nl; ++j) {
     const T a = p0[loc[j]], b = p1[loc[j]];
-    if (a > hi) { hi = a; ha = 0; hj = loc[j]; }
-    if (b > hi) { hi = b; ha = 1; hj = loc[j]; }
-    if (a < lo) { lo = a; la = 0; lj = loc[j]; }
-    if (b < lo) { lo = b; la = 1; lj = loc[j]; }
+    if (lt(hi, a)) { hi = a; ha = 0; hj = loc[j]; }
+    if (lt(hi, b)) { hi = b; ha = 1; hj = loc[j]; }
+    if (lt(a, lo)) { lo = a; la = 0; lj = loc[j]; }
+    if (lt(b, lo)) { lo = b; la = 1; lj = loc[j]; }
   }
-  if (gmx != T(0)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], gmx);
-  if (gmn != T(0)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], gmn);
+  if (nez(gmx)) atomicAdd(ha == 0 ? &pb0[hj] : &pb1[hj], gmx);
+  if (nez(gmn)) atomicAdd(la == 0 ? &pb0[lj] : &pb1[lj], gmn);
 }
 
 // Reverse of corrective pass k under FCT, second half, per cell i: the unlimited fluxes
@@ -429,9 +446,9 @@ __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi,
       dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
     }
     const T gout = vbl.p[d][i] + fp * dv;
-    if (gout != T(0)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
+    if (nez(gout)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
   }
-  if (acc != T(0)) atomicAdd(&pb[i], acc);
+  if (nez(acc)) atomicAdd(&pb[i], acc);
   if (mxb) bounds_rev<T, ND>(nb, i, mxb[i], mnb[i], p0, psi, pb0, pb);
   CELL_END
 }

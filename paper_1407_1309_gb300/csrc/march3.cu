@@ -98,13 +98,13 @@ __device__ __forceinline__ void fetch(const float* row, int lane, float (&w)[NC 
   w[NC + 2] = R2;
 }
 
-__device__ __forceinline__ float frac1(float n, float d) { return d != 0.0f ? __fdividef(n, d) : 0.0f; }
+__device__ __forceinline__ float frac1(float n, float d) { return divisible(d) ? __fdividef(n, d) : 0.0f; }
 // n1/d and n2/d with one guard and one approximate reciprocal (0 when d == 0)
 __device__ __forceinline__ void frac2v(float n1, float n2, float d, float& r1, float& r2) {
   float r;
   asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(d));
-  r1 = d != 0.0f ? n1 * r : 0.0f;
-  r2 = d != 0.0f ? n2 * r : 0.0f;
+  r1 = divisible(d) ? n1 * r : 0.0f;
+  r2 = divisible(d) ? n2 * r : 0.0f;
 }
 
 // One face of Eq. 6 with the cross terms of the two transverse dimensions q1, q2 (in the

@@ -30,7 +30,8 @@ template <typename T> __device__ __forceinline__ T qdiv(T n, T d);
 template <> __device__ __forceinline__ float qdiv<float>(float n, float d) { return __fdividef(n, d); }
 template <> __device__ __forceinline__ double qdiv<double>(double n, double d) { return dev::nr_div(n, d); }
 // psi-fraction with the zero-denominator guard (the ratio of Eq. 6 is 0 when its sum is 0)
-template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return d != T(0) ? qdiv(n, d) : T(0); }
+// (a divisor below the smallest normal number counts as zero: stencil2d.cuh)
+template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return dev::divisible(d) ? qdiv(n, d) : T(0); }
 
 template <typename T> struct In3 { const T* p[3]; };
 template <typename T> struct Out3 { T* p[3]; };
@@ -335,8 +336,8 @@ __device__ __forceinline__ void frac2(T n1, T n2, T d, T& r1, T& r2) {
   if constexpr (sizeof(T) == 4) {
     float r;
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(d));
-    r1 = d != T(0) ? n1 * r : T(0);
-    r2 = d != T(0) ? n2 * r : T(0);
+    r1 = dev::divisible(d) ? n1 * r : T(0);
+    r2 = dev::divisible(d) ? n2 * r : T(0);
   } else {
     r1 = fracg(n1, d);
     r2 = fracg(n2, d);

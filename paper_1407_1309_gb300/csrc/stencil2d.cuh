@@ -47,8 +47,14 @@ __device__ __forceinline__ float min1(float x) { return fminf(1.0f, x); }
 __device__ __forceinline__ double min1(double x) { return fmin(1.0, x); }
 // donor-cell flux (Eq. 5) in advector units: [V]+ L + [V]- R, one term of which is zero
 template <typename T> __device__ __forceinline__ T flux(T L, T R, T V) { return V * (V > T(0) ? L : R); }
+// A divisor the fast divisions can take: not zero and not below the smallest normal number (their
+// approximate reciprocals flush such a divisor to zero).  A psi-sum that small counts as zero in
+// the guard of the psi-fraction: the fraction it would give changes no flux by more than that.
+__device__ __forceinline__ bool divisible(float d) { return fabsf(d) >= 1.17549435e-38f; }
+__device__ __forceinline__ bool divisible(double d) { return ((__double_as_longlong(d) >> 52) & 0x7FF) != 0; }
+
 // psi-fraction of Eq. 6 with the zero-denominator guard
-template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return d != T(0) ? fdiv(n, d) : T(0); }
+template <typename T> __device__ __forceinline__ T ratio(T n, T d) { return divisible(d) ? fdiv(n, d) : T(0); }
 
 // x > 0 (the upwind choice of a flux, the limiter's direction)
 __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
@@ -77,7 +83,7 @@ template <> __device__ __forceinline__ double absv<double>(double x) {
 template <> __device__ __forceinline__ double maxv<double>(double a, double b) { return order_key(a) > order_key(b) ? a : b; }
 template <> __device__ __forceinline__ double minv<double>(double a, double b) { return order_key(a) < order_key(b) ? a : b; }
 template <> __device__ __forceinline__ double flux<double>(double L, double R, double V) { return V * (gt0(V) ? L : R); }
-template <> __device__ __forceinline__ double ratio<double>(double n, double d) { return nonzero(d) ? fdiv(n, d) : 0.0; }
+
 
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
