@@ -32,6 +32,21 @@ template <> __device__ __forceinline__ double qdiv<double>(double n, double d) {
 // psi-fraction with the zero-denominator guard (the ratio of Eq. 6 is 0 when its sum is 0)
 // (a divisor below the smallest normal number counts as zero: stencil2d.cuh)
 template <typename T> __device__ __forceinline__ T fracg(T n, T d) { return dev::divisible(d) ? qdiv(n, d) : T(0); }
+// FP64: the sign tests, extrema and |x| on the integer pipe (stencil2d.cuh)
+template <> __device__ __forceinline__ double posp<double>(double x) { return dev::gt0(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double negp<double>(double x) { return dev::lt0(x) ? x : 0.0; }
+template <> __device__ __forceinline__ double absv<double>(double x) { return dev::absv(x); }
+// extrema (the first argument on ties) and the limiter's direction, through the same helpers
+template <typename T> __device__ __forceinline__ T maxe(T a, T b) { return dev::maxv(a, b); }
+template <typename T> __device__ __forceinline__ T mine(T a, T b) { return dev::minv(a, b); }
+__device__ __forceinline__ bool goes_right(float F, float V) { return F > 0.0f || (F == 0.0f && V > 0.0f); }
+__device__ __forceinline__ bool goes_right(double F, double V) {
+  return dev::gt0(F) || (!dev::nonzero(F) && dev::gt0(V));
+}
+// a flux sum that takes a limiting factor (0 or a subnormal sum gives the factor 1: the FP64
+// division has no reciprocal of a subnormal, and such a sum cannot move the cell's value)
+__device__ __forceinline__ bool factor_sum(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool factor_sum(double x) { return dev::gt0(x) && dev::divisible(x); }
 
 template <typename T> struct In3 { const T* p[3]; };
 template <typename T> struct Out3 { T* p[3]; };
@@ -192,10 +207,10 @@ __global__ void k_bounds(Grid g, const T* __restrict__ p0, const T* __restrict__
     for (int s = -1; s <= 1; s += 2) {
       const long long j = nb.at(d, s);
       const T a = p0[j], b = p1[j];
-      hi = a > hi ? a : hi;
-      hi = b > hi ? b : hi;
-      lo = a < lo ? a : lo;
-      lo = b < lo ? b : lo;
+      hi = maxe(a, hi);
+      hi = maxe(b, hi);
+      lo = mine(a, lo);
+      lo = mine(b, lo);
     }
   }
   mx[i] = hi;
@@ -695,10 +710,10 @@ __global__ void __launch_bounds__(kAx * kAy) k_p1b3(Grid g, const T* __restrict_
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         const T a = cand[j][0], c = cand[j][1];
-        hi = a > hi ? a : hi;
-        hi = c > hi ? c : hi;
-        lo = a < lo ? a : lo;
-        lo = c < lo ? c : lo;
+        hi = maxe(a, hi);
+        hi = maxe(c, hi);
+        lo = mine(a, lo);
+        lo = mine(c, lo);
       }
       const long long i = static_cast<long long>(zc) * plane + static_cast<long long>(y) * nx + x;
       p1[i] = b0;
@@ -874,8 +889,8 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
           ou = ou + (posp(Fp) - negp(Fm));
         }
         const T Gi = G ? gz[r] : T(1);
-        bu[r] = in > T(0) ? qdiv(Gi * posp(sMxz[r] - p), in) : T(1);
-        bd[r] = ou > T(0) ? qdiv(Gi * posp(p - sMnz[r]), ou) : T(1);
+        bu[r] = factor_sum(in) ? qdiv(Gi * posp(sMxz[r] - p), in) : T(1);
+        bd[r] = factor_sum(ou) ? qdiv(Gi * posp(p - sMnz[r]), ou) : T(1);
       }
     }
     __syncthreads();
@@ -894,12 +909,12 @@ __global__ void __launch_bounds__(kAx * kAy) k_corr3(Grid g, const T* __restrict
       // limited advector at a face: V m, m = min(1, factor of the upwind side, factor of the downwind side)
       auto limit = [&](T L, T Rr, T V, T buL, T bdL, T buR, T bdR) {
         const T F = flux(L, Rr, V, unit);
-        const bool right = F > T(0) || (F == T(0) && V > T(0));
+        const bool right = goes_right(F, V);
         const T a = right ? bdL : buL;
         const T b = right ? buR : bdR;
         T m = T(1);
-        if (a < m) m = a;
-        if (b < m) m = b;
+        m = mine(a, m);
+        m = mine(b, m);
         return V * m;
       };
       // faces (d, +) and (d, -) of this cell: psi, limited advector
@@ -991,8 +1006,8 @@ __global__ void k_beta(Grid g, const T* __restrict__ psi, In3<T> V, const T* __r
     out = out + (posp(Fp) - negp(Fm));
   }
   const T Gi = G ? G[i] : T(1);
-  bu[i] = in > T(0) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
-  bd[i] = out > T(0) ? qdiv(Gi * posp(p - mn[i]), out) : T(1);
+  bu[i] = factor_sum(in) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
+  bd[i] = factor_sum(out) ? qdiv(Gi * posp(p - mn[i]), out) : T(1);
   }
 }
 
@@ -1010,12 +1025,12 @@ __global__ void k_limit(Grid g, const T* __restrict__ psi, In3<T> Vu, bool unit,
     const long long ip = nb.at(d, +1);
     const T V = Vu.p[d][i];
     const T F = flux(p, psi[ip], V, unit);
-    const bool right = F > T(0) || (F == T(0) && V > T(0));
+    const bool right = goes_right(F, V);
     const T a = right ? bd[i] : bu[i];
     const T b = right ? bu[ip] : bd[ip];
     T m = T(1);
-    if (a < m) m = a;
-    if (b < m) m = b;
+    m = mine(a, m);
+    m = mine(b, m);
     Vout.p[d][i] = V * m;
   }
   }
@@ -1112,10 +1127,10 @@ __global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps,
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           const T a = q0[js[t]], b = lev[0][js[t]];
-          hi = a > hi ? a : hi;
-          hi = b > hi ? b : hi;
-          lo = a < lo ? a : lo;
-          lo = b < lo ? b : lo;
+          hi = maxe(a, hi);
+          hi = maxe(b, hi);
+          lo = mine(a, lo);
+          lo = mine(b, lo);
         }
         mx[i] = hi;
         mn[i] = lo;
@@ -1156,8 +1171,8 @@ __global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps,
           in = in + (posp(Fm) - negp(Fp));
           ou = ou + (posp(Fp) - negp(Fm));
           const T Gi = G ? G[i] : T(1);
-          bu[i] = in > T(0) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
-          bd[i] = ou > T(0) ? qdiv(Gi * posp(p - mn[i]), ou) : T(1);
+          bu[i] = factor_sum(in) ? qdiv(Gi * posp(mx[i] - p), in) : T(1);
+          bd[i] = factor_sum(ou) ? qdiv(Gi * posp(p - mn[i]), ou) : T(1);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {  // k_limit
@@ -1165,12 +1180,12 @@ __global__ void __launch_bounds__(kSteps1dThreads) k_steps1d(int n, int n_steps,
           const int ip = Rt(i);
           const T V = vk[i];
           const T F = flux(p, prev[ip], V, o.iga);
-          const bool right = F > T(0) || (F == T(0) && V > T(0));
+          const bool right = goes_right(F, V);
           const T a = right ? bd[i] : bu[i];
           const T b = right ? bu[ip] : bd[ip];
           T m = T(1);
-          if (a < m) m = a;
-          if (b < m) m = b;
+          m = mine(a, m);
+          m = mine(b, m);
           lim[i] = V * m;
         }
         __syncthreads();
