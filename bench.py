@@ -194,18 +194,19 @@ def alu_roofline(cells, seconds_per_step, kernel, n, dtype, sm_max_mhz, sm_count
     return out
 
 
-# Algorithmic FP64 operations per cell-step (adds, multiplies and fused multiply-adds, the work of
-# the FP64 pipe; comparisons and selections not counted), counted from the formulas as the
-# kernels evaluate them, a division being the Newton-Raphson division with remainder correction
-# (7 operations):
-#   2D (n_iters = 2, FCT, G = 1), 94: pass 1 6 (two face fluxes, three flux differences, the
-#   update), pseudo-velocities 29 per face (A and B 9 each, V_q 3, the combination 7, the flux 1),
-#   FCT 24 (in/out sums 8, two factors 8 each), limited fluxes 2, pass 2 4;
-#   3D (n_iters = 3 + tot + FCT + G), 1164: pass 1 72 (six fluxes 3 each, six divisions by G,
-#   six additions, the advector scale), per corrective pass 546: per face 140 (1/Gb 9, A 9, its
-#   coefficient 4, two cross terms 19 each, D_dd with coefficient 25, two D_dq 16 each, the triple
-#   term 23) times three, the factors 48, the limited advector 12, the donor pass 66.
-FP64_OPS_PER_CELL_STEP = {"2d": 94, "3d": 72 + 2 * 546}
+# FP64 arithmetic per cell-step (adds, multiplies and fused multiply-adds, one each: the work of
+# the FP64 pipe, in the unit of the measured FMA rate; comparisons and selections not counted, a
+# division being the Newton-Raphson division with remainder correction, 7):
+#   2D (n_iters = 2, FCT, G = 1), 94, counted from the formulas: pass 1 6 (two face fluxes, three
+#   flux differences, the update), pseudo-velocities 29 per face (A and B 9 each, V_q 3, the
+#   combination 7, the flux 1), FCT 24 (in/out sums 8, two factors 8 each), limited fluxes 2,
+#   pass 2 4 (the 2D kernels execute 118 per cell-step at 1024^2, their recomputed halo included);
+#   3D (n_iters = 3 + tot + FCT + G), 992, counted by ncu as the DADD + DMUL + DFMA instructions of
+#   one step of the staged FP64 kernels at 128^3 (no recomputed halo): pass 1 46, the bounds 0,
+#   per corrective pass 473 (pseudo-advector with the cross and third-order terms 376, factors 42,
+#   limiter 9, donor pass 46).  (A hand tally of the 3D formulas, 1164, counted multiply-add
+#   pairs the compiler fuses.)
+FP64_OPS_PER_CELL_STEP = {"2d": 94, "3d": 992}
 
 
 def measure_fma_rates(dev):
