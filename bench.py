@@ -1230,7 +1230,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded rotating-cone workload, no dataset)",
-           "config": config(args, {"same_config": True}),
+           "config": config(args, {"same_config": True, "l2": "not applicable (the oracle runs on the host cores)"}),
            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 6), "unit": UNIT},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
