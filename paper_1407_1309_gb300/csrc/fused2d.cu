@@ -61,8 +61,9 @@ struct F2Params {
 // One warp marches one tile: the strip `strip` (columns strip*kStride - kLead ...) from
 // row R0 down ty rows of the field described by p; `ring` is the warp's shared-memory ring.
 // COMP: the state is the pair psi = hi + lo (hi in p.psi, lo in p.lo); every stencil
-// quantity is formed from the hi parts, both donor passes add their fluxes with two-sums
-// (donor_comp), the first pass also moves the low parts with their own donor-cell fluxes
+// quantity is formed from the hi parts, both donor passes add their flux divergence to hi with
+// an error-free two-sum (donor_comp), the first pass also moves the low parts with their own
+// donor-cell fluxes
 // (the corrective pass's low-part fluxes are of the order of FP32 rounding and omitted),
 // and both parts are stored.
 // TAPE: the step also writes, for the tile's own rows, what the reverse step reads: psi^(1)
