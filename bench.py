@@ -141,11 +141,17 @@ KERNEL_SOURCES = {"k_fused2d": ("fused2d.cu", "stencil2d.cuh"), "k_band2d": ("ba
 
 
 def kernel_sources_sha256(kernel):
+    """SHA-256 of the code of the kernel's sources, comments and white space left out (a stamp
+    taken on the code stays valid across edits of comments only)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES.get(kernel, ()):
-        with open(os.path.join(ROOT, "paper_1407_1309_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1407_1309_gb300", "csrc", name), encoding="utf-8") as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 
