@@ -4,7 +4,10 @@ the initial field psi0 and the advector components GC.
 Forward: n_steps steps through the C ABI (fused kernels where they apply),
 keeping psi every `checkpoint_every` steps on the device.  Backward: for each
 segment, last first, the states inside the segment are recomputed from its
-checkpoint, then the hand-written adjoint kernels walk the segment backwards,
+checkpoint (except for the last two segments when the backward runs on graphs with
+tapes: the forward records their states and tapes itself, in the backward's own buffers,
+since the backward would recompute exactly those first), then the hand-written adjoint
+kernels walk the segment backwards,
 accumulating dL/dGC over all steps.  When one segment's tapes fit in device
 memory (`tape_budget`), the recomputation records every step's tape
 (mpdata_adjoint_record: states and intermediates in one forward sweep) and the
@@ -41,11 +44,38 @@ class MPDATAFunction(torch.autograd.Function):
         nxt = torch.empty_like(cur)
         gcd = [g.detach().contiguous() for g in gc]
         ckpts = [cur.clone()]
-        for s in range(n_steps):
-            solver.advance(cur, nxt, gcd)
-            cur, nxt = nxt, cur
-            if (s + 1) % checkpoint_every == 0 and s + 1 < n_steps:
+        # the segments whose tapes this forward records for the backward (last first: buffer set
+        # 0 for the last segment, 1 for the one before), when the backward will be the pipelined
+        # one on graphs with tapes
+        n_ck = (n_steps + checkpoint_every - 1) // checkpoint_every
+        pre = {}
+        if (use_graphs and any(ctx.needs_input_grad[4:]) and _fused_record(solver) and
+                _tapes_fit(solver, 2 * min(checkpoint_every, n_steps), cur)):
+            token = object()
+            for idx, seg in enumerate(range(n_ck - 1, max(n_ck - 3, -1), -1)):
+                start, end = seg * checkpoint_every, min(seg * checkpoint_every + checkpoint_every, n_steps)
+                sg = _segment_graph(solver, end - start, cur, gcd, True, idx % 2)
+                sg.owner = token
+                pre[seg] = sg
+            ctx.pre_token = token
+        s = 0
+        while s < n_steps:
+            seg = s // checkpoint_every
+            if seg in pre:  # this segment's steps by the backward's own recording graph
+                sg = pre[seg]
+                sg.load(gcd)
+                sg.states[0].copy_(cur)
+                sg.rec_graph.replay()
+                nxt.copy_(sg.spare)
+                cur, nxt = nxt, cur
+                s = min(s + checkpoint_every, n_steps)
+            else:
+                solver.advance(cur, nxt, gcd)
+                cur, nxt = nxt, cur
+                s += 1
+            if s % checkpoint_every == 0 and s < n_steps:
                 ckpts.append(cur.clone())
+        ctx.pre = set(pre)
         ctx.solver = solver
         ctx.n_steps = n_steps
         ctx.every = checkpoint_every
@@ -64,7 +94,9 @@ class MPDATAFunction(torch.autograd.Function):
         gcb = [torch.zeros_like(g) for g in gc]
         taped = _tapes_fit(solver, 2 * min(every, n), pb)  # two buffer sets when pipelined
         if ctx.use_graphs and taped:
-            return (None, None, None, None, *_pipelined_backward(solver, ckpts, gc, pb, n, every))
+            pre = {seg for seg in getattr(ctx, "pre", set())}
+            return (None, None, None, None,
+                    *_pipelined_backward(solver, ckpts, gc, pb, n, every, pre, getattr(ctx, "pre_token", None)))
         taped = taped or _tapes_fit(solver, min(every, n), pb)
         if ctx.use_graphs:
             used = []
@@ -83,11 +115,13 @@ class MPDATAFunction(torch.autograd.Function):
             start, end = seg * every, min(seg * every + every, n)
             states = [ckpts[seg]]
             if taped:
+                # every step recorded with its result (the segment's last result is not needed,
+                # but with it the recording is the forward's own fused step where that applies)
                 tapes = torch.empty((end - start, solver.tape_numel()), dtype=pb.dtype, device=pb.device)
                 for s in range(end - start):
-                    nxt = torch.empty_like(states[-1]) if s + 1 < end - start else None
+                    nxt = torch.empty_like(states[-1])
                     solver.adjoint_record(states[-1], gc, tapes[s], psi_next=nxt)
-                    if nxt is not None:
+                    if s + 1 < end - start:
                         states.append(nxt)
                 for s in range(end - start - 1, -1, -1):
                     solver.adjoint_replay(states[s], gc, tapes[s], pb, gc_bar=gcb)
@@ -105,6 +139,15 @@ class MPDATAFunction(torch.autograd.Function):
 tape_budget = None
 
 
+def _fused_record(solver: Mpdata) -> bool:
+    """Whether mpdata_adjoint_record runs the forward's own fused kernel (one 2D field, two
+    passes, FCT or none and no other option), so that a recorded step's result is the
+    forward step's bit for bit."""
+    from . import capi
+    return (len(solver.shapes) == 1 and len(solver.shapes[0]) == 2 and solver.n_iters == 2 and
+            (solver.opts & ~capi.FCT) == 0)
+
+
 def _tapes_fit(solver: Mpdata, length: int, like) -> bool:
     need = length * solver.tape_numel() * like.element_size()
     if tape_budget is not None:
@@ -113,10 +156,12 @@ def _tapes_fit(solver: Mpdata, length: int, like) -> bool:
     return need <= free // 4
 
 
-def _pipelined_backward(solver: Mpdata, ckpts, gc, pb, n: int, every: int):
+def _pipelined_backward(solver: Mpdata, ckpts, gc, pb, n: int, every: int, pre=frozenset(), token=None):
     """The taped backward with graphs, two segments in flight: while one segment's reverse
     sweeps run on one stream, the next segment (earlier in time; it needs only its checkpoint)
-    records its states and tapes on another.  Two buffer sets alternate between segments."""
+    records its states and tapes on another.  Two buffer sets alternate between segments.
+    Segments in `pre` were recorded by the forward into their buffer set, which still holds
+    them if no other rollout has recorded into it since (`token`)."""
     dev = pb.device
     cur = torch.cuda.current_stream(dev)
     gcb = [torch.zeros_like(g) for g in gc]
@@ -140,8 +185,9 @@ def _pipelined_backward(solver: Mpdata, ckpts, gc, pb, n: int, every: int):
         if sg in last_rev:
             s_rec.wait_event(last_rev[sg])
         with torch.cuda.stream(s_rec):
-            sg.states[0].copy_(ckpts[seg])
-            sg.rec_graph.replay()
+            if seg not in pre or token is None or getattr(sg, "owner", None) is not token:
+                sg.states[0].copy_(ckpts[seg])
+                sg.rec_graph.replay()
             recorded = torch.cuda.Event()
             recorded.record(s_rec)
         s_rev.wait_event(recorded)
@@ -152,6 +198,8 @@ def _pipelined_backward(solver: Mpdata, ckpts, gc, pb, n: int, every: int):
             done = torch.cuda.Event()
             done.record(s_rev)
         last_rev[sg] = done
+    for sg in used:
+        sg.owner = None  # a second backward of the same forward recomputes its segments
     with torch.cuda.stream(s_rev):
         for sg in used:
             for acc, b in zip(gcb, sg.gcb):
@@ -184,6 +232,7 @@ class _SegmentGraph:
         self.pb = torch.empty_like(like)
         self.gc = [torch.zeros_like(g) for g in gc_like]
         self.gcb = [torch.zeros_like(g) for g in gc_like]
+        self.spare = torch.empty_like(like)  # the result of a segment's last recorded step
         self.tapes = torch.zeros((length, solver.tape_numel()), dtype=like.dtype, device=like.device) \
             if taped else None
         gc, gcb, tapes = self.gc, self.gcb, self.tapes
@@ -207,7 +256,7 @@ class _SegmentGraph:
                 self.rec_graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(self.rec_graph, stream=side):
                     for s in range(length):
-                        nxt = self.states[s + 1] if s + 1 < length else None
+                        nxt = self.states[s + 1] if s + 1 < length else self.spare
                         solver.adjoint_record(self.states[s], gc, tapes[s], psi_next=nxt)
                 self.rev_graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(self.rev_graph, stream=side):

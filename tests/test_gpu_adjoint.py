@@ -364,3 +364,31 @@ def test_reverse_from_fused_tape_matches_staged_tape_512(name, dtype):
             assert np.abs(a - b).max() <= 1e-12 * scale
         else:
             assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+
+
+def test_forward_recorded_segments_are_used_only_by_their_own_backward():
+    """With graphs and tapes the forward records its last two segments for the backward, in the
+    backward's buffers; a second rollout on the same handle takes those buffers over, and the
+    first rollout's backward then recomputes its segments: the gradients equal those of a
+    rollout whose backward follows its forward directly."""
+    psi0_np, gc_np, pert = workloads.adjoint_2d(64, seed=3)
+    dev = torch.device("cuda")
+    f64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    target = f64(psi0_np + 0.05 * pert)
+
+    def grads(interleave):
+        with Mpdata((64, 64), dtype=torch.float64, n_iters=2, opts=capi.FCT) as m:
+            gg = [f64(v).requires_grad_(True) for v in gc_np]
+            p0 = f64(psi0_np).requires_grad_(True)
+            out = rollout(m, p0, gg, 30, 7)
+            if interleave:
+                q0 = f64(0.9 * psi0_np).requires_grad_(True)
+                other = rollout(m, q0, [f64(1.1 * v).requires_grad_(True) for v in gc_np], 30, 7)
+                assert other.shape == out.shape
+            (0.5 * (out - target) ** 2).sum().backward()
+            torch.cuda.synchronize()
+            return [p0.grad.clone()] + [g.grad.clone() for g in gg]
+
+    direct, interleaved = grads(False), grads(True)
+    for a, b in zip(direct, interleaved):
+        assert torch.allclose(a, b, rtol=1e-12, atol=1e-14 * float(a.abs().max()))
