@@ -8,7 +8,7 @@
 // Work decomposition: a block of warps owns a tile of 32*NC (x) by 8 (y) cells and walks a
 // chunk of z-planes.  Lane l of warp w owns the NC adjacent cells x0 + NC*l .. x0 + NC*l + NC-1
 // of one row, so one 16-byte (NC = 4) shared-memory load brings a row segment of all its cells,
-// and the neighbours just outside the segment come from the neighbouring lanes by shuffles.  The
+// and two more loads the neighbours just outside the segment.  The
 // planes the march reads are staged in shared-memory rings, row by row with four halo cells on
 // each side in x so that every 16-byte chunk of a row is aligned in global and shared memory;
 // each chunk is one cp.async, issued for the next step while this one computes.  The chunks wrap
@@ -73,11 +73,14 @@ struct Plan {
   }
 };
 
-// Row segment of this lane: w[i + 1] is the cell x + i, i = -1 .. NC + 1 (x the lane's first cell);
-// the outer values come from the neighbouring lanes, at the tile's ends from the row's halo.
+// Row segment of this lane: w[i + 1] is the cell x + i, i = -1 .. NC + 1 (x the lane's first cell),
+// read straight from the staged row (its halo cells included): three loads and no shuffles,
+// lane-edge branches or selects (measured 11 % faster over the 3D step than taking the outer
+// values from the neighbouring lanes by shuffles, for about a third more shared-memory wavefronts)
 template <int NC>
 __device__ __forceinline__ void fetch(const float* row, int lane, float (&w)[NC + 3]) {
   const float* p = row + 4 + NC * lane;
+  w[0] = p[-1];
   if constexpr (NC == 4) {
     const float4 v = *reinterpret_cast<const float4*>(p);
     w[1] = v.x; w[2] = v.y; w[3] = v.z; w[4] = v.w;
@@ -85,17 +88,9 @@ __device__ __forceinline__ void fetch(const float* row, int lane, float (&w)[NC 
     const float2 v = *reinterpret_cast<const float2*>(p);
     w[1] = v.x; w[2] = v.y;
   }
-  float L = __shfl_up_sync(kFull, w[NC], 1);
-  float R1 = __shfl_down_sync(kFull, w[1], 1);
-  float R2 = __shfl_down_sync(kFull, w[2], 1);
-  if (lane == 0) L = row[3];
-  if (lane == 31) {
-    R1 = row[4 + 32 * NC];
-    R2 = row[5 + 32 * NC];
-  }
-  w[0] = L;
-  w[NC + 1] = R1;
-  w[NC + 2] = R2;
+  const float2 r = *reinterpret_cast<const float2*>(p + NC);
+  w[NC + 1] = r.x;
+  w[NC + 2] = r.y;
 }
 
 __device__ __forceinline__ float frac1(float n, float d) { return divisible(d) ? __fdividef(n, d) : 0.0f; }
