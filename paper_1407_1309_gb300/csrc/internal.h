@@ -199,6 +199,12 @@ bool antidiff3_vec(const Grid& g, const float* psi, const float* const* v, float
 bool p1b3_vec(const Grid& g, const float* psi, const float* const* v, float vscale, const float* G, bool kahan,
               float* p1, float* mx, float* mn, cudaStream_t st);
 
+// Vectorised FP32 FCT corrective pass (march3.cu): factors, limiter and donor pass as one z-march,
+// same conditions, and neither the Kahan summation nor a source term (post); lim[0] null when the
+// limited advector is not wanted.
+bool corr3_vec(const Grid& g, const float* psi, const float* const* vu, const float* G, bool iga, bool kahan,
+               const float* mx, const float* mn, bool post, float* const* lim, float* out, cudaStream_t st);
+
 // Prognosed velocity and shallow-water sources (vip.cu).  state: h then the momenta q_d, n cells
 // each.  vip_advector: the advector of the step (adv, nd arrays) from the velocities q/h (h > eps)
 // extrapolated to n + 1/2 (ext: nd scratch arrays; uprev: u^{n-1} in, u^n out, ignored when

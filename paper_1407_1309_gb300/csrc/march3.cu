@@ -1,9 +1,10 @@
 // Vectorised 3D z-march kernels (FP32) for fields of at least 128 columns whose x extent is a
 // multiple of 4: the pseudo-advector of Eq. 6 with its multi-dimensional cross terms and
 // third-order terms (Sect. 3.1.1-3.1.2; infinite gauge and |psi| of Sect. 3.1.5) of a corrective
-// pass, and pass 1 (Eqs. 4-5) with the FCT bounds (Sect. 3.1.4).  The FCT corrective pass itself
-// keeps the scalar z-march of staged.cu (a vectorised form of it measured slower at 256^3: its
-// shared-memory rings left one block per SM).
+// pass, pass 1 (Eqs. 4-5) with the FCT bounds (Sect. 3.1.4), and the FCT corrective pass
+// (factors, limiter and donor pass).  The corrective pass keeps in shared memory only what
+// neighbouring rows read (psi, the x and y advector components, the factors) and takes the
+// values only the cell itself reads into registers, so that two blocks fit on an SM.
 //
 // Work decomposition: a block of warps owns a tile of 32*NC (x) by 8 (y) cells and walks a
 // chunk of z-planes.  Lane l of warp w owns the NC adjacent cells x0 + NC*l .. x0 + NC*l + NC-1
@@ -561,6 +562,318 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
   }
 }
 
+// ---------------------------------------------------------------- FCT corrective pass
+// One FCT corrective pass (Sect. 3.1.4: the factors beta_up and beta_dn, the limited advector
+// V min(1, beta, beta), then the donor-cell pass of Eqs. 4-5 with it) as one z-march with lanes
+// of NC cells: the work of the scalar k_corr3 (staged.cu), the same expressions in the same
+// order.  At step s every warp forms the factors of plane s on its row (rows y0-1 .. y0+8) into
+// a ring of three planes; then warps 1 .. kRows limit and advance their row of plane s-1, while
+// warps 0 and kRows+1 form the factors of plane s in the columns just left and right of the
+// tile, which the limiter reads at the next step.  psi and the x and y components of the
+// unlimited advector are staged in shared-memory rings (cp.async, one step ahead); the values
+// that only the cell itself reads (the z component, the bounds and G) come from global memory
+// into registers, also one step ahead.
+constexpr int kKPsiRing = 5, kKVRing = 3, kKBRing = 3;
+constexpr int kKPsiRows = kRows + 4;  // psi: rows y0-2 .. y0+9
+constexpr int kKVRows = kRows + 3;    // x and y components: rows y0-2 .. y0+8
+constexpr int kKBRows = kRows + 2;    // factors: rows y0-1 .. y0+8
+template <int NC>
+constexpr size_t corr3v_smem() {
+  return sizeof(float) * row_w<NC>() * (kKPsiRing * kKPsiRows + 2 * kKVRing * kKVRows + 2 * kKBRing * kKBRows);
+}
+
+// The lane's NC cells of a staged row (no neighbours)
+template <int NC>
+__device__ __forceinline__ void center(const float* row, int lane, float (&w)[NC]) {
+  const float* p = row + 4 + NC * lane;
+  if constexpr (NC == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    w[0] = v.x; w[1] = v.y;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void put(float* dst, const float (&v)[NC]) {
+  if constexpr (NC == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+}
+
+// The FCT factors of one cell: in/out sums of the unlimited fluxes through its six faces
+// (dimensions z, y, x: the neighbours and face advectors on the + and - side), then
+// beta_up = G[psi_max - psi]+ / in and beta_dn = G[psi - psi_min]+ / out, 1 where the sum is not
+// positive
+template <bool UNIT>
+__device__ __forceinline__ void factors1(float p, float pzp, float pzm, float pyp, float pym, float pxp, float pxm,
+                                         float vzp, float vzm, float vyp, float vym, float vxp, float vxm, float Gi,
+                                         float mxi, float mni, float& bu, float& bd) {
+  float in = 0.0f, ou = 0.0f;
+  {
+    const float Fp = fluxv<UNIT>(p, pzp, vzp), Fm = fluxv<UNIT>(pzm, p, vzm);
+    in = in + (posp(Fm) - negp(Fp));
+    ou = ou + (posp(Fp) - negp(Fm));
+  }
+  {
+    const float Fp = fluxv<UNIT>(p, pyp, vyp), Fm = fluxv<UNIT>(pym, p, vym);
+    in = in + (posp(Fm) - negp(Fp));
+    ou = ou + (posp(Fp) - negp(Fm));
+  }
+  {
+    const float Fp = fluxv<UNIT>(p, pxp, vxp), Fm = fluxv<UNIT>(pxm, p, vxm);
+    in = in + (posp(Fm) - negp(Fp));
+    ou = ou + (posp(Fp) - negp(Fm));
+  }
+  bu = in > 0.0f ? __fdividef(Gi * posp(mxi - p), in) : 1.0f;
+  bd = ou > 0.0f ? __fdividef(Gi * posp(p - mni), ou) : 1.0f;
+}
+
+// The limited advector V min(1, a, b) of a face between L and R: the upwind side's outflow
+// factor and the downwind side's inflow factor (by the direction of the unlimited flux)
+template <bool UNIT>
+__device__ __forceinline__ float limited(float L, float R, float V, float buL, float bdL, float buR, float bdR) {
+  const float F = fluxv<UNIT>(L, R, V);
+  const bool right = F > 0.0f || (F == 0.0f && V > 0.0f);
+  const float a = right ? bdL : buL;
+  const float b = right ? buR : bdR;
+  float m = 1.0f;
+  m = minv(a, m);
+  m = minv(b, m);
+  return V * m;
+}
+
+template <int NC, bool NUG, bool UNIT, bool LIM>
+__global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __restrict__ psi, V3 Vu,
+                                                         const float* __restrict__ G, const float* __restrict__ mxg,
+                                                         const float* __restrict__ mng, O3 lim,
+                                                         float* __restrict__ out) {
+  constexpr int W = row_w<NC>();
+  constexpr int nP = kKPsiRows * W, nV = kKVRows * W, nB = kKBRows * W;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* const sP = reinterpret_cast<float*>(smem_raw);  // [5][nP] psi
+  float* const sX = sP + kKPsiRing * nP;                  // [3][nV] x component
+  float* const sY = sX + kKVRing * nV;                    // [3][nV] y component
+  float* const sU = sY + kKVRing * nV;                    // [3][nB] beta_up
+  float* const sD = sU + kKBRing * nB;                    // [3][nB] beta_dn
+  const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
+  const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+  const int x0 = blockIdx.x * 32 * NC, y0 = blockIdx.y * kRows;
+  const int zb = blockIdx.z * kZc;
+  const int ze = zb + kZc < nz ? zb + kZc : nz;
+  const long long plane = static_cast<long long>(ny) * nx;
+  Plan<NC, kKPsiRows, kCThreads> pp;
+  Plan<NC, kKVRows, kCThreads> pv;
+  pp.init(tid, x0, y0 - 2, nx, ny);
+  pv.init(tid, x0, y0 - 2, nx, ny);
+  auto zoff = [&](int z) { return static_cast<long long>(wrapi3(z, nz)) * plane; };
+  auto rot = [](int s, int j, int n) { const int v = s + j; return v >= n ? v - n : v; };
+  // this warp's row y0 - 1 + w and the lane's first column, wrapped, for the register loads
+  const int y = y0 - 1 + w;
+  const long long yo = static_cast<long long>(wrapi3(y, ny)) * nx;
+  const int xl = x0 + NC * lane;
+  const int xw = wrapi3(xl, nx);
+  auto ld = [&](const float* a, long long zo, float (&r)[NC]) {
+    const float* q = a + zo + yo + xw;
+    if constexpr (NC == 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(q));
+      r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(q));
+      r[0] = v.x; r[1] = v.y;
+    }
+  };
+  // ring slots at step s: psi plane s+j (j = -2 .. 2) in rot(kp, j + 2, 5); the x and y
+  // components of plane s+j (j = -1 .. 1) in rot(kv, j + 1, 3); the factors of plane s+j
+  // (j = -2 .. 0) in rot(kb, j + 2, 3).  Registers: the z component of planes s+1 (loading),
+  // s, s-1, s-2; the bounds of plane s+1 (loading); G of planes s+1 (loading), s, s-1.
+  int kp = 0, kv = 0, kb = 0;
+  float vz_n[NC], vz_c[NC], vz_m[NC], vz_mm[NC], mx_n[NC], mn_n[NC], g_n[NC], g_c[NC], g_m[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) { vz_m[c] = 0.0f; g_c[c] = 1.0f; g_n[c] = 1.0f; }
+  {  // prologue (step zb-1): psi planes zb-2 .. zb, components of plane zb-1
+    pp.copy(sP + 1 * nP, psi + zoff(zb - 2), tid);
+    pp.copy(sP + 2 * nP, psi + zoff(zb - 1), tid);
+    pp.copy(sP + 3 * nP, psi + zoff(zb), tid);
+    pv.copy(sX + 1 * nV, Vu.p[2] + zoff(zb - 1), tid);
+    pv.copy(sY + 1 * nV, Vu.p[1] + zoff(zb - 1), tid);
+    cp_commit();
+    ld(Vu.p[0], zoff(zb - 2), vz_c);
+    const long long zo = zoff(zb - 1);
+    ld(Vu.p[0], zo, vz_n);
+    ld(mxg, zo, mx_n);
+    ld(mng, zo, mn_n);
+    if (NUG) ld(G, zo, g_n);
+    cp_wait<0>();
+  }
+  for (int s = zb - 1; s <= ze; ++s) {
+    __syncthreads();  // step s's planes are in (each thread waited for its own copies)
+    float mx_c[NC], mn_c[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      vz_mm[c] = vz_m[c]; vz_m[c] = vz_c[c]; vz_c[c] = vz_n[c];
+      g_m[c] = g_c[c]; g_c[c] = g_n[c];
+      mx_c[c] = mx_n[c]; mn_c[c] = mn_n[c];
+    }
+    if (s + 1 <= ze) {
+      pp.copy(sP + rot(kp, 4, kKPsiRing) * nP, psi + zoff(s + 2), tid);
+      const long long zo = zoff(s + 1);
+      pv.copy(sX + rot(kv, 2, kKVRing) * nV, Vu.p[2] + zo, tid);
+      pv.copy(sY + rot(kv, 2, kKVRing) * nV, Vu.p[1] + zo, tid);
+      ld(Vu.p[0], zo, vz_n);
+      ld(mxg, zo, mx_n);
+      ld(mng, zo, mn_n);
+      if (NUG) ld(G, zo, g_n);
+    }
+    cp_commit();
+    const float* P0 = sP + rot(kp, 2, kKPsiRing) * nP;  // psi of plane s
+    const float* Pp = sP + rot(kp, 3, kKPsiRing) * nP;  // s+1
+    const float* Pm = sP + rot(kp, 1, kKPsiRing) * nP;  // s-1
+    const float* X0 = sX + rot(kv, 1, kKVRing) * nV;    // components of plane s
+    const float* Y0 = sY + rot(kv, 1, kKVRing) * nV;
+    float* const U0 = sU + rot(kb, 2, kKBRing) * nB;    // factors of plane s
+    float* const D0 = sD + rot(kb, 2, kKBRing) * nB;
+    {  // factors of plane s, row y0 - 1 + w (psi and component row w + 1, factor row w)
+      float pc[NC + 3], vx[NC + 3], pu[NC], pd[NC], pzp[NC], pzm[NC], vy[NC], vym[NC];
+      fetch<NC>(P0 + (w + 1) * W, lane, pc);
+      fetch<NC>(X0 + (w + 1) * W, lane, vx);
+      center<NC>(P0 + (w + 2) * W, lane, pu);
+      center<NC>(P0 + w * W, lane, pd);
+      center<NC>(Pp + (w + 1) * W, lane, pzp);
+      center<NC>(Pm + (w + 1) * W, lane, pzm);
+      center<NC>(Y0 + (w + 1) * W, lane, vy);
+      center<NC>(Y0 + w * W, lane, vym);
+      float bu[NC], bd[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int i = c + 1;
+        factors1<UNIT>(pc[i], pzp[c], pzm[c], pu[c], pd[c], pc[i + 1], pc[i - 1], vz_c[c], vz_m[c], vy[c], vym[c],
+                       vx[i], vx[i - 1], NUG ? g_c[c] : 1.0f, mx_c[c], mn_c[c], bu[c], bd[c]);
+      }
+      put<NC>(U0 + w * W + 4 + NC * lane, bu);
+      put<NC>(D0 + w * W + 4 + NC * lane, bd);
+    }
+    __syncthreads();
+    const int q = s - 1;
+    if (w >= 1 && w <= kRows) {
+      if (q >= zb && y < ny) {  // limit and advance row y of plane q = s - 1
+        const float* Q0 = Pm;                                  // psi of plane q
+        const float* Qm = sP + kp * nP;                        // q - 1
+        const float* XQ = sX + kv * nV;                        // components of plane q
+        const float* YQ = sY + kv * nV;
+        const float* UQ = sU + rot(kb, 1, kKBRing) * nB;       // factors of plane q
+        const float* DQ = sD + rot(kb, 1, kKBRing) * nB;
+        const float* UQm = sU + kb * nB;                       // q - 1
+        const float* DQm = sD + kb * nB;
+        // the cells' psi and factors; the donor sum and the limited advectors, dimension by
+        // dimension (z, y, x) so that only one dimension's neighbours are live at a time
+        float p[NC], bu[NC], bd[NC], acc[NC], hz[NC], hy[NC], hx[NC];
+        center<NC>(Q0 + (w + 1) * W, lane, p);
+        center<NC>(UQ + w * W, lane, bu);
+        center<NC>(DQ + w * W, lane, bd);
+        float Gc[NC];  // G of the cells (the divisor of the donor terms)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[c] = p[c]; Gc[c] = NUG ? g_m[c] : 1.0f; }
+        // the donor terms of one dimension: -F+/G then +F-/G, added in that order
+        auto donor_d = [&](int c, float Fp, float Fm) {
+          const float t0 = NUG ? -__fdividef(Fp, Gc[c]) : -Fp;
+          const float t1 = NUG ? __fdividef(Fm, Gc[c]) : Fm;
+          acc[c] = acc[c] + t0;
+          acc[c] = acc[c] + t1;
+        };
+        {  // z
+          float nzp[NC], nzm[NC], uzp[NC], dzp[NC], uzm[NC], dzm[NC];
+          center<NC>(P0 + (w + 1) * W, lane, nzp);
+          center<NC>(Qm + (w + 1) * W, lane, nzm);
+          center<NC>(U0 + w * W, lane, uzp);
+          center<NC>(D0 + w * W, lane, dzp);
+          center<NC>(UQm + w * W, lane, uzm);
+          center<NC>(DQm + w * W, lane, dzm);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const float hp = limited<UNIT>(p[c], nzp[c], vz_m[c], bu[c], bd[c], uzp[c], dzp[c]);
+            const float hm = limited<UNIT>(nzm[c], p[c], vz_mm[c], uzm[c], dzm[c], bu[c], bd[c]);
+            donor_d(c, fluxv<UNIT>(p[c], nzp[c], hp), fluxv<UNIT>(nzm[c], p[c], hm));
+            hz[c] = hp;
+          }
+        }
+        {  // y
+          float nyp[NC], nym[NC], vy[NC], vym[NC], uu[NC], du[NC], ud[NC], dd[NC];
+          center<NC>(Q0 + (w + 2) * W, lane, nyp);
+          center<NC>(Q0 + w * W, lane, nym);
+          center<NC>(YQ + (w + 1) * W, lane, vy);
+          center<NC>(YQ + w * W, lane, vym);
+          center<NC>(UQ + (w + 1) * W, lane, uu);
+          center<NC>(DQ + (w + 1) * W, lane, du);
+          center<NC>(UQ + (w - 1) * W, lane, ud);
+          center<NC>(DQ + (w - 1) * W, lane, dd);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const float hp = limited<UNIT>(p[c], nyp[c], vy[c], bu[c], bd[c], uu[c], du[c]);
+            const float hm = limited<UNIT>(nym[c], p[c], vym[c], ud[c], dd[c], bu[c], bd[c]);
+            donor_d(c, fluxv<UNIT>(p[c], nyp[c], hp), fluxv<UNIT>(nym[c], p[c], hm));
+            hy[c] = hp;
+          }
+        }
+        {  // x: the row segments with their outer neighbours
+          float pc[NC + 3], vx[NC + 3], uc[NC + 3], dc[NC + 3];
+          fetch<NC>(Q0 + (w + 1) * W, lane, pc);
+          fetch<NC>(XQ + (w + 1) * W, lane, vx);
+          fetch<NC>(UQ + w * W, lane, uc);
+          fetch<NC>(DQ + w * W, lane, dc);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int i = c + 1;
+            const float hp = limited<UNIT>(p[c], pc[i + 1], vx[i], bu[c], bd[c], uc[i + 1], dc[i + 1]);
+            const float hm = limited<UNIT>(pc[i - 1], p[c], vx[i - 1], uc[i - 1], dc[i - 1], bu[c], bd[c]);
+            donor_d(c, fluxv<UNIT>(p[c], pc[i + 1], hp), fluxv<UNIT>(pc[i - 1], p[c], hm));
+            hx[c] = hp;
+          }
+        }
+        const long long o = static_cast<long long>(q) * plane + static_cast<long long>(y) * nx + xl;
+        if (xl + NC <= nx) {
+          put<NC>(out + o, acc);
+          if constexpr (LIM) {
+            put<NC>(lim.p[0] + o, hz);
+            put<NC>(lim.p[1] + o, hy);
+            put<NC>(lim.p[2] + o, hx);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (xl + c < nx) {
+              out[o + c] = acc[c];
+              if constexpr (LIM) {
+                lim.p[0][o + c] = hz[c];
+                lim.p[1][o + c] = hy[c];
+                lim.p[2][o + c] = hx[c];
+              }
+            }
+          }
+        }
+      }
+    } else if (s >= zb && s < ze && lane < kRows) {
+      // warps 0 and kRows+1: the factors of plane s in the column left (right) of the tile, factor
+      // row r = lane + 1 (field row y0 + lane), for the limiter of the next step
+      const int r = lane + 1;
+      const int cix = w == 0 ? 3 : 4 + 32 * NC;  // ring column of x0 - 1 (x0 + 32 NC)
+      const long long ce = static_cast<long long>(wrapi3(y0 - 1 + r, ny)) * nx +
+                           wrapi3(w == 0 ? x0 - 1 : x0 + 32 * NC, nx);
+      const long long zs = zoff(s) + ce, zsm = zoff(s - 1) + ce;
+      const int pr = (r + 1) * W + cix;  // psi and component ring index of the cell
+      float bu, bd;
+      factors1<UNIT>(P0[pr], Pp[pr], Pm[pr], P0[pr + W], P0[pr - W], P0[pr + 1], P0[pr - 1], Vu.p[0][zs],
+                     Vu.p[0][zsm], Y0[pr], Y0[pr - W], X0[pr], X0[pr - 1], NUG ? G[zs] : 1.0f, mxg[zs], mng[zs], bu,
+                     bd);
+      U0[r * W + cix] = bu;
+      D0[r * W + cix] = bd;
+    }
+    cp_wait<0>();
+    kp = rot(kp, 1, kKPsiRing);
+    kv = rot(kv, 1, kKVRing);
+    kb = rot(kb, 1, kKBRing);
+  }
+}
+
 template <int NC, int MINB, bool ABS, bool IGA, bool TOT, bool NUG>
 void launch_v(const Grid& g, const float* psi, const float* const* v, float vscale, const float* G, float* const* out,
               cudaStream_t st) {
@@ -589,6 +902,21 @@ void launch_b(const Grid& g, const float* psi, const float* const* v, float vsca
                   static_cast<unsigned>((g.n[1] + kRows - 1) / kRows), static_cast<unsigned>((g.n[0] + kZc - 1) / kZc));
   V3 vv{{v[0], v[1], v[2]}};
   k_p1b3v<NC, KAHAN, NUG><<<grid, dim3(32, kCWarps), p1b3v_smem<NC>(), st>>>(g, psi, vv, vscale, G, p1, mx, mn);
+}
+
+template <int NC, bool NUG, bool UNIT, bool LIM>
+void launch_k(const Grid& g, const float* psi, const float* const* vu, const float* G, const float* mx,
+              const float* mn, float* const* lim, float* out, cudaStream_t st) {
+  static PerDevice<bool> attr;
+  attr.get([](int) {
+    return cudaFuncSetAttribute(k_corr3v<NC, NUG, UNIT, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(corr3v_smem<NC>())) == cudaSuccess;
+  });
+  const dim3 grid(static_cast<unsigned>((g.n[2] + 32 * NC - 1) / (32 * NC)),
+                  static_cast<unsigned>((g.n[1] + kRows - 1) / kRows), static_cast<unsigned>((g.n[0] + kZc - 1) / kZc));
+  V3 vv{{vu[0], vu[1], vu[2]}};
+  O3 lo{{lim[0], lim[1], lim[2]}};
+  k_corr3v<NC, NUG, UNIT, LIM><<<grid, dim3(32, kCWarps), corr3v_smem<NC>(), st>>>(g, psi, vv, G, mx, mn, lo, out);
 }
 
 // The vectorised z-march runs with lanes of 4 cells on fields of at least 128 columns; narrower
@@ -644,6 +972,28 @@ bool p1b3_vec(const Grid& g, const float* psi, const float* const* v, float vsca
   } while (0)
   if (kahan) MPD_B(true); else MPD_B(false);
 #undef MPD_B
+  return true;
+}
+
+// The vectorised FCT corrective pass (FP32; same conditions as antidiff3_vec, and neither the
+// Kahan summation nor a source term); false (nothing launched) otherwise.
+bool corr3_vec(const Grid& g, const float* psi, const float* const* vu, const float* G, bool iga, bool kahan,
+               const float* mx, const float* mn, bool post, float* const* lim, float* out, cudaStream_t st) {
+  if (g.nd != 3 || g.n[2] % 4 != 0 || g.any_open() || kahan || post) return false;
+  if (!al16(psi) || !al16(G) || !al16(vu[0]) || !al16(vu[1]) || !al16(vu[2]) || !al16(mx) || !al16(mn) ||
+      !al16(out) || !al16(lim[0]) || !al16(lim[1]) || !al16(lim[2]) || !use_vec(g))
+    return false;
+  const bool nug = G != nullptr, lm = lim[0] != nullptr;
+#define MPD_K(N, U, L) launch_k<4, N, U, L>(g, psi, vu, G, mx, mn, lim, out, st)
+#define MPD_KL(N, U) \
+  do { if (lm) MPD_K(N, U, true); else MPD_K(N, U, false); } while (0)
+#define MPD_KU(N) \
+  do { if (iga) MPD_KL(N, true); else MPD_KL(N, false); } while (0)
+  if (nug) MPD_KU(true);
+  else MPD_KU(false);
+#undef MPD_KU
+#undef MPD_KL
+#undef MPD_K
   return true;
 }
 

@@ -1295,12 +1295,17 @@ cudaError_t staged_nd(const Grid& g, const Opts& o, const StepArgs<T>& a, const 
     In3<T> vuse{{vk.p[0], vk.p[1], vk.p[2]}};
     // FP32: factors, limiter and donor pass in one z-march (it limits each face from both sides
     // and forms the factors on a one-cell halo: cheaper than the array traffic it saves in
-    // FP32, dearer in FP64, which the arithmetic bounds)
+    // FP32, dearer in FP64, which the arithmetic bounds); lanes of 4 cells (march3.cu) where
+    // the field allows, else one cell per thread
     if (ND == 3 && o.fct && sizeof(T) == 4 && !o.open) {
       T* dst = (k == K) ? a.psi_out : (prev == s.pa ? s.pb : s.pa);
       Out3<T> lk{{nullptr, nullptr, nullptr}};
       if (k < K) lk = Out3<T>{{lim[0], lim[1], lim[2]}};
-      launch_corr3<T>(g, prev, vuse, G, o.iga, o.kahan, s.mx, s.mn, a.r, a.dt, k == K && o.rhs_a, lk, dst, st);
+      bool done = false;
+      if constexpr (sizeof(T) == 4)
+        done = corr3_vec(g, prev, vuse.p, G, o.iga, o.kahan, s.mx, s.mn, k == K && o.rhs_a, lk.p, dst, st);
+      if (!done)
+        launch_corr3<T>(g, prev, vuse, G, o.iga, o.kahan, s.mx, s.mn, a.r, a.dt, k == K && o.rhs_a, lk, dst, st);
       prev = dst;
       vprev = In3<T>{{lim[0], lim[1], lim[2]}};
       vscale = T(1);
