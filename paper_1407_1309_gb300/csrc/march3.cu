@@ -572,14 +572,18 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
 // tile, which the limiter reads at the next step.  psi and the x and y components of the
 // unlimited advector are staged in shared-memory rings (cp.async, one step ahead); the values
 // that only the cell itself reads (the z component, the bounds and G) come from global memory
-// into registers, also one step ahead.
+// into registers, also one step ahead (those of the cells beside the tile into a small ring).
 constexpr int kKPsiRing = 5, kKVRing = 3, kKBRing = 3;
 constexpr int kKPsiRows = kRows + 4;  // psi: rows y0-2 .. y0+9
 constexpr int kKVRows = kRows + 3;    // x and y components: rows y0-2 .. y0+8
 constexpr int kKBRows = kRows + 2;    // factors: rows y0-1 .. y0+8
+// the z component, the bounds and G of the cells just left and right of the tile (rows y0 ..
+// y0+7), whose factors warps 0 and kRows+1 form: a ring of three planes, 4 arrays each
+constexpr int kKHRing = 3, kKHCells = 2 * kRows;
 template <int NC>
 constexpr size_t corr3v_smem() {
-  return sizeof(float) * row_w<NC>() * (kKPsiRing * kKPsiRows + 2 * kKVRing * kKVRows + 2 * kKBRing * kKBRows);
+  return sizeof(float) * (row_w<NC>() * (kKPsiRing * kKPsiRows + 2 * kKVRing * kKVRows + 2 * kKBRing * kKBRows) +
+                           kKHRing * 4 * kKHCells);
 }
 
 // The lane's NC cells of a staged row (no neighbours)
@@ -655,6 +659,7 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
   float* const sY = sX + kKVRing * nV;                    // [3][nV] y component
   float* const sU = sY + kKVRing * nV;                    // [3][nB] beta_up
   float* const sD = sU + kKBRing * nB;                    // [3][nB] beta_dn
+  float* const sH = sD + kKBRing * nB;                    // [3][4][kKHCells] halo cells' vz, mx, mn, G
   const int nz = g.n[0], ny = g.n[1], nx = g.n[2];
   const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
   const int x0 = blockIdx.x * 32 * NC, y0 = blockIdx.y * kRows;
@@ -686,7 +691,19 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
   // components of plane s+j (j = -1 .. 1) in rot(kv, j + 1, 3); the factors of plane s+j
   // (j = -2 .. 0) in rot(kb, j + 2, 3).  Registers: the z component of planes s+1 (loading),
   // s, s-1, s-2; the bounds of plane s+1 (loading); G of planes s+1 (loading), s, s-1.
-  int kp = 0, kv = 0, kb = 0;
+  int kp = 0, kv = 0, kb = 0, kh = 0;
+  // halo-cell arrays of plane s+j (j = -1 .. 1) in ring slot rot(kh, j + 1, 3); thread tid <
+  // 4 kKHCells copies array ha (the z component, the bounds, G) of cell hk (the left column for
+  // hk < kRows; field row y0 + hk % kRows)
+  auto copy_h = [&](int slot, long long zo) {
+    const int ha = tid / kKHCells, hk = tid - ha * kKHCells;
+    if (tid < 4 * kKHCells && (ha < 3 || NUG)) {
+      const float* src = ha == 0 ? Vu.p[0] : (ha == 1 ? mxg : (ha == 2 ? mng : G));
+      const long long off = static_cast<long long>(wrapi3(y0 + hk % kRows, ny)) * nx +
+                            wrapi3(hk < kRows ? x0 - 1 : x0 + 32 * NC, nx);
+      cp_async<4>(sH + (slot * 4 + ha) * kKHCells + hk, src + zo + off);
+    }
+  };
   float vz_n[NC], vz_c[NC], vz_m[NC], vz_mm[NC], mx_n[NC], mn_n[NC], g_n[NC], g_c[NC], g_m[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) { vz_m[c] = 0.0f; g_c[c] = 1.0f; g_n[c] = 1.0f; }
@@ -696,6 +713,7 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
     pp.copy(sP + 3 * nP, psi + zoff(zb), tid);
     pv.copy(sX + 1 * nV, Vu.p[2] + zoff(zb - 1), tid);
     pv.copy(sY + 1 * nV, Vu.p[1] + zoff(zb - 1), tid);
+    copy_h(1, zoff(zb - 1));
     cp_commit();
     ld(Vu.p[0], zoff(zb - 2), vz_c);
     const long long zo = zoff(zb - 1);
@@ -719,6 +737,7 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
       const long long zo = zoff(s + 1);
       pv.copy(sX + rot(kv, 2, kKVRing) * nV, Vu.p[2] + zo, tid);
       pv.copy(sY + rot(kv, 2, kKVRing) * nV, Vu.p[1] + zo, tid);
+      copy_h(rot(kh, 2, kKHRing), zo);
       ld(Vu.p[0], zo, vz_n);
       ld(mxg, zo, mx_n);
       ld(mng, zo, mn_n);
@@ -856,14 +875,13 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
       // row r = lane + 1 (field row y0 + lane), for the limiter of the next step
       const int r = lane + 1;
       const int cix = w == 0 ? 3 : 4 + 32 * NC;  // ring column of x0 - 1 (x0 + 32 NC)
-      const long long ce = static_cast<long long>(wrapi3(y0 - 1 + r, ny)) * nx +
-                           wrapi3(w == 0 ? x0 - 1 : x0 + 32 * NC, nx);
-      const long long zs = zoff(s) + ce, zsm = zoff(s - 1) + ce;
-      const int pr = (r + 1) * W + cix;  // psi and component ring index of the cell
+      const int pr = (r + 1) * W + cix;          // psi and component ring index of the cell
+      const float* Hs = sH + rot(kh, 1, kKHRing) * 4 * kKHCells + (w == 0 ? 0 : kRows) + lane;  // plane s
+      const float* Hm = sH + kh * 4 * kKHCells + (w == 0 ? 0 : kRows) + lane;                   // s - 1
       float bu, bd;
-      factors1<UNIT>(P0[pr], Pp[pr], Pm[pr], P0[pr + W], P0[pr - W], P0[pr + 1], P0[pr - 1], Vu.p[0][zs],
-                     Vu.p[0][zsm], Y0[pr], Y0[pr - W], X0[pr], X0[pr - 1], NUG ? G[zs] : 1.0f, mxg[zs], mng[zs], bu,
-                     bd);
+      factors1<UNIT>(P0[pr], Pp[pr], Pm[pr], P0[pr + W], P0[pr - W], P0[pr + 1], P0[pr - 1], Hs[0], Hm[0], Y0[pr],
+                     Y0[pr - W], X0[pr], X0[pr - 1], NUG ? Hs[3 * kKHCells] : 1.0f, Hs[kKHCells],
+                     Hs[2 * kKHCells], bu, bd);
       U0[r * W + cix] = bu;
       D0[r * W + cix] = bd;
     }
@@ -871,6 +889,7 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
     kp = rot(kp, 1, kKPsiRing);
     kv = rot(kv, 1, kKVRing);
     kb = rot(kb, 1, kKBRing);
+    kh = rot(kh, 1, kKHRing);
   }
 }
 
