@@ -94,6 +94,24 @@ __device__ __forceinline__ void fetch(const float* row, int lane, float (&w)[NC 
   w[NC + 2] = r.y;
 }
 
+// The lane's NC cells of a staged row (no neighbours)
+template <int NC>
+__device__ __forceinline__ void center(const float* row, int lane, float (&w)[NC]) {
+  const float* p = row + 4 + NC * lane;
+  if constexpr (NC == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  } else {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    w[0] = v.x; w[1] = v.y;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void put(float* dst, const float (&v)[NC]) {
+  if constexpr (NC == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+}
+
 __device__ __forceinline__ float frac1(float n, float d) { return divisible(d) ? __fdividef(n, d) : 0.0f; }
 // n1/d and n2/d with one guard and one approximate reciprocal (0 when d == 0)
 __device__ __forceinline__ void frac2v(float n1, float n2, float d, float& r1, float& r2) {
@@ -437,7 +455,7 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
   const int xw = wrapi3(xl, nx);
   constexpr bool nug = NUG;
   // psi^(1) of the cell in column col of this warp's row of plane z, element by element
-  auto pass1_col = [&](int col, long long zo) {
+  auto pass1_col = [&](int col, float Gi) {
     const float* N0 = Np(0) + (w + 1) * W;
     const float* X0 = Xp(0) + w * W;
     const float* Y0 = Yp(0);
@@ -445,74 +463,82 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
     const float nm[3] = {Np(-1)[(w + 1) * W + col], N0[col - W], N0[col - 1]};
     const float vp[3] = {Zp(0)[w * W + col] * vscale, Y0[(w + 1) * W + col] * vscale, X0[col] * vscale};
     const float vm[3] = {Zp(-1)[w * W + col] * vscale, Y0[w * W + col] * vscale, X0[col - 1] * vscale};
-    const float Gi = nug ? G[zo + yoff + wrapi3(x0 - 4 + col, nx)] : 1.0f;
     return donor1<KAHAN>(N0[col], np, nm, vp, vm, Gi, nug);
   };
+  // G of the lane's cells in this warp's row, and (lanes 0 and 31) of the cell left (right) of the
+  // tile, loaded one plane ahead
+  const int hcol = lane == 0 ? 3 : 4 + 32 * NC;  // ring column of the edge lanes' extra cell
+  const long long hoff = yoff + wrapi3(x0 - 4 + hcol, nx);
+  float g_n[NC], gh_n = 1.0f;
+  auto load_g = [&](long long zo) {
+    if constexpr (NUG) {
+      const long long gb = zo + yoff + xw;
+      if constexpr (NC == 4) {
+        const float4 c = __ldg(reinterpret_cast<const float4*>(G + gb));
+        g_n[0] = c.x; g_n[1] = c.y; g_n[2] = c.z; g_n[3] = c.w;
+      } else {
+        const float2 c = __ldg(reinterpret_cast<const float2*>(G + gb));
+        g_n[0] = c.x; g_n[1] = c.y;
+      }
+      if (lane == 0 || lane == 31) gh_n = __ldg(G + zo + hoff);
+    }
+  };
+#pragma unroll
+  for (int c = 0; c < NC; ++c) g_n[c] = 1.0f;
+  load_g(zoff(zb - 1));
   for (int z = zb - 1; z <= ze; ++z) {
     __syncthreads();  // step z's planes are in (each thread waited for its own copies)
+    float gi[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) gi[c] = g_n[c];
+    const float gh = gh_n;
     if (z + 1 <= ze) {
       pn.copy(Np(2), psi + zoff(z + 2), tid);
       const long long zo = zoff(z + 1);
       pz.copy(Zp(1), V.p[0] + zo, tid);
       px.copy(Xp(1), V.p[2] + zo, tid);
       py.copy(Yp(1), V.p[1] + zo, tid);
+      load_g(zo);
     }
     cp_commit();
     {  // psi^(1) of plane z, row yb
-      const long long zo = zoff(z);
-      float n0[NC + 3], nu[NC + 3], nd[NC + 3], nzp[NC + 3], nzm[NC + 3];
+      float n0[NC + 3], vx[NC + 3], nu[NC], nd[NC], nzp[NC], nzm[NC], vy[NC], vym[NC], vz[NC], vzm[NC];
       fetch<NC>(Np(0) + (w + 1) * W, lane, n0);
-      fetch<NC>(Np(0) + (w + 2) * W, lane, nu);
-      fetch<NC>(Np(0) + w * W, lane, nd);
-      fetch<NC>(Np(1) + (w + 1) * W, lane, nzp);
-      fetch<NC>(Np(-1) + (w + 1) * W, lane, nzm);
-      float vx[NC + 3], vy[NC + 3], vym[NC + 3], vz[NC + 3], vzm[NC + 3];
       fetch<NC>(Xp(0) + w * W, lane, vx);
-      fetch<NC>(Yp(0) + (w + 1) * W, lane, vy);
-      fetch<NC>(Yp(0) + w * W, lane, vym);
-      fetch<NC>(Zp(0) + w * W, lane, vz);
-      fetch<NC>(Zp(-1) + w * W, lane, vzm);
-      float gi[NC];
-      if constexpr (NUG) {
-        const long long gb = zo + yoff + xw;
-        if constexpr (NC == 4) {
-          const float4 c = *reinterpret_cast<const float4*>(G + gb);
-          gi[0] = c.x; gi[1] = c.y; gi[2] = c.z; gi[3] = c.w;
-        } else {
-          const float2 c = *reinterpret_cast<const float2*>(G + gb);
-          gi[0] = c.x; gi[1] = c.y;
-        }
-      }
+      center<NC>(Np(0) + (w + 2) * W, lane, nu);
+      center<NC>(Np(0) + w * W, lane, nd);
+      center<NC>(Np(1) + (w + 1) * W, lane, nzp);
+      center<NC>(Np(-1) + (w + 1) * W, lane, nzm);
+      center<NC>(Yp(0) + (w + 1) * W, lane, vy);
+      center<NC>(Yp(0) + w * W, lane, vym);
+      center<NC>(Zp(0) + w * W, lane, vz);
+      center<NC>(Zp(-1) + w * W, lane, vzm);
       float r[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int i = c + 1;
-        const float np[3] = {nzp[i], nu[i], n0[i + 1]}, nm[3] = {nzm[i], nd[i], n0[i - 1]};
-        const float vp[3] = {vz[i] * vscale, vy[i] * vscale, vx[i] * vscale};
-        const float vm[3] = {vzm[i] * vscale, vym[i] * vscale, vx[i - 1] * vscale};
+        const float np[3] = {nzp[c], nu[c], n0[i + 1]}, nm[3] = {nzm[c], nd[c], n0[i - 1]};
+        const float vp[3] = {vz[c] * vscale, vy[c] * vscale, vx[i] * vscale};
+        const float vm[3] = {vzm[c] * vscale, vym[c] * vscale, vx[i - 1] * vscale};
         r[c] = donor1<KAHAN>(n0[i], np, nm, vp, vm, nug ? gi[c] : 1.0f, nug);
       }
-      float* Q = Qp(0) + w * W + 4 + NC * lane;
-      if constexpr (NC == 4) *reinterpret_cast<float4*>(Q) = make_float4(r[0], r[1], r[2], r[3]);
-      else *reinterpret_cast<float2*>(Q) = make_float2(r[0], r[1]);
-      if (lane == 0) Qp(0)[w * W + 3] = pass1_col(3, zo);
-      if (lane == 31) Qp(0)[w * W + 4 + 32 * NC] = pass1_col(4 + 32 * NC, zo);
+      put<NC>(Qp(0) + w * W + 4 + NC * lane, r);
+      if (lane == 0 || lane == 31) Qp(0)[w * W + hcol] = pass1_col(hcol, gh);
     }
     __syncthreads();
     const int q = z - 1;
     if (w >= 1 && w <= kRows && q >= zb && yb < ny) {  // bounds of plane q, row yb
-      float a0[NC + 3], au[NC + 3], ad[NC + 3], azp[NC + 3], azm[NC + 3];
-      float b0[NC + 3], bu[NC + 3], bd[NC + 3], bzp[NC + 3], bzm[NC + 3];
+      float a0[NC + 3], b0[NC + 3], au[NC], ad[NC], azp[NC], azm[NC], bu[NC], bd[NC], bzp[NC], bzm[NC];
       fetch<NC>(Np(-1) + (w + 1) * W, lane, a0);
-      fetch<NC>(Np(-1) + (w + 2) * W, lane, au);
-      fetch<NC>(Np(-1) + w * W, lane, ad);
-      fetch<NC>(Np(0) + (w + 1) * W, lane, azp);
-      fetch<NC>(Np(-2) + (w + 1) * W, lane, azm);
       fetch<NC>(Qp(-1) + w * W, lane, b0);
-      fetch<NC>(Qp(-1) + (w + 1) * W, lane, bu);
-      fetch<NC>(Qp(-1) + (w - 1) * W, lane, bd);
-      fetch<NC>(Qp(0) + w * W, lane, bzp);
-      fetch<NC>(Qp(-2) + w * W, lane, bzm);
+      center<NC>(Np(-1) + (w + 2) * W, lane, au);
+      center<NC>(Np(-1) + w * W, lane, ad);
+      center<NC>(Np(0) + (w + 1) * W, lane, azp);
+      center<NC>(Np(-2) + (w + 1) * W, lane, azm);
+      center<NC>(Qp(-1) + (w + 1) * W, lane, bu);
+      center<NC>(Qp(-1) + (w - 1) * W, lane, bd);
+      center<NC>(Qp(0) + w * W, lane, bzp);
+      center<NC>(Qp(-2) + w * W, lane, bzm);
       float hi[NC], lo[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -520,8 +546,8 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
         float h = a0[i] > b0[i] ? a0[i] : b0[i];
         float l = a0[i] < b0[i] ? a0[i] : b0[i];
         // neighbours in the order z-1, z+1, y-1, y+1, x-1, x+1; psi^n before psi^(1)
-        const float ca[6] = {azm[i], azp[i], ad[i], au[i], a0[i - 1], a0[i + 1]};
-        const float cb[6] = {bzm[i], bzp[i], bd[i], bu[i], b0[i - 1], b0[i + 1]};
+        const float ca[6] = {azm[c], azp[c], ad[c], au[c], a0[i - 1], a0[i + 1]};
+        const float cb[6] = {bzm[c], bzp[c], bd[c], bu[c], b0[i - 1], b0[i + 1]};
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
           h = ca[j] > h ? ca[j] : h;
@@ -584,24 +610,6 @@ template <int NC>
 constexpr size_t corr3v_smem() {
   return sizeof(float) * (row_w<NC>() * (kKPsiRing * kKPsiRows + 2 * kKVRing * kKVRows + 2 * kKBRing * kKBRows) +
                            kKHRing * 4 * kKHCells);
-}
-
-// The lane's NC cells of a staged row (no neighbours)
-template <int NC>
-__device__ __forceinline__ void center(const float* row, int lane, float (&w)[NC]) {
-  const float* p = row + 4 + NC * lane;
-  if constexpr (NC == 4) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-  } else {
-    const float2 v = *reinterpret_cast<const float2*>(p);
-    w[0] = v.x; w[1] = v.y;
-  }
-}
-template <int NC>
-__device__ __forceinline__ void put(float* dst, const float (&v)[NC]) {
-  if constexpr (NC == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-  else *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
 }
 
 // The FCT factors of one cell: in/out sums of the unlimited fluxes through its six faces
