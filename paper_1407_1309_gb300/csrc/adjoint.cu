@@ -12,6 +12,7 @@
 //                   psi^(1): scatter (atomics)
 //   ka_donor_flux   (no FCT) donor-cell pass k: gather
 //   ka_antidiff     (no FCT) antidiffusive advector: scatter (atomics)
+// (the pseudo-advector's reverse has a second form, for the third-order terms and |psi|)
 //   ka_donor_flux   the first pass, which writes the step's outputs
 //
 // Adjoint arrays that receive scatters start at zero; the others are set by their
@@ -19,7 +20,7 @@
 // Conventions at the kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0
 // there), a max/min passes the derivative of the first extremal candidate in the
 // forward candidate order, the limiter's min(1, a, b) that of the first minimum.
-// The third-order terms and the source terms have no adjoint here.
+// The divergent-flow term and the source terms have no adjoint here.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -34,11 +35,10 @@ template <typename T> __device__ __forceinline__ T dpos(T x) { return x > T(0) ?
 template <typename T> __device__ __forceinline__ T dneg(T x) { return x < T(0) ? T(1) : (x > T(0) ? T(0) : T(0.5)); }
 template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 template <typename T> __device__ __forceinline__ T absv(T x) { return x < T(0) ? -x : x; }
-// x > 0, x < 0, x != 0 and a < b: native for FP32; FP64 on the integer pipe (the FP64 kernels
-// are bound by the FP64 pipe; stencil2d.cuh), the same results for finite arguments up to the
-// sign of a zero
+// x > 0, x < 0, x != 0 and a < b: native for FP32 (x < 0 only in the generic templates above);
+// FP64 on the integer pipe (the FP64 kernels are bound by the FP64 pipe; stencil2d.cuh), the
+// same results for finite arguments up to the sign of a zero
 __device__ __forceinline__ bool gtz(float x) { return x > 0.0f; }
-__device__ __forceinline__ bool ltz(float x) { return x < 0.0f; }
 __device__ __forceinline__ bool nez(float x) { return x != 0.0f; }
 __device__ __forceinline__ bool lt(float a, float b) { return a < b; }
 __device__ __forceinline__ bool gtz(double x) { return dev::gt0(x); }
@@ -103,6 +103,9 @@ struct Nbr {
   }
   __device__ __forceinline__ long long at(int d, int s) const { return i + off[d][s + 2]; }
   __device__ __forceinline__ long long at2(int d, int s, int q, int t) const { return i + off[d][s + 2] + off[q][t + 2]; }
+  __device__ __forceinline__ long long at3(int d, int s, int q, int t, int e, int u) const {
+    return i + off[d][s + 2] + off[q][t + 2] + off[e][u + 2];
+  }
 };
 
 // 2D: 32-bit cell indices (the reverse step refuses 2D fields of 2^31 cells or more) and the
@@ -276,16 +279,162 @@ __device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const declt
   atomicAdd(&vhb.p[d][i], gV);
 }
 
+// The same with the options the form above leaves out, selected at run time: |psi| in every
+// psi-fraction (abs_psi, Sect. 3.1.5; d|psi|/dpsi = sgn psi, 0 at 0) and the third-order terms
+// (tot, Sect. 3.1.2), with C = V/Gb and C_q = Vq/Gb:
+//   + Gb (3 C|C| - 2 C^3 - C)/3 D_dd + sum_q Gb |C| C_q (1 - 2|C|) D_dq - (2/3) Gb C C_q1 C_q2 D_q1q2
+// D_dd = (psi_{i+2} - psi_{i+1} - psi_i + psi_{i-1}) over their sum along d; D_dq = ((psi at
+// i+e_d+e_q) - (i+e_q) - (i+e_d-e_q) + (i-e_q)) over their sum; D_q1q2 the same of the four
+// pairs psi_j + psi_{j+e_d} at j = i +-e_q1 +-e_q2, signs (+,+) +, (+,-) -, (-,+) -, (-,-) +
+// (over their count, 4, 4 and 8, under infinite gauge).  A fraction n/S of values with signs s_j
+// in n has the derivatives (s_j - n/S)/S.  Scatters to pb and vhb.
+template <typename T, int ND>
+__device__ __forceinline__ void antidiff_face_rev_ext(const Nbr<ND>& nb, const decltype(Nbr<ND>::i) i, const int d,
+                                                      const T gout, const T* __restrict__ psi, const P3<T>& Vin,
+                                                      const T* __restrict__ G, const bool iga, const bool tot,
+                                                      const bool abs_psi, T* pb, const W3<T>& vhb) {
+  using I = decltype(Nbr<ND>::i);
+  auto ps = [&](I j) { return abs_psi ? absv(psi[j]) : psi[j]; };
+  auto scat = [&](I j, T v) { atomicAdd(&pb[j], abs_psi ? v * sgn(psi[j]) : v); };
+  // a fraction and its derivatives for the entries of sign +1 (kp) and -1 (km); cnt under infinite gauge
+  auto fraction = [&](T n, T S, T cnt, T& D, T& kp, T& km) {
+    if (iga) {
+      D = n / cnt; kp = T(1) / cnt; km = T(-1) / cnt;
+    } else if (dev::divisible(S)) {
+      const T r = adiv(T(1), S);
+      D = n * r; kp = (T(1) - D) * r; km = (T(-1) - D) * r;
+    } else {
+      D = kp = km = T(0);
+    }
+  };
+  const auto ip = nb.at(d, +1);
+  const T Gb = G ? T(0.5) * (G[i] + G[ip]) : T(1);
+  const T V = Vin.p[d][i];
+  const T p0 = ps(i), p1 = ps(ip);
+  T A, dA0, dA1;
+  if (iga) {
+    A = (p1 - p0) * T(0.5); dA0 = T(-0.5); dA1 = T(0.5);
+  } else {
+    const T s = p0 + p1;
+    if (dev::divisible(s)) {
+      const T r = adiv(T(1), s);
+      A = (p1 - p0) * r; dA0 = T(-2) * p1 * (r * r); dA1 = T(2) * p0 * (r * r);
+    } else {
+      A = dA0 = dA1 = T(0);
+    }
+  }
+  const T rGb = G ? adiv(T(1), Gb) : T(1);
+  const T c = absv(V) - V * V * rGb;
+  T gV = gout * (sgn(V) - T(2) * V * rGb) * A;
+  scat(i, gout * c * dA0);
+  scat(ip, gout * c * dA1);
+  const T aV = absv(V), sV = sgn(V);
+  const T c2 = aV * rGb * (T(1) - T(2) * aV * rGb);     // the coefficient of Vq D_dq
+  const T dc2 = sV * (rGb - T(4) * aV * (rGb * rGb));   // and its derivative in V
+  T Vq[3] = {T(0), T(0), T(0)}, gVq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    if (q == d) continue;
+    const auto iqp = nb.at(q, +1), idqp = nb.at2(q, +1, d, +1);
+    const auto iqm = nb.at(q, -1), idqm = nb.at2(q, -1, d, +1);
+    const T* Q = Vin.p[q];
+    Vq[q] = T(0.25) * ((Q[i] + Q[ip]) + (Q[iqm] + Q[idqm]));
+    const T a = ps(iqp), b = ps(idqp), e = ps(iqm), f = ps(idqm);
+    const T Tp = a + b, Bt = e + f;
+    T B, dBT, dBB;
+    if (iga) {
+      B = (Tp - Bt) * T(0.25); dBT = T(0.25); dBB = T(-0.25);
+    } else {
+      const T S = Tp + Bt;
+      if (dev::divisible(S)) {
+        const T r = adiv(T(1), S);
+        B = (Tp - Bt) * r; dBT = T(2) * Bt * (r * r); dBB = T(-2) * Tp * (r * r);
+      } else {
+        B = dBT = dBB = T(0);
+      }
+    }
+    gV += gout * (T(-0.5) * Vq[q] * rGb * B);
+    gVq[q] = gout * (T(-0.5) * V * rGb * B);
+    const T gB = gout * (T(-0.5) * V * Vq[q] * rGb);
+    T ga = gB * dBT, gb = gB * dBT, ge = gB * dBB, gf = gB * dBB;
+    if (tot) {  // D_dq
+      T D2, kp, km;
+      fraction((b - a) - (f - e), (a + b) + (e + f), T(4), D2, kp, km);
+      gV += gout * dc2 * Vq[q] * D2;
+      gVq[q] += gout * c2 * D2;
+      const T g2 = gout * c2 * Vq[q];
+      gb += g2 * kp; ga += g2 * km; gf += g2 * km; ge += g2 * kp;
+    }
+    scat(iqp, ga);
+    scat(idqp, gb);
+    scat(iqm, ge);
+    scat(idqm, gf);
+  }
+  if (tot) {
+    {  // D_dd
+      const auto im = nb.at(d, -1), ip2 = nb.at(d, +2);
+      const T pm = ps(im), p2 = ps(ip2);
+      T D, kp, km;
+      fraction(((p2 - p1) - p0) + pm, ((p2 + p1) + p0) + pm, T(4), D, kp, km);
+      const T cD = ((T(3) * V * aV) * rGb - (T(2) * V * V * V) * (rGb * rGb) - V) * (T(1) / T(3));
+      gV += gout * ((T(6) * aV * rGb - T(6) * V * V * (rGb * rGb) - T(1)) * (T(1) / T(3))) * D;
+      const T gd = gout * cD;
+      scat(ip2, gd * kp);
+      scat(ip, gd * km);
+      scat(i, gd * km);
+      scat(im, gd * kp);
+    }
+    if constexpr (ND == 3) {  // D_q1q2: q1 < q2 the two dimensions other than d
+      const int q1 = d == 0 ? 1 : 0, q2 = d == 2 ? 1 : 2;
+      const int s1[4] = {+1, +1, -1, -1}, s2[4] = {+1, -1, +1, -1};
+      I j0[4], j1[4];
+      T pr[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        j0[k] = nb.at2(q1, s1[k], q2, s2[k]);
+        j1[k] = nb.at3(q1, s1[k], q2, s2[k], d, +1);
+        pr[k] = ps(j0[k]) + ps(j1[k]);
+      }
+      T D3, kp, km;
+      fraction((pr[0] - pr[1]) - (pr[2] - pr[3]), (pr[0] + pr[1]) + (pr[2] + pr[3]), T(8), D3, kp, km);
+      const T w3 = T(-2) / T(3) * (rGb * rGb);
+      gV += gout * (w3 * Vq[q1] * Vq[q2]) * D3;
+      gVq[q1] += gout * (w3 * V * Vq[q2]) * D3;
+      gVq[q2] += gout * (w3 * V * Vq[q1]) * D3;
+      const T g3 = gout * (w3 * V * Vq[q1] * Vq[q2]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T gk = g3 * ((k == 0 || k == 3) ? kp : km);
+        scat(j0[k], gk);
+        scat(j1[k], gk);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    if (q == d) continue;
+    const T gq = gVq[q] * T(0.25);
+    atomicAdd(&vhb.p[q][i], gq);
+    atomicAdd(&vhb.p[q][ip], gq);
+    atomicAdd(&vhb.p[q][nb.at(q, -1)], gq);
+    atomicAdd(&vhb.p[q][nb.at2(q, -1, d, +1)], gq);
+  }
+  atomicAdd(&vhb.p[d][i], gV);
+}
+
 // Reverse of the antidiffusive advector of a pass without the limiter: vb holds the adjoint
 // of its output on every face.
-template <typename T, int ND>
+template <typename T, int ND, bool EXT>
 __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> Vin, const T* __restrict__ G,
-                            bool iga, T* pb, W3<T> vhb) {
+                            bool iga, bool tot, bool abs_psi, T* pb, W3<T> vhb) {
   CELL_INDEX
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const T gout = vb.p[d][i];
-    if (nez(gout)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
+    if (nez(gout)) {
+      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, iga, tot, abs_psi, pb, vhb);
+      else antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
+    }
   }
   CELL_END
 }
@@ -427,10 +576,10 @@ __device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const decltype(Nbr
 // complete dL/dV on the face (d, i) with the limiter's part vbl, then the antidiffusive
 // advector that produced V (Eq. 6, scattered into pb and vhb).  On the last pass reversed
 // (mxb not null) also the bounds over psi^n = p0 and psi^(1) = psi.
-template <typename T, int ND>
+template <typename T, int ND, bool EXT>
 __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi, P3<T> Vu, P3<T> Vin,
-                         const T* __restrict__ G, bool unit, T* pb, W3<T> vhb, const T* __restrict__ mxb,
-                         const T* __restrict__ mnb, const T* __restrict__ p0, T* pb0) {
+                         const T* __restrict__ G, bool unit, bool tot, bool abs_psi, T* pb, W3<T> vhb,
+                         const T* __restrict__ mxb, const T* __restrict__ mnb, const T* __restrict__ p0, T* pb0) {
   grid_wait();
   grid_release();
   CELL_INDEX
@@ -446,7 +595,10 @@ __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi,
       dv = dpos(v) * psi[i] + dneg(v) * psi[ip];
     }
     const T gout = vbl.p[d][i] + fp * dv;
-    if (nez(gout)) antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
+    if (nez(gout)) {
+      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, unit, tot, abs_psi, pb, vhb);
+      else antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
+    }
   }
   if (nez(acc)) atomicAdd(&pb[i], acc);
   if (mxb) bounds_rev<T, ND>(nb, i, mxb[i], mnb[i], p0, psi, pb0, pb);
@@ -602,6 +754,7 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
 
   const int bs = 256;
   const unsigned nb = static_cast<unsigned>((N + bs - 1) / bs);
+  const bool ext = o.tot || o.abs;  // the pseudo-advector's reverse with the third-order terms or |psi|
   for (int k = K; k >= 2; --k) {
     const T* pbk = (k == K) ? psi_bar : pbl[k];
     P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
@@ -623,8 +776,9 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       P3<T> fbr{{fb[0], fb[1], fb[2]}};
       P3<T> vbr{{vbk[k][0], vbk[k][1], vbk[k][2]}};
       const bool last = k == 2;
-      if (launch_after(ka_fct_b<T, ND>, cell_grid(g, bs), dim3(bs), st, g, fbr, vbr, tp.psi[k - 1], vu, vprev, G,
-                       static_cast<bool>(o.iga), pbl[k - 1], vhbp, last ? mxb : nullptr, last ? mnb : nullptr,
+      if (launch_after(ext ? ka_fct_b<T, ND, true> : ka_fct_b<T, ND, false>, cell_grid(g, bs), dim3(bs), st, g, fbr,
+                       vbr, tp.psi[k - 1], vu, vprev, G, static_cast<bool>(o.iga), static_cast<bool>(o.tot),
+                       static_cast<bool>(o.abs), pbl[k - 1], vhbp, last ? mxb : nullptr, last ? mnb : nullptr,
                        tp.psi[0], pbl[0]) != cudaSuccess)
         return MPDATA_ECUDA;
     } else {
@@ -632,7 +786,12 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       ka_donor_flux<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, pbk, tp.psi[k - 1], vh, G, o.iga, pbl[k - 1],
                                                                    vhbk, nullptr, W3<T>{}, nullptr, 0, 0);
       P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
-      ka_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, pbl[k - 1], vhbp);
+      if (ext)
+        ka_antidiff<T, ND, true><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, o.tot, o.abs,
+                                                                  pbl[k - 1], vhbp);
+      else
+        ka_antidiff<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, false, false,
+                                                                   pbl[k - 1], vhbp);
     }
   }
   P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
@@ -666,7 +825,7 @@ int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const 
                      void* const* gc_bar, AdjMode mode, T* tape, T* psi_next) {
   Opts o = make_opts(handle_opts(h), handle_n_iters(h));
   handle_tuning(h, &o.kernel, &o.tile_rows);  // the fused recording follows the forward's kernel
-  if (o.tot || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+  if (o.dfl || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
   const Grid& gr = handle_grids(h)[0];
   if (gr.nd == 2 && gr.N >= (1LL << 31)) return MPDATA_EUNSUPPORTED;  // 32-bit indices of Nbr<2>
   const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,

@@ -577,3 +577,30 @@ def test_kahan_summation_is_closer_to_exact_than_plain(shape, ratio):
     rms = {k: float(np.sqrt((e ** 2).mean())) for k, e in errs.items()}
     assert rms["kahan"] < ratio * rms["plain"], rms
     assert np.abs(errs["kahan"]).max() <= 1.5
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("name", ["fct", "tot3_fct"])
+def test_abs_tangent_linear_and_adjoint(shape, name):
+    """abs on a variable-sign field (no cell near zero, where |psi| has its kink): the
+    tangent-linear step agrees with central differences of the forward step, and the adjoint is
+    its transpose (<TL dx, y> = <dx, AD y>)."""
+    n_iters, opts = ABS_SETS[name]
+    opts |= oracle.ABS
+    rng = np.random.default_rng(13)
+    f = wl.low_modes(rng, shape, 6)
+    psi = 0.5 * f / np.abs(f).max()
+    psi = np.where(np.abs(psi) < 0.05, psi + 0.1, psi)  # keep every cell away from the kink
+    gc = nondivergent(shape, rng, 0.3)
+    dpsi = rng.normal(size=shape)
+    dgc = [rng.normal(size=shape) * 0.1 for _ in shape]
+    tl = oracle.tl_step(psi, gc, dpsi, dgc, n_iters=n_iters, opts=opts)
+    eps = 1e-6
+    fp = oracle.step(psi + eps * dpsi, [v + eps * dv for v, dv in zip(gc, dgc)], n_iters=n_iters, opts=opts)
+    fm = oracle.step(psi - eps * dpsi, [v - eps * dv for v, dv in zip(gc, dgc)], n_iters=n_iters, opts=opts)
+    assert np.linalg.norm((fp - fm) / (2 * eps) - tl) <= 1e-8 * np.linalg.norm(tl)
+    y = rng.normal(size=shape)
+    pb, gcb = oracle.adj_step(psi, gc, y, n_iters=n_iters, opts=opts)
+    lhs = float(np.sum(tl * y))
+    rhs = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
