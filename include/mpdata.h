@@ -200,16 +200,17 @@ int mpdata_advance_compensated(mpdata_t h, const void* psi_in, const void* lo_in
 /*
  * Reverse of ONE step from state psi_n (the derivative of the donor-cell passes,
  * Eqs. 4-5, the antidiffusive advector, Eq. 6 with its multi-D cross terms, the
- * third-order terms of Sect. 3.1.2 and |psi| in its psi-fractions, Sect. 3.1.5, and
- * the FCT limiter, Sect. 3.1.4): on entry psi_bar = dL/dpsi^{n+1}, on exit
+ * third-order terms of Sect. 3.1.2, the divergent-flow term of Sect. 3.1.3 and |psi| in
+ * its psi-fractions, Sect. 3.1.5, and the FCT limiter, Sect. 3.1.4): on entry
+ * psi_bar = dL/dpsi^{n+1}, on exit
  * dL/dpsi^n (in place).  gc_bar (host array of ndims device pointers, or NULL):
  * dL/dgc_d is ADDED to gc_bar[d].  Branches (signs, FCT min/max) follow the
  * forward step's choices; [x]+ and [x]- have derivative 1/2 at 0 (|x| 0 at 0); a min/max
  * passes the derivative of its first extremal candidate.  The step is
  * recomputed internally, as mpdata_adjoint_record records it; the adjoint scratch
  * is allocated on first use and kept with the handle.  Errors: EINVAL;
- * EUNSUPPORTED for batched handles, for the dfl option, for source terms, open edges, for
- * n_iters > 4 and for 2D fields of 2^31 cells or more; ENOMEM; ECUDA.
+ * EUNSUPPORTED for batched handles, for source terms, open edges, for n_iters > 4 and for 2D
+ * fields of 2^31 cells or more; ENOMEM; ECUDA.
  */
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g,
                         void* psi_bar, void* const* gc_bar);

@@ -12,7 +12,8 @@
 //                   psi^(1): scatter (atomics)
 //   ka_donor_flux   (no FCT) donor-cell pass k: gather
 //   ka_antidiff     (no FCT) antidiffusive advector: scatter (atomics)
-// (the pseudo-advector's reverse has a second form, for the third-order terms and |psi|)
+// (the pseudo-advector's reverse has a second form, for the third-order terms, |psi| and the
+// divergent-flow term)
 //   ka_donor_flux   the first pass, which writes the step's outputs
 //
 // Adjoint arrays that receive scatters start at zero; the others are set by their
@@ -20,7 +21,7 @@
 // Conventions at the kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0
 // there), a max/min passes the derivative of the first extremal candidate in the
 // forward candidate order, the limiter's min(1, a, b) that of the first minimum.
-// The divergent-flow term and the source terms have no adjoint here.
+// The source terms have no adjoint here.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -280,8 +281,9 @@ __device__ __forceinline__ void antidiff_face_rev(const Nbr<ND>& nb, const declt
 }
 
 // The same with the options the form above leaves out, selected at run time: |psi| in every
-// psi-fraction (abs_psi, Sect. 3.1.5; d|psi|/dpsi = sgn psi, 0 at 0) and the third-order terms
-// (tot, Sect. 3.1.2), with C = V/Gb and C_q = Vq/Gb:
+// psi-fraction (abs_psi, Sect. 3.1.5; d|psi|/dpsi = sgn psi, 0 at 0), the divergent-flow term
+// (dfl, Sect. 3.1.3) -1/4 V (div_i + div_{i+e_d}) / Gb with div_j = sum_q (V_q at face j - at
+// face j - e_q), and the third-order terms (tot, Sect. 3.1.2), with C = V/Gb and C_q = Vq/Gb:
 //   + Gb (3 C|C| - 2 C^3 - C)/3 D_dd + sum_q Gb |C| C_q (1 - 2|C|) D_dq - (2/3) Gb C C_q1 C_q2 D_q1q2
 // D_dd = (psi_{i+2} - psi_{i+1} - psi_i + psi_{i-1}) over their sum along d; D_dq = ((psi at
 // i+e_d+e_q) - (i+e_q) - (i+e_d-e_q) + (i-e_q)) over their sum; D_q1q2 the same of the four
@@ -292,7 +294,7 @@ template <typename T, int ND>
 __device__ __forceinline__ void antidiff_face_rev_ext(const Nbr<ND>& nb, const decltype(Nbr<ND>::i) i, const int d,
                                                       const T gout, const T* __restrict__ psi, const P3<T>& Vin,
                                                       const T* __restrict__ G, const bool iga, const bool tot,
-                                                      const bool abs_psi, T* pb, const W3<T>& vhb) {
+                                                      const bool abs_psi, const bool dfl, T* pb, const W3<T>& vhb) {
   using I = decltype(Nbr<ND>::i);
   auto ps = [&](I j) { return abs_psi ? absv(psi[j]) : psi[j]; };
   auto scat = [&](I j, T v) { atomicAdd(&pb[j], abs_psi ? v * sgn(psi[j]) : v); };
@@ -410,6 +412,27 @@ __device__ __forceinline__ void antidiff_face_rev_ext(const Nbr<ND>& nb, const d
       }
     }
   }
+  if (dfl) {
+    // the advector's differences across cells i and i+e_d (for q = d the face between them
+    // enters both with opposite signs)
+    T dsum = T(0);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const T* Q = Vin.p[q];
+      const auto im_q = nb.at(q, -1);
+      const auto ipm_q = q == d ? i : nb.at2(q, -1, d, +1);
+      dsum = dsum + ((Q[i] - Q[im_q]) + (Q[ip] - Q[ipm_q]));
+    }
+    gV += gout * (T(-0.25) * dsum * rGb);
+    const T gw = gout * (T(-0.25) * V * rGb);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      atomicAdd(&vhb.p[q][i], gw);
+      atomicAdd(&vhb.p[q][nb.at(q, -1)], -gw);
+      atomicAdd(&vhb.p[q][ip], gw);
+      atomicAdd(&vhb.p[q][q == d ? i : nb.at2(q, -1, d, +1)], -gw);
+    }
+  }
 #pragma unroll
   for (int q = 0; q < ND; ++q) {
     if (q == d) continue;
@@ -426,13 +449,13 @@ __device__ __forceinline__ void antidiff_face_rev_ext(const Nbr<ND>& nb, const d
 // of its output on every face.
 template <typename T, int ND, bool EXT>
 __global__ void ka_antidiff(Grid g, P3<T> vb, const T* __restrict__ psi, P3<T> Vin, const T* __restrict__ G,
-                            bool iga, bool tot, bool abs_psi, T* pb, W3<T> vhb) {
+                            bool iga, bool tot, bool abs_psi, bool dfl, T* pb, W3<T> vhb) {
   CELL_INDEX
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     const T gout = vb.p[d][i];
     if (nez(gout)) {
-      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, iga, tot, abs_psi, pb, vhb);
+      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, iga, tot, abs_psi, dfl, pb, vhb);
       else antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, iga, pb, vhb);
     }
   }
@@ -578,7 +601,7 @@ __device__ __forceinline__ void bounds_rev(const Nbr<ND>& nb, const decltype(Nbr
 // (mxb not null) also the bounds over psi^n = p0 and psi^(1) = psi.
 template <typename T, int ND, bool EXT>
 __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi, P3<T> Vu, P3<T> Vin,
-                         const T* __restrict__ G, bool unit, bool tot, bool abs_psi, T* pb, W3<T> vhb,
+                         const T* __restrict__ G, bool unit, bool tot, bool abs_psi, bool dfl, T* pb, W3<T> vhb,
                          const T* __restrict__ mxb, const T* __restrict__ mnb, const T* __restrict__ p0, T* pb0) {
   grid_wait();
   grid_release();
@@ -596,7 +619,7 @@ __global__ void ka_fct_b(Grid g, P3<T> fb, P3<T> vbl, const T* __restrict__ psi,
     }
     const T gout = vbl.p[d][i] + fp * dv;
     if (nez(gout)) {
-      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, unit, tot, abs_psi, pb, vhb);
+      if constexpr (EXT) antidiff_face_rev_ext<T, ND>(nb, i, d, gout, psi, Vin, G, unit, tot, abs_psi, dfl, pb, vhb);
       else antidiff_face_rev<T, ND>(nb, i, d, gout, psi, Vin, G, unit, pb, vhb);
     }
   }
@@ -754,7 +777,8 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
 
   const int bs = 256;
   const unsigned nb = static_cast<unsigned>((N + bs - 1) / bs);
-  const bool ext = o.tot || o.abs;  // the pseudo-advector's reverse with the third-order terms or |psi|
+  // the pseudo-advector's reverse with the third-order terms, |psi| or the divergent-flow term
+  const bool ext = o.tot || o.abs || o.dfl;
   for (int k = K; k >= 2; --k) {
     const T* pbk = (k == K) ? psi_bar : pbl[k];
     P3<T> vh{{tp.vh[k][0], tp.vh[k][1], tp.vh[k][2]}};
@@ -778,7 +802,8 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       const bool last = k == 2;
       if (launch_after(ext ? ka_fct_b<T, ND, true> : ka_fct_b<T, ND, false>, cell_grid(g, bs), dim3(bs), st, g, fbr,
                        vbr, tp.psi[k - 1], vu, vprev, G, static_cast<bool>(o.iga), static_cast<bool>(o.tot),
-                       static_cast<bool>(o.abs), pbl[k - 1], vhbp, last ? mxb : nullptr, last ? mnb : nullptr,
+                       static_cast<bool>(o.abs), static_cast<bool>(o.dfl), pbl[k - 1], vhbp, last ? mxb : nullptr,
+                       last ? mnb : nullptr,
                        tp.psi[0], pbl[0]) != cudaSuccess)
         return MPDATA_ECUDA;
     } else {
@@ -788,10 +813,10 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       P3<T> gv{{vhb[k][0], vhb[k][1], vhb[k][2]}};  // dL/dV^k of the advector the antidiff produced
       if (ext)
         ka_antidiff<T, ND, true><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, o.tot, o.abs,
-                                                                  pbl[k - 1], vhbp);
+                                                                  o.dfl, pbl[k - 1], vhbp);
       else
         ka_antidiff<T, ND, false><<<cell_grid(g, bs), bs, 0, st>>>(g, gv, tp.psi[k - 1], vprev, G, o.iga, false, false,
-                                                                   pbl[k - 1], vhbp);
+                                                                   false, pbl[k - 1], vhbp);
     }
   }
   P3<T> v1{{gc[0], D > 1 ? gc[1] : nullptr, D > 2 ? gc[2] : nullptr}};
@@ -825,7 +850,7 @@ int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const 
                      void* const* gc_bar, AdjMode mode, T* tape, T* psi_next) {
   Opts o = make_opts(handle_opts(h), handle_n_iters(h));
   handle_tuning(h, &o.kernel, &o.tile_rows);  // the fused recording follows the forward's kernel
-  if (o.dfl || o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+  if (o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
   const Grid& gr = handle_grids(h)[0];
   if (gr.nd == 2 && gr.N >= (1LL << 31)) return MPDATA_EUNSUPPORTED;  // 32-bit indices of Nbr<2>
   const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,

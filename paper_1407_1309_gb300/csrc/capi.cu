@@ -470,7 +470,7 @@ int mpdata_step(mpdata_t h, void* psi, const void* const* gc, const void* g, con
 int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, void* psi_bar,
                         void* const* gc_bar) {
   if (!h || !psi_bar) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -490,7 +490,7 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
 // Checks shared by the reverse-step entry points: options, fields, a single-field handle.
 static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
   if (!h) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   int rc = validate_fields(h, psi_n, gc, g, nullptr);
   if (rc != MPDATA_OK) return rc;
@@ -501,7 +501,7 @@ static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, 
 
 int mpdata_adjoint_tape_bytes(mpdata_t h, size_t* bytes) {
   if (!h || !bytes) return MPDATA_EINVAL;
-  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_DFL | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
+  if (h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B | MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits))
     return MPDATA_EUNSUPPORTED;
   if (h->n_fields != 1 || h->n_iters > 4) return MPDATA_EUNSUPPORTED;
   *bytes = mpd::adjoint_tape_bytes(h, h->esize);

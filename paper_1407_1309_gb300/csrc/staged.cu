@@ -1347,7 +1347,7 @@ cudaError_t tape_nd(const Grid& g, const Opts& o, const T* const* gc, const T* G
   for (int k = 2; k <= K; ++k) {
     In3<T> vprev{{tp.vh[k - 1][0], tp.vh[k - 1][1], tp.vh[k - 1][2]}};
     Out3<T> vk{{tp.v[k][0], tp.v[k][1], tp.v[k][2]}};
-    if (ND == 3) {
+    if (ND == 3 && !o.dfl) {  // the z-march leaves the divergent-flow term to the generic kernel
       launch_antidiff3<T>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs, vk, st);
     } else {
       k_antidiff<T, ND><<<cell_grid(g, bs), bs, 0, st>>>(g, tp.psi[k - 1], vprev, T(1), G, o.iga, o.tot, o.abs,

@@ -85,8 +85,12 @@ def test_adjoint_fp32_close_to_oracle():
 
 
 # the options with the second form of the pseudo-advector's reverse: the third-order terms
-# (Sect. 3.1.2) and |psi| in the psi-fractions (Sect. 3.1.5), with and without the limiter
+# (Sect. 3.1.2), |psi| in the psi-fractions (Sect. 3.1.5) and the divergent-flow term (Sect.
+# 3.1.3, on a divergent advector), with and without the limiter
 EXT_CASES = {
+    "dfl": (2, capi.DFL),
+    "dfl3_fct": (3, capi.DFL | capi.FCT),
+    "dfl_tot3_fct": (3, capi.DFL | capi.TOT | capi.FCT),
     "tot2_fct": (2, capi.TOT | capi.FCT),
     "tot3_fct": (3, capi.TOT | capi.FCT),
     "tot3": (3, capi.TOT),
@@ -104,7 +108,12 @@ def ext_inputs(shape, opts, seed):
         psi = psi - 2.0
     if opts & capi.ABS:
         psi = psi - 2.1  # variable sign: the fractions read |psi|
-    return psi, nondivergent(shape, rng, 0.3), rng.normal(size=shape), rng
+    if opts & capi.DFL:  # a divergent advector, |C| <= 0.3
+        gc = [workloads.low_modes(rng, shape, 4) for _ in shape]
+        gc = [0.3 * v / np.abs(v).max() for v in gc]
+    else:
+        gc = nondivergent(shape, rng, 0.3)
+    return psi, gc, rng.normal(size=shape), rng
 
 
 @pytest.mark.parametrize("shape", EXT_SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -133,7 +142,7 @@ def test_adjoint_third_order_and_abs_match_oracle(shape, name, nug):
         assert np.abs(a - b).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("name", ["tot3_fct", "abs_fct"])
+@pytest.mark.parametrize("name", ["tot3_fct", "abs_fct", "dfl3_fct"])
 def test_adjoint_third_order_and_abs_fp32_close_to_oracle(name):
     """FP32 reverse step of the 3D configuration (n_iters = 3, tot, FCT, G) and of the |psi|
     option against the FP64 oracle (inputs rounded to FP32 on both sides): relative L2 1e-5."""
@@ -194,7 +203,7 @@ def test_autograd_gradient_3d_third_order_matches_finite_differences():
 
 
 @pytest.mark.parametrize("shape", [(14, 11), (6, 7, 5)], ids=lambda s: "x".join(map(str, s)))
-@pytest.mark.parametrize("name", ["tot3_fct", "abs_fct"])
+@pytest.mark.parametrize("name", ["tot3_fct", "abs_fct", "dfl3_fct"])
 def test_record_replay_third_order_and_abs(shape, name):
     """The split reverse step (tape, then the sweep from it) with these options gives the
     one-call reverse step (FP64, up to the order of the atomic additions) and the recorded step's
@@ -225,7 +234,7 @@ def test_adjoint_rejects_unsupported():
     dev = torch.device("cuda")
     shape = (8, 8)
     z = [torch.zeros(shape, device=dev), torch.zeros(shape, device=dev)]
-    for opts in (capi.DFL, capi.FCT | capi.DFL):
+    for opts in (capi.RHS_EULER_A, capi.FCT | capi.RHS_EULER_B):
         with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=opts) as m:
             rc = capi.mpdata_adjoint_step(m.h, z[0], z, None, z[1], raw=True)
             assert rc == capi.EUNSUPPORTED
@@ -365,7 +374,7 @@ def test_tape_bytes_and_rejections():
         assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, tape, z[0], raw=True) == capi.EINVAL
         assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, None, z[1], raw=True) == capi.EINVAL
         assert capi.mpdata_adjoint_replay(m.h, z[0], z[:2], None, None, z[1], raw=True) == capi.EINVAL
-    with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=capi.DFL) as m:
+    with Mpdata(shape, dtype=torch.float32, n_iters=2, opts=capi.RHS_EULER_A) as m:
         assert capi.mpdata_adjoint_record(m.h, z[0], z[:2], None, z[2], z[1], raw=True) == capi.EUNSUPPORTED
 
 

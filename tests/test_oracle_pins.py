@@ -604,3 +604,31 @@ def test_abs_tangent_linear_and_adjoint(shape, name):
     lhs = float(np.sum(tl * y))
     rhs = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("name", ["dfl", "dfl_it3_fct"])
+def test_dfl_tangent_linear_and_adjoint(shape, name):
+    """The divergent-flow term on a divergent advector (smooth seeded fields, |C| <= 0.3): the
+    tangent-linear step agrees with central differences of the forward step, and the adjoint is
+    its transpose (<TL dx, y> = <dx, AD y>)."""
+    n_iters, opts = OPTION_SETS[name]
+    rng = np.random.default_rng(17)
+    f = wl.low_modes(rng, shape, 6)
+    psi = 2.0 + 0.5 * f / np.abs(f).max()
+    gc = []
+    for _ in shape:
+        v = wl.low_modes(rng, shape, 4)
+        gc.append(0.3 * v / np.abs(v).max())
+    dpsi = rng.normal(size=shape)
+    dgc = [rng.normal(size=shape) * 0.1 for _ in shape]
+    tl = oracle.tl_step(psi, gc, dpsi, dgc, n_iters=n_iters, opts=opts)
+    eps = 1e-6
+    fp = oracle.step(psi + eps * dpsi, [v + eps * dv for v, dv in zip(gc, dgc)], n_iters=n_iters, opts=opts)
+    fm = oracle.step(psi - eps * dpsi, [v - eps * dv for v, dv in zip(gc, dgc)], n_iters=n_iters, opts=opts)
+    assert np.linalg.norm((fp - fm) / (2 * eps) - tl) <= 1e-8 * np.linalg.norm(tl)
+    y = rng.normal(size=shape)
+    pb, gcb = oracle.adj_step(psi, gc, y, n_iters=n_iters, opts=opts)
+    lhs = float(np.sum(tl * y))
+    rhs = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
