@@ -1,8 +1,8 @@
 """The variable-sign option abs (Sect. 3.1.5: |psi| in every psi-fraction of the
 pseudo-velocity) and the divergent-flow option dfl (Sect. 3.1.3) on the GPU against the
 oracle: 1D, 2D and 3D, with the limiter and the third-order terms, FP64 and FP32, single and
-batched handles; on a positive field abs is the basic scheme bit for bit; neither has a
-reverse step."""
+batched handles; on a positive field abs is the basic scheme bit for bit.  (Their reverse
+steps are checked against the oracle's adjoint in test_gpu_adjoint.py.)"""
 import numpy as np
 import pytest
 import torch
@@ -98,11 +98,8 @@ def test_abs_batched_handle_matches_oracle():
         off += n
 
 
-def test_abs_has_no_reverse_step_and_excludes_iga():
+def test_abs_excludes_iga():
     shape = (16, 16)
-    z = [torch.zeros(shape, dtype=torch.float64, device=DEV) for _ in range(3)]
-    with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.ABS | capi.FCT) as m:
-        assert capi.mpdata_adjoint_step(m.h, z[0], z[:2], None, z[2], raw=True) == capi.EUNSUPPORTED
     rc, h = capi.mpdata_create(2, [shape], capi.F64, 2, capi.ABS | capi.IGA, raw=True)
     assert rc == capi.EINVAL and not h
 
@@ -147,10 +144,7 @@ def test_dfl_fp32_and_nonunit_g_close_to_oracle(shape):
     assert np.abs(out64 - ref64).max() <= 1e-12 * np.abs(ref64).max()
 
 
-def test_dfl_has_no_reverse_step_and_excludes_iga():
+def test_dfl_excludes_iga():
     shape = (16, 16)
-    z = [torch.zeros(shape, dtype=torch.float64, device=DEV) for _ in range(3)]
-    with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.DFL | capi.FCT) as m:
-        assert capi.mpdata_adjoint_step(m.h, z[0], z[:2], None, z[2], raw=True) == capi.EUNSUPPORTED
     rc, h = capi.mpdata_create(2, [shape], capi.F64, 2, capi.DFL | capi.IGA, raw=True)
     assert rc == capi.EINVAL and not h
