@@ -525,7 +525,9 @@ __global__ void __launch_bounds__(kCThreads) k_p1b3v(Grid g, const float* __rest
       put<NC>(Qp(0) + w * W + 4 + NC * lane, r);
       if (lane == 0 || lane == 31) Qp(0)[w * W + hcol] = pass1_col(hcol, gh);
     }
-    __syncthreads();
+    // no barrier here: of plane z the bounds below read only the thread's own cells, written
+    // just above; what they read of other rows and lanes is plane z-1's, written at the
+    // previous step, before this step's barrier
     const int q = z - 1;
     if (w >= 1 && w <= kRows && q >= zb && yb < ny) {  // bounds of plane q, row yb
       float a0[NC + 3], b0[NC + 3], au[NC], ad[NC], azp[NC], azm[NC], bu[NC], bd[NC], bzp[NC], bzm[NC];
@@ -779,7 +781,9 @@ __global__ void __launch_bounds__(kCThreads, 2) k_corr3v(Grid g, const float* __
       put<NC>(U0 + w * W + 4 + NC * lane, bu);
       put<NC>(D0 + w * W + 4 + NC * lane, bd);
     }
-    __syncthreads();
+    // no barrier here: of plane s the limiter below reads only the thread's own factors, written
+    // just above; the factors of other rows and lanes it reads are plane s-1's, written at the
+    // previous step (the edge warps' columns included), before this step's barrier
     const int q = s - 1;
     if (w >= 1 && w <= kRows) {
       if (q >= zb && y < ny) {  // limit and advance row y of plane q = s - 1
