@@ -28,8 +28,12 @@ CASES = {
     "it2_fct": (2, capi.FCT),
 }
 # (z, y, x): x above 32 and ragged, y above 8, z above 16 and ragged (scalar z-march); x a
-# multiple of 4 above the 64- and 128-cell tiles of the vectorised z-march, the last tile partial
-SEAM_SHAPES = [(37, 19, 70), (17, 9, 33), (33, 17, 65), (37, 19, 136), (17, 9, 260), (21, 11, 68), (18, 3, 4)]
+# multiple of 4 above the 128-cell tiles of the vectorised z-march, the last tile partial; for
+# the vectorised kernels also one plane of one row (every halo row and plane wraps onto the
+# cell's own), a chunk shorter than 16 planes with fewer rows than a tile, and three tiles with
+# a 4-cell tail
+SEAM_SHAPES = [(37, 19, 70), (17, 9, 33), (33, 17, 65), (37, 19, 136), (17, 9, 260), (21, 11, 68), (18, 3, 4),
+               (1, 1, 132), (5, 3, 128), (18, 9, 388)]
 
 
 def rounded(a, dtype):
