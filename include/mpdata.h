@@ -227,10 +227,10 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
  *   factors of Sect. 3.1.4: (K-1)(1+d) arrays of N elements, plus d(K-1) + 2 + 2(K-1) with
  *   FCT (K = n_iters, d = ndims, N = cells).
  * mpdata_adjoint_record: the forward step from psi_n, writing its tape into `tape` and, when
- *   psi_next is not NULL, psi^{n+1} into psi_next (which must not be psi_n).  FP32 2D steps
- *   with n_iters = 2 (without Kahan summation, G, infinite gauge) and psi_next run the fused
- *   step kernel of mpdata_advance that also writes the tape (one launch); the rest run the
- *   staged kernels.  The tape refers to psi_n and gc, which must hold the same values at
+ *   psi_next is not NULL, psi^{n+1} into psi_next (which must not be psi_n).  2D steps with
+ *   n_iters = 2 (FP32 and FP64; without Kahan summation, G, infinite gauge, the third-order,
+ *   |psi| or divergent-flow terms) and psi_next run the fused step kernel of mpdata_advance
+ *   that also writes the tape (one launch); the rest run the staged kernels.  The tape refers to psi_n and gc, which must hold the same values at
  *   replay.
  * mpdata_adjoint_replay: the reverse sweep of the step recorded in `tape`, with the arguments
  *   and result of mpdata_adjoint_step (psi_bar in place, gc_bar accumulated).  Record + replay
