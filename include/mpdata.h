@@ -216,6 +216,21 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
                         void* psi_bar, void* const* gc_bar);
 
 /*
+ * mpdata_adjoint_step for a handle with an Euler source term (MPDATA_RHS_EULER_A or _B, Sect.
+ * 4.1: psi^{n+1} = ADV(psi^n) + dt R, or ADV(psi^n + dt R)), given the forward step's source r
+ * (device, N elements of the handle's dtype, read-only) and dt.  R is an input of the step, not
+ * a function of psi, so the reverse passes psi_bar through the source's addition unchanged;
+ * under euler_b the step is reversed about psi^n + dt R.  r_bar (device, N elements, or NULL):
+ * dL/dR is ADDED to it, dt dL/dpsi^{n+1} (euler_a) or dt dL/dpsi^n (euler_b).  Other arguments
+ * and errors as mpdata_adjoint_step; EINVAL also for a NULL r or a misaligned r_bar;
+ * EUNSUPPORTED for a handle without either source bit.  (mpdata_adjoint_step,
+ * mpdata_adjoint_record and mpdata_adjoint_replay, which take no source, return EUNSUPPORTED
+ * for such handles.)
+ */
+int mpdata_adjoint_step_rhs(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, const void* r,
+                            double dt, void* psi_bar, void* const* gc_bar, void* r_bar);
+
+/*
  * mpdata_adjoint_step split in two, so that a caller holding the forward states of several
  * steps (a checkpointed rollout) records each step's tape while it recomputes the states and
  * then runs only the reverse sweeps:

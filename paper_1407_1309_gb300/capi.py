@@ -27,7 +27,7 @@ EXPORTED = (
     "mpdata_diff_norms", "mpdata_check_courant", "mpdata_request_stop", "mpdata_clear_stop",
     "mpdata_sync", "mpdata_destroy", "mpdata_strerror", "mpdata_version", "mpdata_tune", "mpdata_set_stream",
     "mpdata_advance_compensated", "mpdata_selftest_division", "mpdata_selftest_fma_rate",
-    "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay",
+    "mpdata_adjoint_tape_bytes", "mpdata_adjoint_record", "mpdata_adjoint_replay", "mpdata_adjoint_step_rhs",
     "mpdata_set_rhs_linear", "mpdata_step_noalloc", "mpdata_sw_advance", "mpdata_sw_reset",
 )
 TUNE_TILE_ROWS = 1
@@ -74,6 +74,7 @@ def load(build_if_needed: bool = True):
             "mpdata_selftest_division": ([P, P, P, I64, P], I),
             "mpdata_selftest_fma_rate": ([I, I64, P, ctypes.POINTER(I64), P], I),
             "mpdata_adjoint_step": ([P, P, PP, P, P, PP], I),
+            "mpdata_adjoint_step_rhs": ([P, P, PP, P, P, D, P, PP, P], I),
             "mpdata_adjoint_tape_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], I),
             "mpdata_adjoint_record": ([P, P, PP, P, P, P], I),
             "mpdata_adjoint_replay": ([P, P, PP, P, P, P, PP], I),
@@ -269,6 +270,18 @@ def mpdata_adjoint_step(h, psi_n, gc, g, psi_bar, gc_bar=None, *, raw=False):
     if raw:
         return rc
     _check(rc, "mpdata_adjoint_step")
+
+
+def mpdata_adjoint_step_rhs(h, psi_n, gc, g, r, dt, psi_bar, gc_bar=None, r_bar=None, *, raw=False):
+    gcp, _k1 = _ptr_array(gc)
+    gbp = None
+    if gc_bar is not None:
+        gbp, _k2 = _ptr_array(gc_bar)
+    rc = load().mpdata_adjoint_step_rhs(h, _ptr(psi_n), gcp, _ptr(g), _ptr(r), float(dt), _ptr(psi_bar), gbp,
+                                        _ptr(r_bar))
+    if raw:
+        return rc
+    _check(rc, "mpdata_adjoint_step_rhs")
 
 
 def mpdata_adjoint_tape_bytes(h):

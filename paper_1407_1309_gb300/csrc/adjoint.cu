@@ -21,7 +21,9 @@
 // Conventions at the kinks: d[x]+/dx = d[x]-/dx = 1/2 at x = 0 (so d|x|/dx = 0
 // there), a max/min passes the derivative of the first extremal candidate in the
 // forward candidate order, the limiter's min(1, a, b) that of the first minimum.
-// The source terms have no adjoint here.
+// The Euler source terms (a given R added after or before the advection) enter only the one-call
+// reverse step: the reverse passes psi_bar through the addition, euler_b reverses the step about
+// psi^n + dt R, and dL/dR = dt psi_bar is accumulated where asked.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -634,6 +636,20 @@ __global__ void ka_accumulate(long long n, const T* __restrict__ src, T* __restr
   if (i < n) dst[i] += src[i];
 }
 
+// dst += a x (the source adjoint dL/dR = dt psi_bar)
+template <typename T>
+__global__ void ka_axpy(long long n, T a, const T* __restrict__ x, T* __restrict__ dst) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i < n) dst[i] += a * x[i];
+}
+
+// psi^0 = psi^n + dt R of a step with the euler_b source (the forward's pre-add, same expression)
+template <typename T>
+__global__ void ka_pre(long long n, const T* __restrict__ psi, const T* __restrict__ r, T dt, T* __restrict__ out) {
+  const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (i < n) out[i] = psi[i] + dt * r[i];
+}
+
 // Arrays of one step's tape: psi levels 1..K-1, the unlimited pseudo-advectors of passes
 // 2..K and, under FCT, the limited ones, the bounds and the factors.
 size_t tape_arrays(int K, int D, bool fct) {
@@ -688,10 +704,11 @@ struct AdjScratch {
 // sweep from a tape the caller recorded.
 enum class AdjMode { kStep, kRecord, kReplay };
 
+// R, dt, r_bar: the Euler source of the step (one-call reverse step only; R null without one).
 template <typename T, int ND>
 int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const T* const* gc, const T* G,
                T* psi_bar, void* const* gc_bar, cudaStream_t st, AdjMode mode = AdjMode::kStep,
-               T* tape = nullptr, T* psi_next = nullptr) {
+               T* tape = nullptr, T* psi_next = nullptr, const T* R = nullptr, T dt = T(0), T* r_bar = nullptr) {
   const int K = o.n_iters, D = ND;
   const long long N = g.N;
   Tape<T> tp{};
@@ -709,8 +726,9 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
     if (staged_forward_tape<T>(g, o, gc, G, tp, levels, psi_next, st) != cudaSuccess) return MPDATA_ECUDA;
     return MPDATA_OK;
   }
-  // the one-call reverse step keeps its tape (and the recorded step's unused result) in the scratch
-  const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) + 1 : 0;
+  // the one-call reverse step keeps its tape (and the recorded step's unused result, and under
+  // euler_b the advected state psi^n + dt R) in the scratch
+  const size_t tape_n = mode == AdjMode::kStep ? tape_arrays(K, D, o.fct) + 1 + (o.rhs_b ? 1 : 0) : 0;
   const size_t need = (tape_n + adj_arrays(K, D, o.fct)) * static_cast<size_t>(N) * sizeof(T);
   void** slot = handle_adj(h);
   // the adjoint scratch is allocated on first use and kept with the handle
@@ -725,6 +743,15 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
   // kept in the scratch too (behind them)
   T* cur = static_cast<T*>(hdr->ptr);
   T* const tape_base = mode == AdjMode::kStep ? cur + adj_arrays(K, D, o.fct) * static_cast<size_t>(N) : tape;
+  const int bs0 = 256;
+  const unsigned nb0 = static_cast<unsigned>((N + bs0 - 1) / bs0);
+  if (mode == AdjMode::kStep && o.rhs_b) {  // the step advects psi^n + dt R: its tape starts there
+    T* const p0 = tape_base + (tape_arrays(K, D, o.fct) + 1) * static_cast<size_t>(N);
+    ka_pre<T><<<nb0, bs0, 0, st>>>(N, psi_n, R, dt, p0);
+    psi_n = p0;
+  }
+  // euler_a: dL/dR = dt dL/dpsi^{n+1}, taken before the sweep overwrites psi_bar
+  if (mode == AdjMode::kStep && o.rhs_a && r_bar) ka_axpy<T><<<nb0, bs0, 0, st>>>(N, dt, psi_bar, r_bar);
   carve_tape<T>(tape_base, N, K, D, o.fct, psi_n, gc, tp, levels);
   auto take = [&]() { T* q = cur; cur += N; return q; };
   // adjoint arrays: first those that only receive atomic scatters (zeroed), then those
@@ -842,15 +869,19 @@ int adjoint_nd(mpdata_s* h, const Grid& g, const Opts& o, const T* psi_n, const 
       for (int d = 0; d < D; ++d)
         if (gc_bar[d]) ka_accumulate<T><<<nb, bs, 0, st>>>(N, vhb[1][d], static_cast<T*>(gc_bar[d]));
   }
+  // euler_b: dL/dR = dt dL/dpsi^0 = dt dL/dpsi^n
+  if (mode == AdjMode::kStep && o.rhs_b && r_bar) ka_axpy<T><<<nb, bs, 0, st>>>(N, dt, psi_bar, r_bar);
   return cudaGetLastError() == cudaSuccess ? MPDATA_OK : MPDATA_ECUDA;
 }
 
 template <typename T>
 int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const T* g, T* psi_bar,
-                     void* const* gc_bar, AdjMode mode, T* tape, T* psi_next) {
+                     void* const* gc_bar, AdjMode mode, T* tape, T* psi_next, const T* R = nullptr, T dt = T(0),
+                     T* r_bar = nullptr) {
   Opts o = make_opts(handle_opts(h), handle_n_iters(h));
   handle_tuning(h, &o.kernel, &o.tile_rows);  // the fused recording follows the forward's kernel
-  if (o.rhs_a || o.rhs_b || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
+  // the Euler sources only in the one-call reverse step, which is given R
+  if (((o.rhs_a || o.rhs_b) && (mode != AdjMode::kStep || !R)) || o.n_iters > kTapeMax) return MPDATA_EUNSUPPORTED;
   const Grid& gr = handle_grids(h)[0];
   if (gr.nd == 2 && gr.N >= (1LL << 31)) return MPDATA_EUNSUPPORTED;  // 32-bit indices of Nbr<2>
   const T* gc[3] = {static_cast<const T*>(gcv[0]), gr.nd > 1 ? static_cast<const T*>(gcv[1]) : nullptr,
@@ -858,9 +889,9 @@ int adjoint_dispatch(mpdata_s* h, const T* psi_n, const void* const* gcv, const 
   const T* G = o.nug ? g : nullptr;
   cudaStream_t st = handle_stream(h);
   switch (gr.nd) {
-    case 1: return adjoint_nd<T, 1>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
-    case 2: return adjoint_nd<T, 2>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
-    case 3: return adjoint_nd<T, 3>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next);
+    case 1: return adjoint_nd<T, 1>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next, R, dt, r_bar);
+    case 2: return adjoint_nd<T, 2>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next, R, dt, r_bar);
+    case 3: return adjoint_nd<T, 3>(h, gr, o, psi_n, gc, G, psi_bar, gc_bar, st, mode, tape, psi_next, R, dt, r_bar);
   }
   return MPDATA_EINVAL;
 }
@@ -889,6 +920,12 @@ int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g,
 }
 
 template <typename T>
+int adjoint_step_rhs(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, const T* r, T dt, T* psi_bar,
+                     void* const* gc_bar, T* r_bar) {
+  return adjoint_dispatch<T>(h, psi_n, gc, g, psi_bar, gc_bar, AdjMode::kStep, nullptr, nullptr, r, dt, r_bar);
+}
+
+template <typename T>
 int adjoint_record(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* tape, T* psi_next) {
   return adjoint_dispatch<T>(h, psi_n, gc, g, nullptr, nullptr, AdjMode::kRecord, tape, psi_next);
 }
@@ -901,6 +938,10 @@ int adjoint_replay(mpdata_s* h, const T* psi_n, const void* const* gc, const T* 
 
 template int adjoint_step<float>(mpdata_s*, const float*, const void* const*, const float*, float*, void* const*);
 template int adjoint_step<double>(mpdata_s*, const double*, const void* const*, const double*, double*, void* const*);
+template int adjoint_step_rhs<float>(mpdata_s*, const float*, const void* const*, const float*, const float*, float,
+                                     float*, void* const*, float*);
+template int adjoint_step_rhs<double>(mpdata_s*, const double*, const void* const*, const double*, const double*,
+                                      double, double*, void* const*, double*);
 template int adjoint_record<float>(mpdata_s*, const float*, const void* const*, const float*, float*, float*);
 template int adjoint_record<double>(mpdata_s*, const double*, const void* const*, const double*, double*, double*);
 template int adjoint_replay<float>(mpdata_s*, const float*, const void* const*, const float*, const float*, float*,

@@ -487,6 +487,28 @@ int mpdata_adjoint_step(mpdata_t h, const void* psi_n, const void* const* gc, co
                                    static_cast<double*>(psi_bar), gc_bar);
 }
 
+int mpdata_adjoint_step_rhs(mpdata_t h, const void* psi_n, const void* const* gc, const void* g, const void* r,
+                            double dt, void* psi_bar, void* const* gc_bar, void* r_bar) {
+  if (!h || !psi_bar || !r) return MPDATA_EINVAL;
+  if (!(h->opts & (MPDATA_RHS_EULER_A | MPDATA_RHS_EULER_B))) return MPDATA_EUNSUPPORTED;
+  if (h->opts & (MPDATA_RHS_TRAPEZ | MPDATA_SW | mpd::kOpenBits)) return MPDATA_EUNSUPPORTED;
+  int rc = validate_fields(h, psi_n, gc, g, r);
+  if (rc != MPDATA_OK) return rc;
+  if (!aligned(psi_bar, h->esize) || !aligned(r_bar, h->esize)) return MPDATA_EINVAL;
+  if (gc_bar)
+    for (int d = 0; d < h->nd; ++d)
+      if (gc_bar[d] && !aligned(gc_bar[d], h->esize)) return MPDATA_EINVAL;
+  if (h->n_fields != 1) return MPDATA_EUNSUPPORTED;
+  DeviceGuard dg(h->device);
+  if (h->dtype == MPDATA_F32)
+    return mpd::adjoint_step_rhs<float>(h, static_cast<const float*>(psi_n), gc, static_cast<const float*>(g),
+                                        static_cast<const float*>(r), static_cast<float>(dt),
+                                        static_cast<float*>(psi_bar), gc_bar, static_cast<float*>(r_bar));
+  return mpd::adjoint_step_rhs<double>(h, static_cast<const double*>(psi_n), gc, static_cast<const double*>(g),
+                                       static_cast<const double*>(r), dt, static_cast<double*>(psi_bar), gc_bar,
+                                       static_cast<double*>(r_bar));
+}
+
 // Checks shared by the reverse-step entry points: options, fields, a single-field handle.
 static int adjoint_checks(mpdata_t h, const void* psi_n, const void* const* gc, const void* g) {
   if (!h) return MPDATA_EINVAL;

@@ -88,6 +88,11 @@ void batched_free(mpdata_s* h);
 template <typename T>
 int adjoint_step(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, T* psi_bar,
                  void* const* gc_bar);
+// The same with the Euler source terms: R (r, dt of the step) added after (euler_a) or before
+// (euler_b) the advection; r_bar (nullable) accumulates dL/dR.
+template <typename T>
+int adjoint_step_rhs(mpdata_s* h, const T* psi_n, const void* const* gc, const T* g, const T* r, T dt, T* psi_bar,
+                     void* const* gc_bar, T* r_bar);
 void adjoint_free(mpdata_s* h);
 // The reverse step split in two: the forward tape of one step recorded into a caller buffer of
 // adjoint_tape_bytes (plus the step's result when psi_next is not null), and the reverse sweep

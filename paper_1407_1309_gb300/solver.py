@@ -56,9 +56,13 @@ class Mpdata:
         capi.mpdata_advance_compensated(self.h, psi_in, lo_in, psi_out, lo_out, gc, g, r, dt, n_steps, gc_scale)
         return psi_out, lo_out
 
-    def adjoint_step(self, psi_n, gc, psi_bar, g=None, gc_bar=None):
-        """psi_bar (in place): dL/dpsi^{n+1} -> dL/dpsi^n; gc_bar[d] += dL/dgc_d."""
-        capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
+    def adjoint_step(self, psi_n, gc, psi_bar, g=None, gc_bar=None, r=None, dt=0.0, r_bar=None):
+        """psi_bar (in place): dL/dpsi^{n+1} -> dL/dpsi^n; gc_bar[d] += dL/dgc_d.  Handles with an
+        Euler source pass the step's source r and dt (and r_bar += dL/dR if given)."""
+        if r is not None:
+            capi.mpdata_adjoint_step_rhs(self.h, psi_n, gc, g, r, dt, psi_bar, gc_bar, r_bar)
+        else:
+            capi.mpdata_adjoint_step(self.h, psi_n, gc, g, psi_bar, gc_bar)
         return psi_bar
 
     def tape_numel(self):

@@ -230,6 +230,58 @@ def test_record_replay_third_order_and_abs(shape, name):
     assert np.abs(nxt.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+SRC_CASES = {"fct": (2, capi.FCT), "tot3_fct": (3, capi.TOT | capi.FCT)}
+
+
+@pytest.mark.parametrize("shape", [(41,), (14, 11), (6, 7, 5)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("rhs", ["euler_a", "euler_b"])
+@pytest.mark.parametrize("name", sorted(SRC_CASES))
+def test_adjoint_with_euler_sources_matches_oracle(shape, rhs, name):
+    """The reverse step of a step with an Euler source (Sect. 4.1; R given, dt = 0.3) against the
+    oracle's adjoint (FP64, max-norm 1e-12), and dL/dR, accumulated onto r_bar, against its closed
+    form dt * dL/dpsi^{n+1} (euler_a) or dt * dL/dpsi^n (euler_b) and against central differences
+    of the oracle's forward step along a random direction."""
+    n_iters, opts = SRC_CASES[name]
+    rng = np.random.default_rng(len(shape) * 100 + n_iters + (7 if rhs == "euler_b" else 0))
+    psi = smooth_positive(shape, rng)
+    gc = nondivergent(shape, rng, 0.3)
+    y = rng.normal(size=shape)
+    R, dt = 0.5 * rng.normal(size=shape), 0.3
+    ref_pb, ref_gcb = oracle.adj_step(psi, gc, y, r=R, dt=dt, n_iters=n_iters, opts=opts, rhs=rhs)
+    dev = torch.device("cuda")
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    bit = capi.RHS_EULER_A if rhs == "euler_a" else capi.RHS_EULER_B
+    with Mpdata(shape, dtype=torch.float64, n_iters=n_iters, opts=opts | bit) as m:
+        pb = t(y)
+        gcb = [torch.zeros(shape, dtype=torch.float64, device=dev) for _ in shape]
+        rb = torch.full(shape, 0.25, dtype=torch.float64, device=dev)  # accumulated onto
+        m.adjoint_step(t(psi), [t(v) for v in gc], pb, gc_bar=gcb, r=t(R), dt=dt, r_bar=rb)
+        torch.cuda.synchronize()
+        got_pb, got_rb = pb.cpu().numpy(), rb.cpu().numpy() - 0.25
+        got_gcb = [v.cpu().numpy() for v in gcb]
+    scale = max(np.abs(ref_pb).max(), max(np.abs(v).max() for v in ref_gcb))
+    assert np.abs(got_pb - ref_pb).max() <= 1e-12 * scale
+    for a, b in zip(got_gcb, ref_gcb):
+        assert np.abs(a - b).max() <= 1e-12 * scale
+    want = dt * (y if rhs == "euler_a" else ref_pb)
+    assert np.abs(got_rb - want).max() <= 1e-12 * np.abs(want).max()
+    dR, eps = rng.normal(size=shape), 1e-6
+    L = lambda rr: float(np.sum(y * oracle.step(psi, gc, r=rr, dt=dt, n_iters=n_iters, opts=opts, rhs=rhs)))
+    fd = (L(R + eps * dR) - L(R - eps * dR)) / (2 * eps)
+    assert abs(fd - float(np.sum(got_rb * dR))) <= 1e-6 * max(abs(fd), 1.0)
+
+
+def test_adjoint_with_sources_argument_checks():
+    dev = torch.device("cuda")
+    shape = (8, 8)
+    z = [torch.zeros(shape, dtype=torch.float64, device=dev) for _ in range(4)]
+    with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.FCT) as m:  # no source bit
+        assert capi.mpdata_adjoint_step_rhs(m.h, z[0], z[:2], None, z[2], 0.1, z[3], raw=True) == capi.EUNSUPPORTED
+    with Mpdata(shape, dtype=torch.float64, n_iters=2, opts=capi.FCT | capi.RHS_EULER_A) as m:
+        assert capi.mpdata_adjoint_step_rhs(m.h, z[0], z[:2], None, None, 0.1, z[3], raw=True) == capi.EINVAL
+        assert capi.mpdata_adjoint_step(m.h, z[0], z[:2], None, z[3], raw=True) == capi.EUNSUPPORTED
+
+
 def test_adjoint_rejects_unsupported():
     dev = torch.device("cuda")
     shape = (8, 8)
