@@ -632,3 +632,29 @@ def test_dfl_tangent_linear_and_adjoint(shape, name):
     lhs = float(np.sum(tl * y))
     rhs = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{len(s)}d")
+@pytest.mark.parametrize("rhs", ["euler_a", "euler_b"])
+def test_adjoint_dot_product_with_sources(shape, rhs):
+    """Euler sources (Sect. 4.1) with a given R: the tangent-linear step agrees with central
+    differences of the forward step, and the adjoint is its transpose."""
+    n_iters, opts = OPTION_SETS["fct"]
+    rng = np.random.default_rng(19)
+    f = wl.low_modes(rng, shape, 6)
+    psi = 2.0 + 0.5 * f / np.abs(f).max()
+    gc = nondivergent(shape, rng, 0.3)
+    R, dt = 0.5 * rng.normal(size=shape), 0.3
+    dpsi = rng.normal(size=shape)
+    dgc = [rng.normal(size=shape) * 0.1 for _ in shape]
+    kw = dict(r=R, dt=dt, n_iters=n_iters, opts=opts, rhs=rhs)
+    tl = oracle.tl_step(psi, gc, dpsi, dgc, **kw)
+    eps = 1e-6
+    fp = oracle.step(psi + eps * dpsi, [v + eps * dv for v, dv in zip(gc, dgc)], **kw)
+    fm = oracle.step(psi - eps * dpsi, [v - eps * dv for v, dv in zip(gc, dgc)], **kw)
+    assert np.linalg.norm((fp - fm) / (2 * eps) - tl) <= 1e-8 * np.linalg.norm(tl)
+    y = rng.normal(size=shape)
+    pb, gcb = oracle.adj_step(psi, gc, y, **kw)
+    lhs = float(np.sum(tl * y))
+    rhs_ = float(np.sum(dpsi * pb) + sum(np.sum(a * b) for a, b in zip(dgc, gcb)))
+    assert abs(lhs - rhs_) <= 1e-12 * max(abs(lhs), 1.0)
